@@ -1,0 +1,313 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by arithmetic.
+
+Each ``pin_*`` function raises ``AssertionError`` if the oracle disagrees with
+what it pins.  ``tests/test_oracle.py`` runs them one by one; the planted-
+mistake test runs all of them against oracle builds with a deliberate bug and
+requires each bug to trip at least one pin.
+"""
+from __future__ import annotations
+
+import itertools
+import os
+import random
+from fractions import Fraction
+
+import numpy as np
+
+import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+_KIND = {"unsigned": O.UNSIGNED, "signed": O.SIGNED, "float": O.FLOAT}
+
+
+def load_trace(name):
+    """(format, ascending, rows) of a golden trace file."""
+    fmt = asc = None
+    rows = {}
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            if line.startswith("w="):
+                kv = dict(p.split("=") for p in line.split())
+                fmt = O.KeyFormat(int(kv["w"]), _KIND[kv["kind"]], int(kv["e"]), int(kv["f"]))
+                asc = kv["asc"] == "1"
+                continue
+            lvl, vals = line.split(":")
+            toks = vals.split()
+            if fmt.kind == O.FLOAT:
+                words = [int(t, 2) for t in toks]
+            else:
+                words = [int(t) & ((1 << fmt.w) - 1) for t in toks]
+            rows[int(lvl)] = words
+    return fmt, asc, rows
+
+
+def _run_levels(words, fmt, asc, mode, levels, **kw):
+    """State after ``levels`` bit levels; None = untouched input, 0 = full sort."""
+    a = np.array(words, dtype=np.uint64)
+    if levels is not None:
+        v, _ = O.bsort_words(a, fmt, not asc, mode, levels, check=True, **kw)
+        assert v == 0, "invariant violations: %d" % v
+    return a.tolist()
+
+
+def _check_trace(name):
+    fmt, asc, rows = load_trace(name)
+    last = max(rows)
+    for lvl, row in rows.items():
+        got = _run_levels(rows[0], fmt, asc, O.STABLE, lvl if lvl else None)
+        assert got == row, "%s level %d: %s != %s" % (name, lvl, got, row)
+    # the literal (swapping) partition reaches the same final row
+    got = _run_levels(rows[0], fmt, asc, O.LITERAL, 0)
+    assert got == rows[last], "%s literal final: %s" % (name, got)
+    got = np.array(rows[0], dtype=np.uint64)
+    O.sort_words_by_definition(got, fmt, not asc)
+    assert got.tolist() == rows[last], "%s definition order: %s" % (name, got.tolist())
+
+
+def pin_fig1_trace():
+    """Fig. 1: every row of the unsigned 3-bit trace."""
+    _check_trace("fig1_unsigned_trace.txt")
+
+
+def pin_fig2_trace():
+    """Fig. 2: every row of the signed 4-bit descending trace (Alg. 3)."""
+    _check_trace("fig2_signed_trace.txt")
+
+
+def pin_fig4_trace():
+    """Fig. 4: every row of the 6-bit minifloat trace (Algs. 4/5)."""
+    _check_trace("fig4_minifloat_trace.txt")
+
+
+def pin_fig4_printed_alg4_is_wrong():
+    """Alg. 4 as printed (both halves ascending) misorders Fig. 4's negatives."""
+    fmt, asc, rows = load_trace("fig4_minifloat_trace.txt")
+    got = _run_levels(rows[0], fmt, asc, O.STABLE, 0, literal_alg4=True)
+    assert got != rows[max(rows)], "printed Alg. 4 unexpectedly matches Fig. 4"
+
+
+def pin_theorem2_counterexamples():
+    """Thm. 2's arrays sort to numeric order in both float widths."""
+    for dt in (np.float32, np.float64, np.float16):
+        for arr in ([-2.0, 0.0, 0.5], [0.75, 2.0], [2.0, 0.75], [0.5, 0.0, -2.0]):
+            x = np.array(arr, dtype=dt)
+            got = O.bsort(x)
+            assert got.tolist() == sorted(arr), (dt, arr, got)
+            got = O.bsort(x, descending=True)
+            assert got.tolist() == sorted(arr, reverse=True), (dt, arr, got)
+
+
+# --- an independent Python restatement of the order, with exact rationals ---
+
+def py_order_key(word: int, fmt: O.KeyFormat):
+    """Sort key of one pattern under the paper's order (exact arithmetic)."""
+    w = fmt.w
+    if fmt.kind == O.UNSIGNED:
+        return (word,)
+    if fmt.kind == O.SIGNED:
+        return (word - (1 << w) if word >> (w - 1) else word,)
+    s = word >> (w - 1)
+    e = (word >> fmt.f) & ((1 << fmt.e) - 1)
+    m = word & ((1 << fmt.f) - 1)
+    bias = (1 << (fmt.e - 1)) - 1
+    if e == (1 << fmt.e) - 1:
+        if m:
+            return (0, -m) if s else (4, m)          # NaNs at both ends
+        return (1,) if s else (3,)                   # -inf, +inf
+    if e == 0:
+        mag = Fraction(m) * Fraction(2) ** (1 - bias - fmt.f)
+    else:
+        mag = Fraction((1 << fmt.f) + m) * Fraction(2) ** (e - bias - fmt.f)
+    return (2, -mag if s else mag, 0 if s else 1)   # -0 before +0
+
+
+def pin_bruteforce_tiny():
+    """All permutations of tiny inputs: the unique ordered one is the oracle's."""
+    rnd = random.Random(1234)
+    fmts = [O.KeyFormat(3, O.UNSIGNED), O.KeyFormat(4, O.SIGNED), O.KeyFormat(5, O.UNSIGNED),
+            O.KeyFormat(6, O.SIGNED), O.KeyFormat(6, O.FLOAT, 3, 2), O.KeyFormat(5, O.FLOAT, 2, 2),
+            O.KeyFormat(4, O.FLOAT, 2, 1)]
+    for fmt in fmts:
+        for trial in range(40):
+            n = rnd.randint(0, 6)
+            xs = [rnd.randrange(1 << fmt.w) for _ in range(n)]
+            for asc in (True, False):
+                want = None
+                for p in itertools.permutations(xs):
+                    ks = [py_order_key(v, fmt) for v in p]
+                    ok = all((ks[i] <= ks[i + 1]) if asc else (ks[i] >= ks[i + 1])
+                             for i in range(len(ks) - 1))
+                    if ok:
+                        if want is None:
+                            want = list(p)
+                        assert list(p) == want, "two different ordered permutations"
+                want = want if want is not None else []
+                for mode in (O.LITERAL, O.STABLE):
+                    a = np.array(xs, dtype=np.uint64)
+                    v, _ = O.bsort_words(a, fmt, not asc, mode, check=True)
+                    assert v == 0
+                    assert a.tolist() == want, (fmt, xs, asc, mode, a.tolist(), want)
+                a = np.array(xs, dtype=np.uint64)
+                O.sort_words_by_definition(a, fmt, not asc)
+                assert a.tolist() == want, (fmt, xs, asc, "definition", a.tolist(), want)
+
+
+def _special_float_sequence(dtype):
+    """Patterns in ascending order, from the paper's special-value rules."""
+    w = np.dtype(dtype).itemsize * 8
+    f = {16: 10, 32: 23, 64: 52}[w]
+    e = w - 1 - f
+    S = 1 << (w - 1)
+    E = ((1 << e) - 1) << f
+    Q = 1 << (f - 1)
+    M = (1 << f) - 1
+    one = ((1 << (e - 1)) - 1) << f
+    pos = [0, 1, M, 1 << f, one, E - 1, E, E | 1, E | (Q - 1), E | Q, E | M]
+    neg = [S | p for p in reversed(pos)]
+    return neg + pos
+
+
+def pin_special_values():
+    """-NaNs < -inf < negatives < -0 < +0 < positives < +inf < +NaNs (Sec. III-C)."""
+    rnd = random.Random(7)
+    for dt in (np.float16, np.float32, np.float64):
+        fmt = O.FORMATS[np.dtype(dt)]
+        seq = _special_float_sequence(dt)
+        for i in range(len(seq) - 1):
+            assert py_order_key(seq[i], fmt) < py_order_key(seq[i + 1], fmt)
+        for trial in range(5):
+            sh = seq[:]
+            rnd.shuffle(sh)
+            for desc in (False, True):
+                want = list(reversed(seq)) if desc else seq
+                a = np.array(sh, dtype=np.uint64)
+                O.bsort_words(a, fmt, desc, O.LITERAL)
+                assert a.tolist() == want, (dt, desc, "bsort")
+                a = np.array(sh, dtype=np.uint64)
+                O.sort_words_by_definition(a, fmt, desc)
+                assert a.tolist() == want, (dt, desc, "definition")
+
+
+def pin_float_values_match_numpy():
+    """The comparator's value of every finite fp16 pattern, and random fp32 /
+    fp64 patterns, equals numpy's conversion of the same bits."""
+    fmt = O.FORMATS[np.dtype(np.float16)]
+    allv = np.arange(1 << 16, dtype=np.uint16)
+    fin = allv[np.isfinite(allv.view(np.float16))]
+    ref = fin.view(np.float16).astype(np.float64)
+    for i in range(0, fin.size, 97):
+        assert O.float_value(int(fin[i]), fmt) == ref[i], hex(int(fin[i]))
+    for i in list(range(0, 64)) + list(range(1024, 1100)):  # subnormals, smallest normals
+        assert O.float_value(int(fin[i]), fmt) == ref[i], hex(int(fin[i]))
+    rng = np.random.default_rng(5)
+    for dt, ut in ((np.float32, np.uint32), (np.float64, np.uint64)):
+        fmt = O.FORMATS[np.dtype(dt)]
+        bits = rng.integers(0, np.iinfo(ut).max, size=4000, dtype=ut, endpoint=True)
+        bits[:8] = [0, 1, 2, 3, 5, 7, 9, 11]  # subnormals
+        vals = bits.view(dt)
+        for b, v in zip(bits, vals):
+            if np.isfinite(v):
+                assert O.float_value(int(b), fmt) == float(v), hex(int(b))
+
+
+def pin_exhaustive_small_words():
+    """Every 8- and 16-bit pattern, shuffled: integers match numpy's sort,
+    floats match the definition sort and numpy on their non-NaN part, and
+    descending is the exact reverse of ascending."""
+    rng = np.random.default_rng(11)
+    for dt in (np.uint8, np.int8, np.uint16, np.int16, np.float16):
+        w = np.dtype(dt).itemsize * 8
+        ut = np.uint8 if w == 8 else np.uint16
+        x = rng.permutation(np.arange(1 << w, dtype=np.uint64).astype(ut)).view(dt)
+        asc = O.bsort(x)
+        desc = O.bsort(x, descending=True)
+        assert np.array_equal(desc.view(ut), asc.view(ut)[::-1])
+        assert np.array_equal(asc.view(ut), O.sort_by_definition(x).view(ut))
+        if np.dtype(dt).kind in "iu":
+            assert np.array_equal(asc, np.sort(x))
+        else:
+            vals = asc[~np.isnan(asc)]
+            assert np.all(vals[:-1] <= vals[1:])
+            n_neg_nan = int(np.sum(np.isnan(asc) & np.signbit(asc)))
+            assert np.all(np.isnan(asc[:n_neg_nan])) and np.all(np.signbit(asc[:n_neg_nan]))
+            z = np.flatnonzero(asc.view(ut) == 0)[0]
+            assert asc.view(ut)[z - 1] == 0x8000  # -0 right before +0
+
+
+def pin_random_vs_numpy_and_definition():
+    """Random arrays of every machine type: the bit partition equals the
+    definition sort; integers also equal numpy's sort; NaN-free floats have
+    numpy's numeric order."""
+    rng = np.random.default_rng(3)
+    for dt in O.FORMATS:
+        w = dt.itemsize * 8
+        ut = {8: np.uint8, 16: np.uint16, 32: np.uint32, 64: np.uint64}[w]
+        bits = rng.integers(0, np.iinfo(ut).max, size=3000, dtype=ut, endpoint=True)
+        x = bits.view(dt)
+        for desc in (False, True):
+            got = O.bsort(x, descending=desc)
+            want = O.sort_by_definition(x, descending=desc)
+            assert np.array_equal(got.view(ut), want.view(ut)), (dt, desc)
+            if dt.kind in "iu":
+                ns = np.sort(x)
+                assert np.array_equal(got, ns[::-1] if desc else ns), (dt, desc)
+            else:
+                clean = x[np.isfinite(x) & (x != 0)]
+                g = O.bsort(clean, descending=desc)
+                ns = np.sort(clean)
+                assert np.array_equal(g, ns[::-1] if desc else ns), (dt, desc)
+
+
+def pin_invariants_every_partition():
+    """Invariants (i)/(ii) of Sec. II hold after every partition, both modes."""
+    rng = np.random.default_rng(9)
+    for dt in O.FORMATS:
+        w = dt.itemsize * 8
+        ut = {8: np.uint8, 16: np.uint16, 32: np.uint32, 64: np.uint64}[w]
+        x = rng.integers(0, np.iinfo(ut).max, size=1500, dtype=ut, endpoint=True).view(dt)
+        for mode in (O.LITERAL, O.STABLE):
+            for desc in (False, True):
+                words = O.to_words(x)
+                v, parts = O.bsort_words(words, O.FORMATS[dt], desc, mode, check=True)
+                assert v == 0 and parts > 0
+
+
+def pin_at_most_w_levels():
+    """Thm. 4: w bit levels sort fully; limiting to w levels changes nothing."""
+    rng = np.random.default_rng(4)
+    for dt in O.FORMATS:
+        w = dt.itemsize * 8
+        ut = {8: np.uint8, 16: np.uint16, 32: np.uint32, 64: np.uint64}[w]
+        x = rng.integers(0, np.iinfo(ut).max, size=800, dtype=ut, endpoint=True).view(dt)
+        full = O.bsort(x, mode=O.STABLE)
+        lim = O.bsort(x, mode=O.STABLE, max_levels=w)
+        assert np.array_equal(full.view(ut), lim.view(ut))
+
+
+def pin_idempotent_and_modes_agree():
+    rng = np.random.default_rng(6)
+    for dt in O.FORMATS:
+        w = dt.itemsize * 8
+        ut = {8: np.uint8, 16: np.uint16, 32: np.uint32, 64: np.uint64}[w]
+        x = rng.integers(0, np.iinfo(ut).max, size=1000, dtype=ut, endpoint=True).view(dt)
+        a = O.bsort(x)
+        assert np.array_equal(O.bsort(a).view(ut), a.view(ut))
+        assert np.array_equal(O.bsort(x, mode=O.STABLE).view(ut), a.view(ut))
+
+
+ALL_PINS = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]
+
+
+def failing():
+    """Names of the pins that fail (used against planted-mistake builds)."""
+    bad = []
+    for p in ALL_PINS:
+        try:
+            p()
+        except Exception:  # noqa: BLE001 - any failure counts
+            bad.append(p.__name__)
+    return bad
