@@ -1,0 +1,337 @@
+"""Benchmark of the GB300 bsort library (one JSON line on rank 0).
+
+Default workload: one array of 2^28 int32 keys, uniform over the full bit
+range (every bit pattern equally likely), sorted ascending -- the 32-bit
+plain-sort configuration the throughput target is quoted on.  A step is one
+complete sort of one such array, already resident in HBM; each timed step
+sorts its own unsorted copy (the 1 GiB input is larger than the 129 MB L2).
+
+  value         Gkeys/s over the timed steps, all ranks (max-over-ranks time)
+  e2e           the same metric through bsort_keys_host(): host array in,
+                host array out, copies inside the timed region
+  roofline      the kernel with the largest share of the step: algorithmic
+                bytes of its launches / their CUDA-event time, against the
+                measured HBM copy bandwidth
+  cpu_baseline  the CPU oracle on a bounded sample of the same workload
+
+``--impl reference`` times the oracle itself (the only reference this paper
+has: it publishes no code) on the same workload, a bounded sample per step.
+With torchrun (N > 1) every rank sorts its own array (independent replicas,
+weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "Gkeys/s & % HBM roofline per dtype at 2^28 keys; batched vs plain; serve p99 ms"
+UNIT = "Gkeys/s"
+DTYPE_TAG = {"uint8": "u8", "int8": "i8", "uint16": "u16", "int16": "i16", "float16": "f16",
+             "uint32": "u32", "int32": "i32", "float32": "f32", "uint64": "u64", "int64": "i64",
+             "float64": "f64"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="bsort", choices=["bsort", "reference"])
+    ap.add_argument("--dtype", default="int32")
+    ap.add_argument("--dist", default="uniform")
+    ap.add_argument("--log2n", type=int, default=28)
+    ap.add_argument("--desc", action="store_true")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-sample-log2", type=int, default=23)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(x, descending, sample_log2):
+    """The oracle (literal partition, single thread) on the first 2^k keys."""
+    import oracle as O
+    O.build()
+    m = min(x.size, 1 << sample_log2)
+    sample = np.ascontiguousarray(x[:m])
+    t0 = time.perf_counter()
+    O.bsort(sample, descending=descending)
+    dt = time.perf_counter() - t0
+    return {"value": m / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "first 2^%d keys of the same input (%d keys), literal partition, one thread, "
+                      "%.1f s" % (sample_log2, m, dt)}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the oracle itself, timed on the host cores."""
+    if rank != 0:
+        return
+    import oracle as O
+    O.build()
+    n = 1 << args.log2n
+    m = min(n, 1 << args.cpu_sample_log2)
+    x = W.make(args.dist, args.dtype, m, seed=args.seed)
+    times = []
+    for i in range(args.warmup + args.steps):
+        y = x.copy()
+        t0 = time.perf_counter()
+        O.bsort(y, descending=args.desc)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = m * len(times) / total / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / len(times) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": DTYPE_TAG.get(args.dtype, args.dtype), "data": "synthetic",
+        "config": {"workload": "plain sort, %s %s, 2^%d keys, %s (each step: the oracle on a "
+                                "2^%d-key sample)" % (args.dtype, args.dist, args.log2n,
+                                                      "descending" if args.desc else "ascending",
+                                                      args.cpu_sample_log2),
+                   "n": n, "sample_keys": m},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "2^%d keys per step, literal partition, one thread"
+                                   % args.cpu_sample_log2},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    import paper_2603_08929_gb300 as bs
+    from paper_2603_08929_gb300 import build as B
+
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0:
+        B.build()
+    if world > 1:
+        torch.distributed.barrier()
+    B.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    n = 1 << args.log2n
+    x = W.make(args.dist, args.dtype, n, seed=args.seed + rank)
+    esize = x.dtype.itemsize
+    total_steps = args.warmup + args.steps
+    base = torch.from_numpy(x).to(dev)
+    bufs = [base.clone() for _ in range(total_steps)]
+    del base
+    ws = torch.empty(bs.workspace_bytes(n, args.dtype), dtype=torch.uint8, device=dev)
+    h = bs.Handle()
+    h.set_profiling(True)
+    stream = torch.cuda.current_stream()
+
+    for i in range(args.warmup):
+        bs.bsort_keys_ws(h, bufs[i], ws, descending=args.desc, stream=stream)
+    torch.cuda.synchronize()
+    if h.get_error(stream) != 0:
+        raise RuntimeError("device error word set during warm-up")
+    h.profile()  # drop the warm-up records
+
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for i in range(args.warmup, total_steps):
+        bs.bsort_keys_ws(h, bufs[i], ws, descending=args.desc, stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    # per-launch CUDA-event times recorded by the library on the same stream
+    prof = h.profile()
+    launches = prof["launches"]
+    per_kind = {}
+    for r in prof["records"]:
+        k = per_kind.setdefault(r["kind"], {"ms": 0.0, "bytes": 0, "launches": 0})
+        k["ms"] += r["ms"]
+        k["bytes"] += r["counted_bytes"]
+        k["launches"] += 1
+    if world > 1:
+        torch.distributed.barrier()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    clock_info = clocks.stop() if clocks else None
+    if h.get_error(stream) != 0:
+        raise RuntimeError("device error word set during the timed steps")
+
+    # step time: sum of each step's sort (events around every launch group)
+    sort_ms = sum(k["ms"] for k in per_kind.values()) / args.steps
+    ms_per_step = elapsed_ms / args.steps
+    if world > 1:
+        t = torch.tensor([ms_per_step], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_per_step = float(t.item())
+    value = n * world / (ms_per_step * 1e-3) / 1e9
+
+    # correctness of the last timed step (cheap properties at full size)
+    out = bufs[-1]
+    ok_sorted = bool(torch.all(out[:-1] <= out[1:]).item()) if (
+        args.dist == "uniform" and args.dtype.startswith(("int", "uint")) and not args.desc) else None
+
+    peak, peak_src = load_peaks()
+    dom_kind = max(per_kind.items(), key=lambda kv: kv[1]["ms"])[0]
+    dk = per_kind[dom_kind]
+    achieved = dk["bytes"] / (dk["ms"] * 1e-3) / 1e9 if dk["ms"] > 0 else 0.0
+    total_bytes = sum(k["bytes"] for k in per_kind.values()) / args.steps
+    sort_gbs = total_bytes / (ms_per_step * 1e-3) / 1e9
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_TAG.get(args.dtype, args.dtype),
+        "data": "synthetic",
+        "config": {"workload": "plain sort, %s %s, 2^%d keys, %s" % (
+            args.dtype, args.dist, args.log2n, "descending" if args.desc else "ascending"),
+            "n": n, "per_gpu_keys": n, "l2": "input 2^%d x %d B > L2; each step sorts its own copy"
+                                            % (args.log2n, esize),
+            "parallelism": "replicas%d" % world},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "kernel": dom_kind, "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
+                     "traffic": None},
+        "sort_roofline": {"counted_bytes_per_step": total_bytes, "achieved": sort_gbs,
+                          "frac": sort_gbs / peak, "peak": peak,
+                          "fixed_2nb_frac": 2 * n * esize / (ms_per_step * 1e-3) / 1e9 / peak},
+        "kernels": {k: {"ms_per_step": v["ms"] / args.steps, "share": v["ms"] / (sort_ms * args.steps),
+                        "gbs": v["bytes"] / (v["ms"] * 1e-3) / 1e9 if v["ms"] > 0 else 0.0,
+                        "launches_per_step": v["launches"] / args.steps}
+                    for k, v in sorted(per_kind.items())},
+        "sorted_check": ok_sorted,
+    }
+    if clock_info:
+        line["clocks"] = clock_info
+
+    if not args.no_e2e:
+        host = torch.from_numpy(x.copy()).pin_memory()
+        pristine = host.clone()
+        for _ in range(2):
+            host.copy_(pristine)
+            bs.bsort_keys_host(host, descending=args.desc)
+        ts = []
+        for _ in range(max(3, min(args.steps, 5))):
+            host.copy_(pristine)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            bs.bsort_keys_host(host, descending=args.desc)
+            ts.append(time.perf_counter() - t0)
+        e2e_s = statistics.median(ts)
+        line["e2e"] = {"value": n / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": n * esize,
+                       "d2h_bytes_per_step": n * esize, "ms_per_step": e2e_s * 1e3,
+                       "api": "bsort_keys_host (pinned host array in and out)"}
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(x, args.desc, args.cpu_sample_log2)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,183 @@
+/*
+ * bsort.h -- C ABI of the GB300 (sm_103a) bsort library.
+ *
+ * Sorts arrays of 8..64-bit unsigned and signed integers and IEEE floats into
+ * the order defined by the bsort paper (Guzman, "bsort: a theoretically
+ * efficient non-comparison-based sorting algorithm for integer and
+ * floating-point numbers"):
+ *   - integers: numeric order (Sec. II, Alg. 2 for unsigned keys; Sec. III-A,
+ *     Alg. 3 for two's-complement keys);
+ *   - floats: sign, then exponent, then mantissa, with the negative half in
+ *     the inverted direction (Sec. III-B, Thms. 2/3, Algs. 4/5, Fig. 4), which
+ *     places -NaN < -inf < negatives < -0 < +0 < positives < +inf < +NaN, NaNs
+ *     ordered by their mantissa field (Sec. III-C, special values).
+ * A descending sort is the exact reverse of the ascending one.  Keys are
+ * moved as raw bit patterns: no NaN canonicalisation, no flushing of
+ * subnormals, signalling NaNs keep their bits.
+ *
+ * Every call sorts in place: the result is written back into the caller's
+ * array, as the paper's functions return "the same array a but sorted"
+ * (Algs. 3/4 outputs).
+ *
+ * Conventions shared by all entry points
+ *   - `keys` / offsets are DEVICE pointers unless the name says host; the
+ *     caller owns them.  Pointers must be aligned to the key size; 16-byte
+ *     alignment is a fast path, not a requirement.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device work is asynchronous on `stream` unless stated.
+ *   - Arguments are validated before any launch; a rejected call launches
+ *     nothing and leaves the keys untouched.
+ *   - Errors detected on the device (a work list exceeding its planned
+ *     capacity, an expired bounded wait) set a device error word that
+ *     bsort_get_error() returns; device code never traps or spins forever.
+ *   - No entry point prints or aborts.
+ */
+#ifndef BSORT_H_
+#define BSORT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BSORT_U8 = 0,
+    BSORT_I8 = 1,
+    BSORT_U16 = 2,
+    BSORT_I16 = 3,
+    BSORT_F16 = 4,  /* IEEE binary16: 1 sign, 5 exponent, 10 mantissa bits */
+    BSORT_U32 = 5,
+    BSORT_I32 = 6,
+    BSORT_F32 = 7,
+    BSORT_U64 = 8,
+    BSORT_I64 = 9,
+    BSORT_F64 = 10
+} bsort_dtype;
+
+typedef enum {
+    BSORT_OK = 0,
+    BSORT_ERR_INVALID_ARG = 1,          /* NULL pointer, bad dtype/mode, bad handle */
+    BSORT_ERR_UNSUPPORTED = 2,          /* valid request this build cannot serve */
+    BSORT_ERR_MISALIGNED = 3,           /* pointer not aligned to the key size */
+    BSORT_ERR_NO_MEMORY = 4,            /* device allocation failed */
+    BSORT_ERR_WORKSPACE_TOO_SMALL = 5,  /* ws_bytes < bsort_workspace_bytes() */
+    BSORT_ERR_CUDA = 6,                 /* a CUDA runtime call failed */
+    BSORT_ERR_TIMEOUT = 7,              /* a bounded device wait expired */
+    BSORT_ERR_CAPACITY = 8,             /* a device work list outgrew its plan */
+    BSORT_ERR_INTERNAL = 9              /* a device-side bounds check refused a store */
+} bsort_status;
+
+typedef enum {
+    BSORT_MODE_PINGPONG = 0,  /* default: an n-key alternate buffer in the workspace */
+    BSORT_MODE_INPLACE = 1    /* reserved: block permutation inside the caller's array */
+} bsort_mode;
+
+typedef struct bsort_handle bsort_handle;
+
+/* Human-readable name of a status code; never NULL. */
+const char *bsort_status_string(bsort_status status);
+
+/*
+ * Sorts keys[0, n) of type `dt` in place on `stream` (ascending if
+ * `descending` == 0).  Uses a per-device default handle whose workspace is
+ * allocated with cudaMalloc on first use and grown when a larger n arrives
+ * (growth synchronises the device).  n == 0 or 1: returns BSORT_OK with no
+ * launch.  keys == NULL with n > 1: BSORT_ERR_INVALID_ARG.
+ */
+bsort_status bsort_keys(void *keys, size_t n, bsort_dtype dt, int descending, void *stream);
+
+/*
+ * Bytes of device workspace bsort_keys_ws() needs for n keys of `dt` in
+ * `mode` (host-only computation, no CUDA call).  Ping-pong mode needs the
+ * n-key alternate buffer plus metadata bounded by n / (finish-threshold).
+ */
+bsort_status bsort_workspace_bytes(size_t n, bsort_dtype dt, bsort_mode mode, size_t *bytes);
+
+/* Creates / destroys an explicit handle (profiling state, device error word,
+ * statistics of the last call).  A handle must not be used by two host
+ * threads at once. */
+bsort_status bsort_handle_create(bsort_handle **handle);
+bsort_status bsort_handle_destroy(bsort_handle *handle);
+
+/*
+ * bsort_keys with a caller-provided workspace: no allocation, no host
+ * synchronisation, so the call can be captured in a CUDA graph.  `workspace`
+ * is a device pointer, 256-byte aligned, of at least
+ * bsort_workspace_bytes(n, dt, mode) bytes; its contents need no
+ * initialisation and are scratch after the call.
+ */
+bsort_status bsort_keys_ws(bsort_handle *handle, void *keys, size_t n, bsort_dtype dt, int descending,
+                           bsort_mode mode, void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * End-to-end sort of a HOST array: copies host_keys[0, n) to the device,
+ * sorts it and copies the result back into host_keys.  Uses the per-device
+ * default handle and a cached device buffer.  Synchronous: returns after the
+ * result is in host memory.  Pinned host memory gives the fastest copies.
+ */
+bsort_status bsort_keys_host(void *host_keys, size_t n, bsort_dtype dt, int descending, void *stream);
+
+/*
+ * Waits for `stream`, then returns (and clears) the device error word of the
+ * last call made with `handle` (NULL = the default handle of the current
+ * device): BSORT_OK, BSORT_ERR_CAPACITY, BSORT_ERR_TIMEOUT or
+ * BSORT_ERR_INTERNAL.
+ */
+bsort_status bsort_get_error(bsort_handle *handle, void *stream);
+
+/* ---- measurement ------------------------------------------------------- */
+
+enum { BSORT_PROFILE_MAX = 1024, BSORT_PROFILE_MAX_CALLS = 64 };
+
+/* kinds of device launches, used in profile records */
+typedef enum {
+    BSORT_K_INIT = 0,     /* resets the work lists */
+    BSORT_K_HIST = 1,     /* key transform + digit histogram of one level */
+    BSORT_K_SCAN = 2,     /* per-digit offsets across chunks */
+    BSORT_K_CLASSIFY = 3, /* bucket digit bases, child classification */
+    BSORT_K_SCATTER = 4,  /* shared-memory-staged digit scatter */
+    BSORT_K_FINISH = 5,   /* per-bucket shared-memory finish + decode */
+    BSORT_K_FILL = 6,     /* write-only fill of constant runs */
+    BSORT_K_COUNT_HIST = 7,  /* 8/16-bit: histogram of all key bits */
+    BSORT_K_COUNT_SCAN = 8,  /* 8/16-bit: bin starts */
+    BSORT_K_COUNT_FILL = 9   /* 8/16-bit: counting fill of the output */
+} bsort_kernel_kind;
+
+typedef struct {
+    int32_t kind;            /* bsort_kernel_kind */
+    int32_t level;           /* MSD level for per-level kernels, else -1 */
+    int32_t call;            /* index of the call since the records were last read */
+    float ms;                /* CUDA-event time of this launch group on the call's stream */
+    uint64_t keys;           /* keys this launch processed (device counters) */
+    uint64_t counted_bytes;  /* algorithmic HBM bytes of this launch */
+} bsort_profile_record;
+
+typedef struct {
+    int32_t num_records;
+    int32_t num_calls;       /* calls covered by the records */
+    int32_t num_launches;    /* kernels launched by those calls */
+    int32_t pad;
+    bsort_profile_record rec[BSORT_PROFILE_MAX];
+} bsort_profile;
+
+/* Enables CUDA-event timing of every launch of later calls on `handle`.
+ * Records accumulate over up to BSORT_PROFILE_MAX_CALLS calls (each call
+ * also copies its work counters into a handle-owned device slot, on its
+ * stream, so no call synchronises) until bsort_handle_get_profile(). */
+bsort_status bsort_handle_set_profiling(bsort_handle *handle, int enable);
+
+/* Synchronises with the device, returns the records accumulated since the
+ * last read (calls beyond BSORT_PROFILE_MAX_CALLS are not recorded) and
+ * clears them. */
+bsort_status bsort_handle_get_profile(bsort_handle *handle, bsort_profile *out);
+
+/* Number of kernels the last call on `handle` launched (host count). */
+bsort_status bsort_last_launch_count(bsort_handle *handle, int *launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSORT_H_ */

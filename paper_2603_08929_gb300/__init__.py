@@ -1,0 +1,212 @@
+"""GB300 (sm_103a) bsort: the bsort key order for 8..64-bit integers and IEEE
+floats, computed by hand-written CUDA kernels behind a C ABI (``include/bsort.h``).
+
+This package is a thin binding: it marshals arguments to the shared library
+``_lib/libbsort.so`` and raises on error.  Every step of a sort runs in the
+library's kernels; there is no CPU path.  Build the library with
+``paper_2603_08929_gb300.build.build()`` (done by ``__graft_entry__.build()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "DTYPES", "BsortError", "lib", "bsort_keys", "bsort_keys_ws", "bsort_keys_host",
+    "workspace_bytes", "Handle", "sort_", "status_string",
+]
+
+BSORT_OK = 0
+MODE_PINGPONG, MODE_INPLACE = 0, 1
+
+# bsort_dtype codes, in the order of include/bsort.h
+DTYPES = ["uint8", "int8", "uint16", "int16", "float16", "uint32", "int32", "float32",
+          "uint64", "int64", "float64"]
+_CODE = {name: i for i, name in enumerate(DTYPES)}
+
+KERNEL_KINDS = ["init", "hist", "scan", "classify", "scatter", "finish", "fill",
+                "count_hist", "count_scan", "count_fill"]
+
+_PROFILE_MAX = 1024
+
+
+class _Record(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("level", ctypes.c_int32), ("call", ctypes.c_int32),
+                ("ms", ctypes.c_float), ("keys", ctypes.c_uint64), ("counted_bytes", ctypes.c_uint64)]
+
+
+class _Profile(ctypes.Structure):
+    _fields_ = [("num_records", ctypes.c_int32), ("num_calls", ctypes.c_int32),
+                ("num_launches", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("rec", _Record * _PROFILE_MAX)]
+
+
+class BsortError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__((what + ": " if what else "") + status_string(status))
+
+
+_lib = None
+
+
+def lib():
+    """The loaded C library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise ImportError("the bsort CUDA library is not built (%s missing); run "
+                              "paper_2603_08929_gb300.build.build()" % path)
+        L = ctypes.CDLL(path)
+        vp, sz, i = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int
+        L.bsort_status_string.argtypes = [i]
+        L.bsort_status_string.restype = ctypes.c_char_p
+        L.bsort_keys.argtypes = [vp, sz, i, i, vp]
+        L.bsort_keys.restype = i
+        L.bsort_workspace_bytes.argtypes = [sz, i, i, ctypes.POINTER(sz)]
+        L.bsort_workspace_bytes.restype = i
+        L.bsort_handle_create.argtypes = [ctypes.POINTER(vp)]
+        L.bsort_handle_create.restype = i
+        L.bsort_handle_destroy.argtypes = [vp]
+        L.bsort_handle_destroy.restype = i
+        L.bsort_keys_ws.argtypes = [vp, vp, sz, i, i, i, vp, sz, vp]
+        L.bsort_keys_ws.restype = i
+        L.bsort_keys_host.argtypes = [vp, sz, i, i, vp]
+        L.bsort_keys_host.restype = i
+        L.bsort_get_error.argtypes = [vp, vp]
+        L.bsort_get_error.restype = i
+        L.bsort_handle_set_profiling.argtypes = [vp, i]
+        L.bsort_handle_set_profiling.restype = i
+        L.bsort_handle_get_profile.argtypes = [vp, ctypes.POINTER(_Profile)]
+        L.bsort_handle_get_profile.restype = i
+        L.bsort_last_launch_count.argtypes = [vp, ctypes.POINTER(i)]
+        L.bsort_last_launch_count.restype = i
+        _lib = L
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return lib().bsort_status_string(int(status)).decode()
+
+
+def _check(status: int, what: str) -> None:
+    if status != BSORT_OK:
+        raise BsortError(status, what)
+
+
+def _dtype_code(dtype) -> int:
+    name = str(dtype).replace("torch.", "")
+    if name not in _CODE:
+        raise TypeError("bsort does not sort dtype %s" % name)
+    return _CODE[name]
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _device_tensor(t):
+    if not (hasattr(t, "is_cuda") and t.is_cuda):
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("bsort sorts contiguous tensors only")
+    return t
+
+
+def bsort_keys(keys, descending: bool = False, stream=None) -> None:
+    """Sorts a contiguous CUDA tensor in place (C ABI ``bsort_keys``)."""
+    _device_tensor(keys)
+    _check(lib().bsort_keys(ctypes.c_void_p(keys.data_ptr()), keys.numel(), _dtype_code(keys.dtype),
+                            int(bool(descending)), _stream_ptr(stream)), "bsort_keys")
+
+
+sort_ = bsort_keys
+
+
+def workspace_bytes(n: int, dtype, mode: int = MODE_PINGPONG) -> int:
+    out = ctypes.c_size_t(0)
+    _check(lib().bsort_workspace_bytes(int(n), _dtype_code(dtype), int(mode), ctypes.byref(out)),
+           "bsort_workspace_bytes")
+    return int(out.value)
+
+
+class Handle:
+    """An explicit library handle (profiling state, error word, last-call stats)."""
+
+    def __init__(self):
+        h = ctypes.c_void_p()
+        _check(lib().bsort_handle_create(ctypes.byref(h)), "bsort_handle_create")
+        self._h = h
+
+    @property
+    def ptr(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().bsort_handle_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+    def set_profiling(self, enable: bool = True):
+        _check(lib().bsort_handle_set_profiling(self._h, int(bool(enable))), "bsort_handle_set_profiling")
+
+    def launch_count(self) -> int:
+        v = ctypes.c_int(0)
+        _check(lib().bsort_last_launch_count(self._h, ctypes.byref(v)), "bsort_last_launch_count")
+        return int(v.value)
+
+    def profile(self) -> dict:
+        """Per-launch records of the calls since the last read (then cleared)."""
+        p = _Profile()
+        _check(lib().bsort_handle_get_profile(self._h, ctypes.byref(p)), "bsort_handle_get_profile")
+        recs = []
+        for r in p.rec[: p.num_records]:
+            recs.append({"kind": KERNEL_KINDS[r.kind], "level": int(r.level), "call": int(r.call),
+                         "ms": float(r.ms), "keys": int(r.keys),
+                         "counted_bytes": int(r.counted_bytes)})
+        return {"calls": int(p.num_calls), "launches": int(p.num_launches), "records": recs}
+
+    def get_error(self, stream=None) -> int:
+        return int(lib().bsort_get_error(self._h, _stream_ptr(stream)))
+
+
+def bsort_keys_ws(handle: Handle, keys, workspace, descending: bool = False, stream=None,
+                  mode: int = MODE_PINGPONG) -> None:
+    """Sorts with a caller-provided device workspace (a uint8 CUDA tensor)."""
+    _device_tensor(keys)
+    _device_tensor(workspace)
+    _check(lib().bsort_keys_ws(handle.ptr, ctypes.c_void_p(keys.data_ptr()), keys.numel(),
+                               _dtype_code(keys.dtype), int(bool(descending)), int(mode),
+                               ctypes.c_void_p(workspace.data_ptr()),
+                               workspace.numel() * workspace.element_size(), _stream_ptr(stream)),
+           "bsort_keys_ws")
+
+
+def bsort_keys_host(keys, descending: bool = False, stream=None) -> None:
+    """End-to-end sort of a host array (numpy array or CPU tensor), in place."""
+    if isinstance(keys, np.ndarray):
+        if not keys.flags.c_contiguous:
+            raise ValueError("bsort sorts contiguous arrays only")
+        ptr, n, code = keys.ctypes.data, keys.size, _dtype_code(keys.dtype.name)
+    else:
+        if keys.is_cuda or not keys.is_contiguous():
+            raise TypeError("expected a contiguous CPU tensor")
+        ptr, n, code = keys.data_ptr(), keys.numel(), _dtype_code(keys.dtype)
+    _check(lib().bsort_keys_host(ctypes.c_void_p(ptr), n, code, int(bool(descending)),
+                                 _stream_ptr(stream)), "bsort_keys_host")

@@ -1,0 +1,499 @@
+// C ABI of the bsort library: argument checks, workspace planning, handles,
+// and dispatch to the counting path (1/2-byte keys) or the MSD path (4/8-byte
+// keys).  Every step of the sort runs in the library's own kernels.
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "bsort_launch.h"
+
+using namespace bsort;
+
+struct bsort_handle {
+    int device = -1;
+    // cached device buffers of the per-device default handles
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    void *stage = nullptr;  // device copy of host keys (bsort_keys_host)
+    size_t stage_bytes = 0;
+    // state of the last call
+    Ctl *last_ctl = nullptr;
+    cudaStream_t last_stream = nullptr;
+    int last_path = 0;  // 0 none, 1 counting, 2 msd
+    int last_key_bytes = 0;
+    uint64_t last_n = 0;
+    bool profiling = false;
+    bool events = false;
+    Ctl *prof_ctl = nullptr;  // device slots: work counters of each recorded call
+    int prof_path[BSORT_PROFILE_MAX_CALLS] = {0};
+    int prof_key_bytes[BSORT_PROFILE_MAX_CALLS] = {0};
+    uint64_t prof_n[BSORT_PROFILE_MAX_CALLS] = {0};
+    Recorder rec;
+    std::mutex mu;
+};
+
+namespace {
+
+struct DtypeInfo {
+    int bytes;
+    int kind;  // 0 unsigned, 1 signed, 2 float
+};
+
+bool dtype_info(bsort_dtype dt, DtypeInfo *out) {
+    static const DtypeInfo table[] = {{1, 0}, {1, 1}, {2, 0}, {2, 1}, {2, 2}, {4, 0},
+                                      {4, 1}, {4, 2}, {8, 0}, {8, 1}, {8, 2}};
+    const int i = static_cast<int>(dt);
+    if (i < 0 || i > 10) return false;
+    *out = table[i];
+    return true;
+}
+
+// Constants of encode(x) = x ^ (msb(x) ? f1 : f0) and its inverse (Sec. III:
+// the sign pass of Algs. 3/4 runs in the inverted direction; negative floats
+// run in the inverted direction on exponent and mantissa).
+Codec codec_for(const DtypeInfo &di, int descending) {
+    const int w = di.bytes * 8;
+    const uint64_t all = w == 64 ? ~0ull : ((1ull << w) - 1);
+    const uint64_t sb = 1ull << (w - 1);
+    const uint64_t dm = descending ? all : 0;
+    Codec c;
+    if (di.kind == 0) {
+        c.f0 = c.f1 = dm;
+        c.d0 = c.d1 = dm;
+    } else if (di.kind == 1) {
+        c.f0 = c.f1 = sb ^ dm;
+        c.d0 = c.d1 = sb ^ dm;
+    } else if (!descending) {
+        c.f0 = sb;   // non-negative: flip the sign bit
+        c.f1 = all;  // negative: flip every bit
+        c.d1 = sb;   // encoded msb 1 <- non-negative
+        c.d0 = all;  // encoded msb 0 <- negative
+    } else {
+        c.f0 = sb ^ all;
+        c.f1 = 0;
+        c.d1 = 0;
+        c.d0 = sb ^ all;
+    }
+    return c;
+}
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+struct MsdLayout {
+    size_t alt, ctl, buckets0, buckets1, chunks0, chunks1, hist, cand, cor, bbase, units, fills, total;
+    uint32_t max_buckets, max_chunks, max_units, max_fills;
+};
+
+MsdLayout msd_layout(size_t n, int key_bytes) {
+    const MsdShape s = msd_shape(key_bytes);
+    MsdLayout L;
+    const uint64_t per_t = n / s.unit_cap + 1;
+    L.max_buckets = static_cast<uint32_t>(n / (s.unit_cap + 1) + 2);
+    L.max_chunks = static_cast<uint32_t>(n / s.chunk + L.max_buckets + 2);
+    L.max_units = static_cast<uint32_t>((4 + 2 * static_cast<uint64_t>(s.levels)) * per_t + 16);
+    L.max_fills = static_cast<uint32_t>(n / kFillPiece + per_t + 16);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = off;
+        off = align_up(off + bytes);
+        return at;
+    };
+    L.alt = take(n * key_bytes);
+    L.ctl = take(sizeof(Ctl));
+    L.buckets0 = take(sizeof(Bucket) * L.max_buckets);
+    L.buckets1 = take(sizeof(Bucket) * L.max_buckets);
+    L.chunks0 = take(sizeof(Chunk) * L.max_chunks);
+    L.chunks1 = take(sizeof(Chunk) * L.max_chunks);
+    L.hist = take(sizeof(uint32_t) * kBins * static_cast<size_t>(L.max_chunks));
+    L.cand = take(sizeof(uint64_t) * L.max_chunks);
+    L.cor = take(sizeof(uint64_t) * L.max_chunks);
+    L.bbase = take(sizeof(uint64_t) * kBins * static_cast<size_t>(L.max_buckets));
+    L.units = take(sizeof(Unit) * L.max_units);
+    L.fills = take(sizeof(Fill) * L.max_fills);
+    L.total = off;
+    return L;
+}
+
+constexpr uint32_t kMaxGrid16 = 160;
+
+uint32_t grid16_for(size_t n) {
+    uint64_t g = (n + 65535) / 65536;
+    if (g < 1) g = 1;
+    if (g > kMaxGrid16) g = kMaxGrid16;
+    return static_cast<uint32_t>(g);
+}
+
+struct CountLayout {
+    size_t hist, starts, partial, total;
+};
+
+CountLayout count_layout(size_t n, int key_bytes) {
+    CountLayout L;
+    const size_t bins = key_bytes == 1 ? 256 : 65536;
+    size_t off = 0;
+    L.hist = off;
+    off = align_up(off + bins * 8);
+    L.starts = off;
+    off = align_up(off + (bins + 1) * 8);
+    L.partial = off;
+    if (key_bytes == 2) off = align_up(off + static_cast<size_t>(grid16_for(n)) * 65536 * 4);
+    L.total = off;
+    return L;
+}
+
+int num_sms_of(int device) {
+    static int cache[64] = {0};
+    if (device < 0 || device >= 64) return 148;
+    if (!cache[device]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || v <= 0) v = 148;
+        cache[device] = v;
+    }
+    return cache[device];
+}
+
+std::mutex g_default_mu;
+bsort_handle *g_default[64] = {nullptr};
+
+bsort_handle *default_handle(int device) {
+    if (device < 0 || device >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_default_mu);
+    if (!g_default[device]) {
+        g_default[device] = new (std::nothrow) bsort_handle();
+        if (g_default[device]) g_default[device]->device = device;
+    }
+    return g_default[device];
+}
+
+bsort_status ensure_events(bsort_handle *h) {
+    if (h->events) return BSORT_OK;
+    for (int i = 0; i < BSORT_PROFILE_MAX; ++i) {
+        if (cudaEventCreate(&h->rec.rec[i].a) != cudaSuccess || cudaEventCreate(&h->rec.rec[i].b) != cudaSuccess)
+            return BSORT_ERR_CUDA;
+    }
+    if (cudaMalloc(&h->prof_ctl, sizeof(Ctl) * BSORT_PROFILE_MAX_CALLS) != cudaSuccess) return BSORT_ERR_NO_MEMORY;
+    h->events = true;
+    return BSORT_OK;
+}
+
+bsort_status check_args(const void *keys, size_t n, bsort_dtype dt, DtypeInfo *di) {
+    if (!dtype_info(dt, di)) return BSORT_ERR_INVALID_ARG;
+    if (n <= 1) return BSORT_OK;
+    if (!keys) return BSORT_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(keys) % di->bytes) return BSORT_ERR_MISALIGNED;
+    if (di->bytes >= 4 && n >= (1ull << 32)) return BSORT_ERR_UNSUPPORTED;
+    return BSORT_OK;
+}
+
+bsort_status run_sort(bsort_handle *h, void *keys, size_t n, const DtypeInfo &di, int descending,
+                      void *workspace, size_t ws_bytes, cudaStream_t st) {
+    (void)cudaGetLastError();  // clear a stale non-sticky error
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return BSORT_ERR_CUDA;
+    const int sms = num_sms_of(dev);
+    h->rec.enabled = h->profiling;
+    h->rec.launches = 0;
+    h->rec.stream = st;
+    if (h->profiling) {
+        const bsort_status es = ensure_events(h);
+        if (es != BSORT_OK) return es;
+    }
+    h->rec.active = h->profiling && h->rec.calls < BSORT_PROFILE_MAX_CALLS;
+    const Codec codec = codec_for(di, descending);
+    char *ws = static_cast<char *>(workspace);
+    h->last_stream = st;
+    h->last_n = n;
+    h->last_key_bytes = di.bytes;
+    if (di.bytes <= 2) {
+        const CountLayout L = count_layout(n, di.bytes);
+        if (ws_bytes < L.total) return BSORT_ERR_WORKSPACE_TOO_SMALL;
+        CountWork cw;
+        cw.keys = keys;
+        cw.n = n;
+        cw.codec = codec;
+        cw.hist = reinterpret_cast<unsigned long long *>(ws + L.hist);
+        cw.starts = reinterpret_cast<unsigned long long *>(ws + L.starts);
+        cw.partial = reinterpret_cast<uint32_t *>(ws + L.partial);
+        cw.grid16 = grid16_for(n);
+        if (di.bytes == 1) launch_count8(cw, st, h->rec, sms);
+        else launch_count16(cw, st, h->rec, sms);
+        h->last_path = 1;
+        h->last_ctl = nullptr;
+    } else {
+        const MsdLayout L = msd_layout(n, di.bytes);
+        if (ws_bytes < L.total) return BSORT_ERR_WORKSPACE_TOO_SMALL;
+        const MsdShape s = msd_shape(di.bytes);
+        Work wk;
+        wk.ctl = reinterpret_cast<Ctl *>(ws + L.ctl);
+        wk.buckets[0] = reinterpret_cast<Bucket *>(ws + L.buckets0);
+        wk.buckets[1] = reinterpret_cast<Bucket *>(ws + L.buckets1);
+        wk.chunks[0] = reinterpret_cast<Chunk *>(ws + L.chunks0);
+        wk.chunks[1] = reinterpret_cast<Chunk *>(ws + L.chunks1);
+        wk.hist = reinterpret_cast<uint32_t *>(ws + L.hist);
+        wk.chunk_and = reinterpret_cast<uint64_t *>(ws + L.cand);
+        wk.chunk_or = reinterpret_cast<uint64_t *>(ws + L.cor);
+        wk.bucket_base = reinterpret_cast<uint64_t *>(ws + L.bbase);
+        wk.units = reinterpret_cast<Unit *>(ws + L.units);
+        wk.fills = reinterpret_cast<Fill *>(ws + L.fills);
+        wk.keys = keys;
+        wk.alt = ws + L.alt;
+        wk.n = n;
+        wk.codec = codec;
+        wk.max_buckets = L.max_buckets;
+        wk.max_chunks = L.max_chunks;
+        wk.max_units = L.max_units;
+        wk.max_fills = L.max_fills;
+        wk.chunk_keys = s.chunk;
+        wk.unit_cap = s.unit_cap;
+        wk.merge_cap = s.merge_cap;
+        wk.w = di.bytes * 8;
+        if (di.bytes == 4) launch_msd<uint32_t>(wk, st, h->rec, sms);
+        else launch_msd<uint64_t>(wk, st, h->rec, sms);
+        h->last_path = 2;
+        h->last_ctl = wk.ctl;
+    }
+    if (h->rec.active) {
+        const int c = h->rec.calls;
+        h->prof_path[c] = h->last_path;
+        h->prof_key_bytes[c] = di.bytes;
+        h->prof_n[c] = n;
+        if (h->last_ctl)
+            cudaMemcpyAsync(h->prof_ctl + c, h->last_ctl, sizeof(Ctl), cudaMemcpyDeviceToDevice, st);
+        ++h->rec.calls;
+    }
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? BSORT_OK : BSORT_ERR_CUDA;
+}
+
+bsort_status grow(void **buf, size_t *have, size_t need) {
+    if (*have >= need && *buf) return BSORT_OK;
+    if (*buf) {
+        cudaFree(*buf);  // synchronises the device
+        *buf = nullptr;
+        *have = 0;
+    }
+    if (cudaMalloc(buf, need ? need : 256) != cudaSuccess) {
+        (void)cudaGetLastError();
+        *buf = nullptr;
+        return BSORT_ERR_NO_MEMORY;
+    }
+    *have = need ? need : 256;
+    return BSORT_OK;
+}
+
+size_t workspace_for(size_t n, const DtypeInfo &di) {
+    return di.bytes <= 2 ? count_layout(n, di.bytes).total : msd_layout(n, di.bytes).total;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *bsort_status_string(bsort_status status) {
+    switch (status) {
+    case BSORT_OK: return "BSORT_OK";
+    case BSORT_ERR_INVALID_ARG: return "BSORT_ERR_INVALID_ARG: invalid argument";
+    case BSORT_ERR_UNSUPPORTED: return "BSORT_ERR_UNSUPPORTED: request not supported by this build";
+    case BSORT_ERR_MISALIGNED: return "BSORT_ERR_MISALIGNED: pointer not aligned to the key size";
+    case BSORT_ERR_NO_MEMORY: return "BSORT_ERR_NO_MEMORY: device allocation failed";
+    case BSORT_ERR_WORKSPACE_TOO_SMALL: return "BSORT_ERR_WORKSPACE_TOO_SMALL: workspace smaller than required";
+    case BSORT_ERR_CUDA: return "BSORT_ERR_CUDA: a CUDA runtime call failed";
+    case BSORT_ERR_TIMEOUT: return "BSORT_ERR_TIMEOUT: a bounded device wait expired";
+    case BSORT_ERR_CAPACITY: return "BSORT_ERR_CAPACITY: a device work list outgrew its plan";
+    case BSORT_ERR_INTERNAL: return "BSORT_ERR_INTERNAL: a device-side bounds check refused a store";
+    }
+    return "BSORT_ERR_UNKNOWN";
+}
+
+bsort_status bsort_workspace_bytes(size_t n, bsort_dtype dt, bsort_mode mode, size_t *bytes) {
+    DtypeInfo di;
+    if (!bytes || !dtype_info(dt, &di)) return BSORT_ERR_INVALID_ARG;
+    if (mode != BSORT_MODE_PINGPONG && mode != BSORT_MODE_INPLACE) return BSORT_ERR_INVALID_ARG;
+    if (mode == BSORT_MODE_INPLACE) return BSORT_ERR_UNSUPPORTED;
+    *bytes = workspace_for(n, di);
+    return BSORT_OK;
+}
+
+bsort_status bsort_handle_create(bsort_handle **handle) {
+    if (!handle) return BSORT_ERR_INVALID_ARG;
+    *handle = new (std::nothrow) bsort_handle();
+    if (!*handle) return BSORT_ERR_NO_MEMORY;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    (*handle)->device = dev;
+    return BSORT_OK;
+}
+
+bsort_status bsort_handle_destroy(bsort_handle *handle) {
+    if (!handle) return BSORT_ERR_INVALID_ARG;
+    for (int d = 0; d < 64; ++d)
+        if (g_default[d] == handle) return BSORT_ERR_INVALID_ARG;  // default handles live until exit
+    if (handle->events) {
+        for (int i = 0; i < BSORT_PROFILE_MAX; ++i) {
+            cudaEventDestroy(handle->rec.rec[i].a);
+            cudaEventDestroy(handle->rec.rec[i].b);
+        }
+        cudaFree(handle->prof_ctl);
+    }
+    delete handle;
+    return BSORT_OK;
+}
+
+bsort_status bsort_keys_ws(bsort_handle *handle, void *keys, size_t n, bsort_dtype dt, int descending,
+                           bsort_mode mode, void *workspace, size_t ws_bytes, void *stream) {
+    if (!handle) return BSORT_ERR_INVALID_ARG;
+    DtypeInfo di;
+    const bsort_status st = check_args(keys, n, dt, &di);
+    if (st != BSORT_OK) return st;
+    if (mode != BSORT_MODE_PINGPONG && mode != BSORT_MODE_INPLACE) return BSORT_ERR_INVALID_ARG;
+    if (mode == BSORT_MODE_INPLACE) return BSORT_ERR_UNSUPPORTED;
+    if (n <= 1) return BSORT_OK;
+    if (!workspace) return BSORT_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(workspace) % kAlign) return BSORT_ERR_MISALIGNED;
+    std::lock_guard<std::mutex> lk(handle->mu);
+    return run_sort(handle, keys, n, di, descending, workspace, ws_bytes, static_cast<cudaStream_t>(stream));
+}
+
+bsort_status bsort_keys(void *keys, size_t n, bsort_dtype dt, int descending, void *stream) {
+    DtypeInfo di;
+    const bsort_status st = check_args(keys, n, dt, &di);
+    if (st != BSORT_OK) return st;
+    if (n <= 1) return BSORT_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return BSORT_ERR_CUDA;
+    bsort_handle *h = default_handle(dev);
+    if (!h) return BSORT_ERR_NO_MEMORY;
+    std::lock_guard<std::mutex> lk(h->mu);
+    const bsort_status gs = grow(&h->ws, &h->ws_bytes, workspace_for(n, di));
+    if (gs != BSORT_OK) return gs;
+    return run_sort(h, keys, n, di, descending, h->ws, h->ws_bytes, static_cast<cudaStream_t>(stream));
+}
+
+bsort_status bsort_keys_host(void *host_keys, size_t n, bsort_dtype dt, int descending, void *stream) {
+    DtypeInfo di;
+    const bsort_status st = check_args(host_keys, n, dt, &di);
+    if (st != BSORT_OK) return st;
+    if (n <= 1) return BSORT_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return BSORT_ERR_CUDA;
+    bsort_handle *h = default_handle(dev);
+    if (!h) return BSORT_ERR_NO_MEMORY;
+    std::lock_guard<std::mutex> lk(h->mu);
+    const size_t bytes = n * di.bytes;
+    bsort_status gs = grow(&h->stage, &h->stage_bytes, bytes);
+    if (gs != BSORT_OK) return gs;
+    gs = grow(&h->ws, &h->ws_bytes, workspace_for(n, di));
+    if (gs != BSORT_OK) return gs;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(h->stage, host_keys, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return BSORT_ERR_CUDA;
+    const bsort_status rs = run_sort(h, h->stage, n, di, descending, h->ws, h->ws_bytes, s);
+    if (rs != BSORT_OK) return rs;
+    if (cudaMemcpyAsync(host_keys, h->stage, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return BSORT_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return BSORT_ERR_CUDA;
+    if (h->last_ctl) {
+        uint32_t err = 0;
+        if (cudaMemcpy(&err, &h->last_ctl->error, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return BSORT_ERR_CUDA;
+        if (err & kErrCapacity) return BSORT_ERR_CAPACITY;
+        if (err & kErrTimeout) return BSORT_ERR_TIMEOUT;
+        if (err & kErrBounds) return BSORT_ERR_INTERNAL;
+    }
+    return BSORT_OK;
+}
+
+bsort_status bsort_get_error(bsort_handle *handle, void *stream) {
+    if (!handle) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return BSORT_ERR_CUDA;
+        handle = default_handle(dev);
+        if (!handle) return BSORT_ERR_NO_MEMORY;
+    }
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return BSORT_ERR_CUDA;
+    if (!handle->last_ctl) return BSORT_OK;
+    uint32_t err = 0;
+    if (cudaMemcpy(&err, &handle->last_ctl->error, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return BSORT_ERR_CUDA;
+    if (err) {
+        const uint32_t zero = 0;
+        cudaMemcpy(&handle->last_ctl->error, &zero, 4, cudaMemcpyHostToDevice);
+    }
+    if (err & kErrCapacity) return BSORT_ERR_CAPACITY;
+    if (err & kErrTimeout) return BSORT_ERR_TIMEOUT;
+    if (err & kErrBounds) return BSORT_ERR_INTERNAL;
+    return BSORT_OK;
+}
+
+bsort_status bsort_handle_set_profiling(bsort_handle *handle, int enable) {
+    if (!handle) return BSORT_ERR_INVALID_ARG;
+    handle->profiling = enable != 0;
+    return BSORT_OK;
+}
+
+bsort_status bsort_last_launch_count(bsort_handle *handle, int *launches) {
+    if (!handle || !launches) return BSORT_ERR_INVALID_ARG;
+    *launches = handle->rec.launches;
+    return BSORT_OK;
+}
+
+bsort_status bsort_handle_get_profile(bsort_handle *handle, bsort_profile *out) {
+    if (!handle || !out) return BSORT_ERR_INVALID_ARG;
+    std::memset(out, 0, sizeof(*out));
+    if (cudaDeviceSynchronize() != cudaSuccess) return BSORT_ERR_CUDA;
+    const int ncalls = handle->rec.calls;
+    static Ctl ctls[BSORT_PROFILE_MAX_CALLS];
+    if (ncalls > 0 && handle->prof_ctl &&
+        cudaMemcpy(ctls, handle->prof_ctl, sizeof(Ctl) * ncalls, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return BSORT_ERR_CUDA;
+    out->num_calls = ncalls;
+    out->num_launches = handle->rec.held_launches;
+    const int nrec = handle->rec.count;
+    for (int i = 0; i < nrec; ++i) {
+        bsort_profile_record &r = out->rec[i];
+        const Recorder::Rec &src = handle->rec.rec[i];
+        r.kind = src.kind;
+        r.level = src.level;
+        r.call = src.call;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, src.a, src.b) != cudaSuccess) ms = -1.f;
+        r.ms = ms;
+        const Ctl &ctl = ctls[src.call];
+        const uint64_t b = static_cast<uint64_t>(handle->prof_key_bytes[src.call]);
+        const uint64_t n = handle->prof_n[src.call];
+        uint64_t keys = 0, bytes = 0;
+        switch (r.kind) {
+        case BSORT_K_HIST:
+            keys = r.level >= 0 && r.level < kMaxLevels ? ctl.hist_keys[r.level] : 0;
+            bytes = keys * b;
+            break;
+        case BSORT_K_SCATTER:
+            keys = r.level >= 0 && r.level < kMaxLevels ? ctl.scatter_keys[r.level] : 0;
+            bytes = 2 * keys * b;
+            break;
+        case BSORT_K_FINISH:
+            keys = ctl.finish_keys;
+            bytes = 2 * keys * b;
+            break;
+        case BSORT_K_FILL:
+            keys = ctl.fill_keys;
+            bytes = keys * b;
+            break;
+        case BSORT_K_COUNT_HIST:
+        case BSORT_K_COUNT_FILL:
+            keys = n;
+            bytes = keys * b;
+            break;
+        default:
+            break;
+        }
+        r.keys = keys;
+        r.counted_bytes = bytes;
+    }
+    out->num_records = nrec;
+    handle->rec.count = 0;
+    handle->rec.calls = 0;
+    handle->rec.held_launches = 0;
+    (void)cudaGetLastError();
+    return BSORT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,132 @@
+// Shared device-side definitions of the bsort CUDA library (sm_103a).
+//
+// The sort works on "encoded" keys: an order-preserving bijection maps every
+// dtype onto unsigned words whose ascending order is the requested order
+// (Sec. III of the paper: the sign pass of Algs. 3/4 runs in the inverted
+// direction, and the negative float half in the inverted direction on its
+// exponent and mantissa bits).  Encoding costs a select and a xor:
+//     encode(x) = x ^ (msb(x) ? F1 : F0),   decode(k) = k ^ (msb(k) ? D1 : D0)
+// with the constants of codec_for().  After encoding, the r-bit MSD digit
+// passes are r consecutive binary partitions of Alg. 1 on masks
+// 1 << (s - i), fused: binary splits refine lexicographically (Thm. 3's
+// induction), so one stable r-bit split equals r successive bit splits.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bsort {
+
+constexpr int kRadixBits = 8;
+constexpr int kBins = 1 << kRadixBits;
+constexpr int kMaxLevels = 8;  // ceil(64 / kRadixBits)
+
+// device error word bits
+constexpr uint32_t kErrCapacity = 1u;
+constexpr uint32_t kErrTimeout = 2u;
+constexpr uint32_t kErrBounds = 4u;  // a device-side bounds check refused a store
+
+struct Codec {
+    uint64_t f0, f1;  // encode: x ^ (msb ? f1 : f0)
+    uint64_t d0, d1;  // decode: k ^ (msb ? d1 : d0)
+};
+
+// One MSD bucket: keys [start, start+len) of buffer `src` agree on every bit
+// at or above position h; bits [0, h) are not partitioned yet.
+struct Bucket {
+    uint64_t start;
+    uint64_t len;
+    uint32_t first_chunk;
+    uint32_t num_chunks;
+    int32_t h;
+    uint8_t src;      // 0: caller's keys buffer, 1: alternate buffer
+    uint8_t raw;      // keys in src still in the caller's encoding
+    uint8_t scatter;  // classify: this bucket is scattered at this level
+    uint8_t pad;
+};
+
+// A contiguous piece of one bucket, processed by one CTA in the histogram and
+// scatter kernels (same decomposition in both, so per-chunk offsets match).
+struct Chunk {
+    uint64_t start;
+    uint32_t len;
+    uint32_t bucket;
+};
+
+// A run of keys (one or several adjacent small buckets) sorted entirely in
+// shared memory and written, decoded, to its final place.
+struct Unit {
+    uint64_t start;
+    uint32_t len;
+    uint8_t src;
+    uint8_t raw;
+    uint8_t pad[2];
+};
+
+// A run of identical keys written without reading (value is encoded).
+struct Fill {
+    uint64_t start;
+    uint64_t value;
+    uint32_t len;
+    uint32_t pad;
+};
+
+struct Ctl {
+    uint32_t n_buckets[2];
+    uint32_t n_chunks[2];
+    uint32_t n_units;
+    uint32_t n_fills;
+    uint32_t error;
+    uint32_t pad;
+    unsigned long long hist_keys[kMaxLevels];     // keys read by the histogram of a level
+    unsigned long long scatter_keys[kMaxLevels];  // keys moved by the scatter of a level
+    unsigned long long finish_keys;
+    unsigned long long fill_keys;
+    unsigned long long raw_reads;                 // keys read while still raw (diagnostic)
+};
+
+// Everything a launch needs, passed by value.
+struct Work {
+    Ctl *ctl;
+    Bucket *buckets[2];
+    Chunk *chunks[2];
+    uint32_t *hist;         // [kBins][max_chunks], digit-major; excl. prefix after the scan
+    uint64_t *chunk_and;    // [max_chunks]
+    uint64_t *chunk_or;     // [max_chunks]
+    uint64_t *bucket_base;  // [max_buckets][kBins]: totals, then absolute digit bases
+    Unit *units;
+    Fill *fills;
+    void *keys;
+    void *alt;
+    uint64_t n;
+    Codec codec;
+    uint32_t max_buckets, max_chunks, max_units, max_fills;
+    uint32_t chunk_keys;  // keys per chunk (multiple of the scatter tile)
+    uint32_t unit_cap;    // largest run the shared-memory finish sorts
+    uint32_t merge_cap;   // adjacent small buckets merge while their sum stays <= this
+    int32_t w;            // key bits
+};
+
+constexpr uint32_t kFillPiece = 1u << 16;  // keys per fill work item
+
+template <typename K>
+__device__ __forceinline__ K encode_key(K x, const Codec &c) {
+    constexpr int W = sizeof(K) * 8;
+    return x ^ static_cast<K>((x >> (W - 1)) ? c.f1 : c.f0);
+}
+
+template <typename K>
+__device__ __forceinline__ K decode_key(K k, const Codec &c) {
+    constexpr int W = sizeof(K) * 8;
+    return k ^ static_cast<K>((k >> (W - 1)) ? c.d1 : c.d0);
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ void set_error(Ctl *ctl, uint32_t bits) { atomicOr(&ctl->error, bits); }
+
+}  // namespace bsort

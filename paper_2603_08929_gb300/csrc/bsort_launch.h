@@ -1,0 +1,76 @@
+// Host-side launch interface between the C ABI (api.cu) and the kernel files.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "bsort.h"
+#include "bsort_device.cuh"
+
+namespace bsort {
+
+// Records a CUDA event pair around each launch group when profiling is on
+// (accumulating over calls until read), and counts launches always.
+struct Recorder {
+    struct Rec {
+        int kind;
+        int level;
+        int call;
+        cudaEvent_t a, b;
+    };
+    bool enabled = false;
+    bool active = false;  // this call is being recorded
+    int count = 0;        // records held
+    int calls = 0;        // calls held
+    int launches = 0;     // launches of the last call
+    int held_launches = 0;
+    cudaStream_t stream = nullptr;
+    Rec rec[BSORT_PROFILE_MAX];
+
+    void begin(int kind, int level) {
+        ++launches;
+        ++held_launches;
+        if (!active || count >= BSORT_PROFILE_MAX) return;
+        rec[count].kind = kind;
+        rec[count].level = level;
+        rec[count].call = calls;
+        cudaEventRecord(rec[count].a, stream);
+    }
+    void end() {
+        if (!active || count >= BSORT_PROFILE_MAX) return;
+        cudaEventRecord(rec[count].b, stream);
+        ++count;
+    }
+};
+
+// Per-key-width tuning of the MSD path.
+struct MsdShape {
+    uint32_t tile;       // keys per scatter tile (threads x items)
+    uint32_t chunk;      // keys per chunk (multiple of tile)
+    uint32_t unit_cap;   // largest bucket finished in shared memory
+    uint32_t merge_cap;  // adjacent small buckets merge up to this many keys
+    int levels;          // host-side level launches (ceil(w / radix bits))
+};
+
+MsdShape msd_shape(int key_bytes);
+
+// Launches the whole MSD pipeline for 4- or 8-byte keys.
+template <typename K>
+void launch_msd(const Work &wk, cudaStream_t st, Recorder &rec, int num_sms);
+
+// Counting sort of 1- or 2-byte keys: histogram of all key bits, bin starts,
+// and a write-only fill of the output.  Scratch comes from `ws`.
+struct CountWork {
+    void *keys;
+    uint64_t n;
+    Codec codec;
+    unsigned long long *hist;     // [bins] global counts
+    unsigned long long *starts;   // [bins + 1] exclusive starts
+    uint32_t *partial;            // 16-bit: [grid][65536] per-CTA counts
+    uint32_t grid16;              // CTAs of the 16-bit histogram
+};
+
+void launch_count8(const CountWork &cw, cudaStream_t st, Recorder &rec, int num_sms);
+void launch_count16(const CountWork &cw, cudaStream_t st, Recorder &rec, int num_sms);
+
+}  // namespace bsort

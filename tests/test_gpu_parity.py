@@ -1,0 +1,123 @@
+"""GPU sorts through the C ABI against the oracle, element by element."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from gpu_util import assert_bit_exact, gpu_sort, to_device
+
+pytestmark = pytest.mark.gpu
+
+INT_DISTS = ["uniform", "zipf", "distinct8", "sorted", "reverse", "normal"]
+FLOAT_DISTS = INT_DISTS + ["float_edge"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    from paper_2603_08929_gb300 import build as b
+    b.build()
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+
+
+def dists_of(dtype):
+    return FLOAT_DISTS if dtype.startswith("float") else INT_DISTS
+
+
+def check(dtype, dist, n, desc, seed=0):
+    x = W.make(dist, dtype, n, seed=seed)
+    want = O.bsort(x, descending=desc)
+    got = gpu_sort(x, desc)
+    assert_bit_exact(got, want, "%s %s n=%d desc=%s" % (dtype, dist, n, desc))
+
+
+def test_config1_int32_65536_seed0():
+    """65,536 int32 keys uniform over the full range from seed 0, ascending."""
+    check("int32", "uniform", 65536, False, seed=0)
+
+
+@pytest.mark.parametrize("desc", [False, True], ids=["asc", "desc"])
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 31, 32, 33, 1000, 4095, 4096, 4097, 8191, 8192, 8193,
+                               16385, 65536, 100003])
+@pytest.mark.parametrize("dtype", W.DTYPES)
+def test_sizes(dtype, n, desc):
+    check(dtype, "uniform", n, desc)
+
+
+@pytest.mark.parametrize("desc", [False, True], ids=["asc", "desc"])
+@pytest.mark.parametrize("dtype", W.DTYPES)
+def test_distributions(dtype, desc):
+    for dist in dists_of(dtype):
+        check(dtype, dist, 300001, desc, seed=1)
+
+
+@pytest.mark.parametrize("dtype", W.DTYPES)
+def test_two_msd_levels(dtype):
+    # 2^22 + 7 keys: buckets after the first 8-bit digit still exceed the
+    # shared-memory finish, so a second level runs
+    for dist in ("uniform", "zipf", "distinct8"):
+        check(dtype, dist, (1 << 22) + 7, dist == "zipf", seed=2)
+
+
+@pytest.mark.parametrize("dtype", ["float16", "float32", "float64"])
+def test_special_values(dtype):
+    from oracle_pins import _special_float_sequence
+    seq = np.array(_special_float_sequence(dtype), dtype=np.uint64)
+    w = np.dtype(dtype).itemsize * 8
+    ut = {16: np.uint16, 32: np.uint32, 64: np.uint64}[w]
+    rng = np.random.default_rng(0)
+    x = np.tile(seq, 500)
+    x = x[rng.permutation(x.size)].astype(ut).view(dtype)
+    for desc in (False, True):
+        got = gpu_sort(x, desc)
+        assert_bit_exact(got, O.bsort(x, descending=desc), "special values desc=%s" % desc)
+
+
+def test_desc_is_reverse_of_asc():
+    x = W.make("float_edge", "float32", 200000, seed=5)
+    a = gpu_sort(x, False)
+    d = gpu_sort(x, True)
+    assert_bit_exact(d, a[::-1].copy(), "desc vs reversed asc")
+
+
+def test_deterministic_repeat():
+    x = W.make("zipf", "int64", 500000, seed=6)
+    assert_bit_exact(gpu_sort(x), gpu_sort(x), "repeat")
+
+
+def test_explicit_workspace_and_stream():
+    import torch
+    import paper_2603_08929_gb300 as bs
+    x = W.make("uniform", "uint32", 1 << 20, seed=7)
+    t = to_device(x)
+    ws = torch.empty(bs.workspace_bytes(x.size, "uint32"), dtype=torch.uint8, device="cuda")
+    h = bs.Handle()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        bs.bsort_keys_ws(h, t, ws, descending=False, stream=s)
+    s.synchronize()
+    assert h.get_error(s) == 0
+    assert_bit_exact(t.cpu().numpy(), O.bsort(x), "bsort_keys_ws")
+    # a workspace one byte short is rejected before any launch
+    with pytest.raises(bs.BsortError):
+        bs.bsort_keys_ws(h, t, ws[:-257], stream=s)
+
+
+def test_host_entry_point():
+    import paper_2603_08929_gb300 as bs
+    for dtype, dist in (("float64", "float_edge"), ("int16", "normal"), ("uint32", "sorted")):
+        x = W.make(dist, dtype, 123457, seed=8)
+        y = x.copy()
+        bs.bsort_keys_host(y)
+        assert_bit_exact(y, O.bsort(x), "bsort_keys_host %s" % dtype)
+
+
+def test_misaligned_and_offset_views():
+    import paper_2603_08929_gb300 as bs
+    x = W.make("uniform", "int32", 50001, seed=9)
+    t = to_device(np.concatenate([np.zeros(1, np.int32), x]))
+    v = t[1:]  # 4-byte aligned, not 16-byte aligned
+    bs.bsort_keys(v)
+    assert_bit_exact(v.cpu().numpy(), O.bsort(x), "offset view")
+    assert int(t[0]) == 0
