@@ -120,6 +120,33 @@ bsort_status bsort_keys_ws(bsort_handle *handle, void *keys, size_t n, bsort_dty
 bsort_status bsort_keys_host(void *host_keys, size_t n, bsort_dtype dt, int descending, void *stream);
 
 /*
+ * The paper has no counterpart of this entry point.  bsort_keys() for callers
+ * that may not allocate device memory while they run -- code under CUDA
+ * graph capture (allocation is not capturable, and cudaMalloc / cudaFree
+ * synchronise the device), programs whose device memory belongs to their own
+ * pool allocator, plugins whose host engine forbids raw allocations.  The
+ * scratch memory is a static device array of BSORT_NOALLOC_SCRATCH_BYTES
+ * inside the library; the call allocates and frees nothing.
+ *   - Sizes: n is accepted while bsort_workspace_bytes(n, dt, PINGPONG)
+ *     fits the array (64 MiB): up to 14,975,296 4-byte keys or 7,461,984
+ *     8-byte keys; 1- and 2-byte keys need a fixed amount, so any n.  A larger
+ *     n returns BSORT_ERR_WORKSPACE_TOO_SMALL before any launch.
+ *   - Set-up: the first call on each device looks up the array's device
+ *     address (cudaGetSymbolAddress) and loads the module that holds it; make
+ *     that first call before any stream capture.  The array then stays
+ *     resident on that device until the process exits.
+ *   - Sharing: all calls on a device share the one array and leave their
+ *     scratch in it.  The sort initialises everything it reads, so stale
+ *     contents do no harm, but calls whose device work overlaps in time
+ *     (different streams with no ordering between them) race on the array
+ *     and give wrong results: order them on one stream or with events.
+ *   - The device error word of these calls lives in the shared array and is
+ *     not reported; the call returns launch-time errors only.
+ */
+#define BSORT_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+bsort_status bsort_keys_noalloc(void *keys, size_t n, bsort_dtype dt, int descending, void *stream);
+
+/*
  * Waits for `stream`, then returns (and clears) the device error word of the
  * last call made with `handle` (NULL = the default handle of the current
  * device): BSORT_OK, BSORT_ERR_CAPACITY, BSORT_ERR_TIMEOUT or

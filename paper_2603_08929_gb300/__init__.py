@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 __all__ = [
-    "DTYPES", "BsortError", "lib", "bsort_keys", "bsort_keys_ws", "bsort_keys_host",
+    "DTYPES", "BsortError", "lib", "bsort_keys", "bsort_keys_ws", "bsort_keys_host", "bsort_keys_noalloc",
     "workspace_bytes", "Handle", "sort_", "status_string",
 ]
 
@@ -86,6 +86,8 @@ def lib():
         L.bsort_handle_get_profile.restype = i
         L.bsort_last_launch_count.argtypes = [vp, ctypes.POINTER(i)]
         L.bsort_last_launch_count.restype = i
+        L.bsort_keys_noalloc.argtypes = [vp, sz, i, i, vp]
+        L.bsort_keys_noalloc.restype = i
         _lib = L
     return _lib
 
@@ -196,6 +198,16 @@ def bsort_keys_ws(handle: Handle, keys, workspace, descending: bool = False, str
                                ctypes.c_void_p(workspace.data_ptr()),
                                workspace.numel() * workspace.element_size(), _stream_ptr(stream)),
            "bsort_keys_ws")
+
+
+def bsort_keys_noalloc(keys, descending: bool = False, stream=None) -> None:
+    """Sorts in place with no device allocation: the scratch is a fixed array
+    inside the library (C ABI ``bsort_keys_noalloc``; see include/bsort.h for
+    the size limit and the rule that overlapping calls must not run at once)."""
+    _device_tensor(keys)
+    _check(lib().bsort_keys_noalloc(ctypes.c_void_p(keys.data_ptr()), keys.numel(),
+                                    _dtype_code(keys.dtype), int(bool(descending)), _stream_ptr(stream)),
+           "bsort_keys_noalloc")
 
 
 def bsort_keys_host(keys, descending: bool = False, stream=None) -> None:

@@ -6,32 +6,10 @@
 #include <mutex>
 #include <new>
 
+#include "bsort_handle.h"
 #include "bsort_launch.h"
 
 using namespace bsort;
-
-struct bsort_handle {
-    int device = -1;
-    // cached device buffers of the per-device default handles
-    void *ws = nullptr;
-    size_t ws_bytes = 0;
-    void *stage = nullptr;  // device copy of host keys (bsort_keys_host)
-    size_t stage_bytes = 0;
-    // state of the last call
-    Ctl *last_ctl = nullptr;
-    cudaStream_t last_stream = nullptr;
-    int last_path = 0;  // 0 none, 1 counting, 2 msd
-    int last_key_bytes = 0;
-    uint64_t last_n = 0;
-    bool profiling = false;
-    bool events = false;
-    Ctl *prof_ctl = nullptr;  // device slots: work counters of each recorded call
-    int prof_path[BSORT_PROFILE_MAX_CALLS] = {0};
-    int prof_key_bytes[BSORT_PROFILE_MAX_CALLS] = {0};
-    uint64_t prof_n[BSORT_PROFILE_MAX_CALLS] = {0};
-    Recorder rec;
-    std::mutex mu;
-};
 
 namespace {
 
