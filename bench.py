@@ -273,7 +273,8 @@ def main():
     # correctness of the last timed step (cheap properties at full size)
     out = bufs[-1]
     ok_sorted = bool(torch.all(out[:-1] <= out[1:]).item()) if (
-        args.dist == "uniform" and args.dtype.startswith(("int", "uint")) and not args.desc) else None
+        args.dist == "uniform" and args.dtype in ("int8", "int16", "int32", "int64", "uint8")
+        and not args.desc) else None
 
     peak, peak_src = load_peaks()
     dom_kind = max(per_kind.items(), key=lambda kv: kv[1]["ms"])[0]

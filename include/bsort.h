@@ -128,7 +128,7 @@ bsort_status bsort_keys_host(void *host_keys, size_t n, bsort_dtype dt, int desc
  * scratch memory is a static device array of BSORT_NOALLOC_SCRATCH_BYTES
  * inside the library; the call allocates and frees nothing.
  *   - Sizes: n is accepted while bsort_workspace_bytes(n, dt, PINGPONG)
- *     fits the array (64 MiB): up to 14,975,296 4-byte keys or 7,461,984
+ *     fits the array (64 MiB): about 14.5 million 4-byte keys or 7.2 million
  *     8-byte keys; 1- and 2-byte keys need a fixed amount, so any n.  A larger
  *     n returns BSORT_ERR_WORKSPACE_TOO_SMALL before any launch.
  *   - Set-up: the first call on each device looks up the array's device

@@ -69,7 +69,8 @@ MsdLayout msd_layout(size_t n, int key_bytes) {
     MsdLayout L;
     const uint64_t per_t = n / s.unit_cap + 1;
     L.max_buckets = static_cast<uint32_t>(n / (s.unit_cap + 1) + 2);
-    L.max_chunks = static_cast<uint32_t>(n / s.chunk + L.max_buckets + 2);
+    // a bucket of len keys spans ceil((len + misalignment) / chunk) <= 1 + (len + 16) / chunk chunks
+    L.max_chunks = static_cast<uint32_t>(L.max_buckets + (n + 16ull * L.max_buckets) / s.chunk + 2);
     L.max_units = static_cast<uint32_t>((4 + 2 * static_cast<uint64_t>(s.levels)) * per_t + 16);
     L.max_fills = static_cast<uint32_t>(n / kFillPiece + per_t + 16);
     size_t off = 0;
@@ -87,7 +88,7 @@ MsdLayout msd_layout(size_t n, int key_bytes) {
     L.hist = take(sizeof(uint32_t) * kBins * static_cast<size_t>(L.max_chunks));
     L.cand = take(sizeof(uint64_t) * L.max_chunks);
     L.cor = take(sizeof(uint64_t) * L.max_chunks);
-    L.bbase = take(sizeof(uint64_t) * kBins * static_cast<size_t>(L.max_buckets));
+    L.bbase = take(sizeof(uint32_t) * kBins * static_cast<size_t>(L.max_buckets));
     L.units = take(sizeof(Unit) * L.max_units);
     L.fills = take(sizeof(Fill) * L.max_fills);
     L.total = off;
@@ -212,7 +213,7 @@ bsort_status run_sort(bsort_handle *h, void *keys, size_t n, const DtypeInfo &di
         wk.hist = reinterpret_cast<uint32_t *>(ws + L.hist);
         wk.chunk_and = reinterpret_cast<uint64_t *>(ws + L.cand);
         wk.chunk_or = reinterpret_cast<uint64_t *>(ws + L.cor);
-        wk.bucket_base = reinterpret_cast<uint64_t *>(ws + L.bbase);
+        wk.bucket_base = reinterpret_cast<uint32_t *>(ws + L.bbase);
         wk.units = reinterpret_cast<Unit *>(ws + L.units);
         wk.fills = reinterpret_cast<Fill *>(ws + L.fills);
         wk.keys = keys;
@@ -227,6 +228,7 @@ bsort_status run_sort(bsort_handle *h, void *keys, size_t n, const DtypeInfo &di
         wk.unit_cap = s.unit_cap;
         wk.merge_cap = s.merge_cap;
         wk.w = di.bytes * 8;
+        wk.keys_vec_ok = (reinterpret_cast<uintptr_t>(keys) & 15) == 0;
         if (di.bytes == 4) launch_msd<uint32_t>(wk, st, h->rec, sms);
         else launch_msd<uint64_t>(wk, st, h->rec, sms);
         h->last_path = 2;

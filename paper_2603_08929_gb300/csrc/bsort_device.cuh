@@ -93,7 +93,7 @@ struct Work {
     uint32_t *hist;         // [kBins][max_chunks], digit-major; excl. prefix after the scan
     uint64_t *chunk_and;    // [max_chunks]
     uint64_t *chunk_or;     // [max_chunks]
-    uint64_t *bucket_base;  // [max_buckets][kBins]: totals, then absolute digit bases
+    uint32_t *bucket_base;  // [max_buckets][kBins]: digit totals, then digit bases relative to the bucket start
     Unit *units;
     Fill *fills;
     void *keys;
@@ -105,6 +105,7 @@ struct Work {
     uint32_t unit_cap;    // largest run the shared-memory finish sorts
     uint32_t merge_cap;   // adjacent small buckets merge while their sum stays <= this
     int32_t w;            // key bits
+    bool keys_vec_ok;     // caller's buffer is 16-byte aligned (vector loads)
 };
 
 constexpr uint32_t kFillPiece = 1u << 16;  // keys per fill work item

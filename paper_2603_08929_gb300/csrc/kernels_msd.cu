@@ -137,80 +137,249 @@ __device__ __forceinline__ void block_and_or(unsigned long long &a, unsigned lon
     __syncthreads();
 }
 
-// Stable rank of a tile held in registers, warp-striped: item j of lane l in
-// warp w has tile index w*32*ITEMS + j*32 + l, and items with index >= n_valid
-// take no part.  Each warp counts its digits in its own shared-memory row
-// (match-any groups equal digits inside a warp step, so skewed tiles cost no
-// more than uniform ones); the rows are then scanned per digit across warps
-// and across digits.  The valid keys land in `out` in digit order, equal
-// digits in tile order; dstart/dcount describe the digit runs.
+// Shared-memory buffers of one tile ranking, carved from dynamic shared
+// memory.  Unstable ranking uses one CTA-wide counter row; stable ranking
+// uses per-digit, per-warp counters laid out digit-major with one pad word
+// per digit (stride WARPS + 1: the banks of a warp's counters spread, and the
+// thread that scans digit d reads its WARPS counters at consecutive words)
+// and two sets of per-warp peer masks.
+template <int THREADS>
+struct RankSmem {
+    static constexpr int WARPS = THREADS / 32;
+    static constexpr int STRIDE = WARPS + 1;
+    uint32_t *cnt;     // [kBins] (unstable)
+    uint32_t *wc;      // [kBins][STRIDE] (stable): counts, then absolute tile offsets
+    uint32_t *wm;      // [2][WARPS][kBins] (stable): peer masks, zero between items
+    uint32_t *dstart;  // [kBins]
+    uint32_t *dcount;  // [kBins]
+    uint32_t *scan;    // [WARPS + 1]
+    static constexpr size_t bytes(bool stable) {
+        return sizeof(uint32_t) * kBins * 3 + sizeof(uint32_t) * (WARPS + 1) +
+               (stable ? sizeof(uint32_t) * (kBins * STRIDE + 2 * WARPS * kBins) : 0);
+    }
+    __device__ static RankSmem carve(unsigned char *p, bool stable) {
+        RankSmem s;
+        s.cnt = reinterpret_cast<uint32_t *>(p);
+        p += sizeof(uint32_t) * kBins;
+        s.dstart = reinterpret_cast<uint32_t *>(p);
+        p += sizeof(uint32_t) * kBins;
+        s.dcount = reinterpret_cast<uint32_t *>(p);
+        p += sizeof(uint32_t) * kBins;
+        s.scan = reinterpret_cast<uint32_t *>(p);
+        p += sizeof(uint32_t) * (WARPS + 1);
+        s.wc = s.wm = nullptr;
+        if (stable) {
+            s.wc = reinterpret_cast<uint32_t *>(p);
+            p += sizeof(uint32_t) * kBins * STRIDE;
+            s.wm = reinterpret_cast<uint32_t *>(p);
+        }
+        return s;
+    }
+};
+
+// Rank of a tile of keys held in registers (ITEMS per thread, bit j of
+// `vmask` set for valid items) by digit (k >> shift) & mask, then placement
+// of the valid keys in `out` in digit order; dstart / dcount describe the
+// digit runs of the tile.
+//
+//  STABLE = false: one CTA-wide counter row; a key's rank among equal digits
+//    is the value its shared-memory atomicAdd returns, so equal digits land in
+//    arbitrary relative order.  That suffices wherever equal digits carry no
+//    order to keep: every MSD digit pass, and the first LSD pass of a finish
+//    (its input order is arbitrary).  A warp step whose 32 keys share one
+//    digit (sorted or skewed data) takes one atomic for the whole warp.
+//  STABLE = true: items are in warp-striped tile order (item j of lane l is
+//    index warp*32*ITEMS + j*32 + l, valid items a prefix).  Lanes with equal
+//    digits find each other through an atomicOr of their lane bit into the
+//    warp's peer-mask word of that digit (two mask sets alternate by item, so
+//    a set is cleared before its next use without a third barrier); the rank
+//    is the number of lower lanes in the group plus the warp's count before
+//    the step, so equal digits keep tile order.
 template <typename K, int THREADS, int ITEMS>
 struct Ranker {
     static constexpr int WARPS = THREADS / 32;
+    static constexpr int STRIDE = WARPS + 1;
     static constexpr int TILE = THREADS * ITEMS;
-    struct Smem {
-        uint16_t warp_cnt[WARPS * kBins];  // per-warp digit counts (<= 32 * ITEMS), then prefixes (< TILE)
-        uint32_t dstart[kBins];
-        uint32_t dcount[kBins];
-        uint32_t scan_tmp[WARPS + 1];
-    };
+    static_assert(THREADS >= kBins, "one thread per digit in the scans");
 
-    __device__ static void rank_and_place(const K (&keys)[ITEMS], int n_valid, int shift, uint32_t mask, Smem &s,
-                                          K *out) {
+    template <bool STABLE>
+    __device__ static void rank_and_place(const K (&keys)[ITEMS], uint32_t vmask, int shift, uint32_t mask,
+                                          const RankSmem<THREADS> &s, K *out) {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        uint16_t *wc = s.warp_cnt + warp * kBins;
-        for (int i = lane; i <= static_cast<int>(mask); i += 32) wc[i] = 0;
-        __syncwarp();
-        const unsigned lt = lanemask_lt();
-        const int wbase = warp * 32 * ITEMS;
-        uint32_t local[ITEMS];
+        const int t = threadIdx.x;
+        // rank of each item among equal digits (< TILE), two per register
+        uint32_t local[(ITEMS + 1) / 2];
 #pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            const int base = wbase + j * 32;
-            local[j] = 0;
-            if (base < n_valid) {  // warp-uniform
-                const bool valid = base + lane < n_valid;
-                const unsigned act = __ballot_sync(kFull, valid);
-                if (valid) {
-                    const uint32_t d = static_cast<uint32_t>(keys[j] >> shift) & mask;
-                    const unsigned peers = __match_any_sync(act, d);
-                    const uint32_t before = wc[d];
-                    const uint32_t r = __popc(peers & lt);
-                    local[j] = before + r;
-                    __syncwarp(act);
-                    if (r == 0) wc[d] = static_cast<uint16_t>(before + __popc(peers));
-                }
-                __syncwarp();
-            }
-        }
-        __syncthreads();
-        // per digit: exclusive prefix over warps, digit totals
-        for (int d = threadIdx.x; d <= static_cast<int>(mask); d += THREADS) {
-            uint32_t run = 0;
-#pragma unroll 4
-            for (int w = 0; w < WARPS; ++w) {
-                const uint32_t c = s.warp_cnt[w * kBins + d];
-                s.warp_cnt[w * kBins + d] = static_cast<uint16_t>(run);
-                run += c;
-            }
-            s.dcount[d] = run;
-        }
-        __syncthreads();
-        uint32_t total;
-        const uint32_t v = threadIdx.x <= mask ? s.dcount[threadIdx.x] : 0;
-        const uint32_t ex = block_exclusive_scan<THREADS>(v, s.scan_tmp, total);
-        if (threadIdx.x <= mask) s.dstart[threadIdx.x] = ex;
-        __syncthreads();
+        for (int j = 0; j < (ITEMS + 1) / 2; ++j) local[j] = 0;
+        if (!STABLE) {
+            if (t <= static_cast<int>(mask)) s.cnt[t] = 0;
+            __syncthreads();
 #pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            if (wbase + j * 32 + lane < n_valid) {
+            for (int j = 0; j < ITEMS; ++j) {
+                const bool valid = (vmask >> j) & 1u;
                 const uint32_t d = static_cast<uint32_t>(keys[j] >> shift) & mask;
-                out[s.dstart[d] + s.warp_cnt[warp * kBins + d] + local[j]] = keys[j];
+                const uint32_t d0 = __shfl_sync(kFull, d, 0);
+                uint32_t r;
+                if (__all_sync(kFull, valid && d == d0)) {
+                    uint32_t b = 0;
+                    if (lane == 0) b = atomicAdd(&s.cnt[d0], 32u);
+                    r = __shfl_sync(kFull, b, 0) + lane;
+                } else {
+                    r = valid ? atomicAdd(&s.cnt[d], 1u) : 0u;
+                }
+                local[j >> 1] |= r << ((j & 1) * 16);
             }
+            __syncthreads();
+            const uint32_t v = t <= static_cast<int>(mask) ? s.cnt[t] : 0u;
+            uint32_t total;
+            const uint32_t ex = block_exclusive_scan<THREADS>(v, s.scan, total);
+            if (t <= static_cast<int>(mask)) {
+                s.dstart[t] = ex;
+                s.dcount[t] = v;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) {
+                if ((vmask >> j) & 1u) {
+                    const uint32_t d = static_cast<uint32_t>(keys[j] >> shift) & mask;
+                    out[s.dstart[d] + ((local[j >> 1] >> ((j & 1) * 16)) & 0xffffu)] = keys[j];
+                }
+            }
+            __syncthreads();
+        } else {
+            for (int i = t; i < (static_cast<int>(mask) + 1) * STRIDE; i += THREADS) s.wc[i] = 0;
+            __syncthreads();
+            const unsigned lt = lanemask_lt();
+            const unsigned bit = 1u << lane;
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) {
+                const bool valid = (vmask >> j) & 1u;
+                if (__any_sync(kFull, valid)) {  // warp-uniform
+                    uint32_t *wm = s.wm + ((j & 1) * WARPS + warp) * kBins;
+                    const uint32_t d = static_cast<uint32_t>(keys[j] >> shift) & mask;
+                    uint32_t *wcd = s.wc + d * STRIDE + warp;
+                    if (valid) atomicOr(&wm[d], bit);
+                    __syncwarp();
+                    const uint32_t peers = wm[d];
+                    const uint32_t before = *wcd;
+                    __syncwarp();
+                    const uint32_t r = __popc(peers & lt);
+                    if (valid && r == 0) {
+                        *wcd = before + __popc(peers);
+                        wm[d] = 0;
+                    }
+                    local[j >> 1] |= (before + r) << ((j & 1) * 16);
+                }
+            }
+            __syncthreads();
+            // thread d: total of digit d, prefix over digits, then the exclusive
+            // prefix over warps written back as absolute tile offsets
+            uint32_t run = 0;
+            if (t <= static_cast<int>(mask)) {
+#pragma unroll
+                for (int w = 0; w < WARPS; ++w) run += s.wc[t * STRIDE + w];
+            }
+            uint32_t total;
+            const uint32_t ex = block_exclusive_scan<THREADS>(run, s.scan, total);
+            if (t <= static_cast<int>(mask)) {
+                s.dstart[t] = ex;
+                s.dcount[t] = run;
+                uint32_t acc = ex;
+#pragma unroll
+                for (int w = 0; w < WARPS; ++w) {
+                    const uint32_t x = s.wc[t * STRIDE + w];
+                    s.wc[t * STRIDE + w] = acc;
+                    acc += x;
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) {
+                if ((vmask >> j) & 1u) {
+                    const uint32_t d = static_cast<uint32_t>(keys[j] >> shift) & mask;
+                    out[s.wc[d * STRIDE + warp] + ((local[j >> 1] >> ((j & 1) * 16)) & 0xffffu)] = keys[j];
+                }
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
 };
+
+// Loads the keys of the tile-relative range [lo_r, hi_r) of the 16-byte-
+// aligned window starting at element `wstart` into registers.  Window index
+// of item j of a thread: warp w owns [w*32*ITEMS, (w+1)*32*ITEMS); its group
+// g = j / V (V keys per 16 bytes) of lane l covers ((w*G + g)*32 + l)*V +
+// (j % V), so a warp reads 512 contiguous bytes per group.  Whole in-range
+// vectors are one 16-byte load when `vec_ok` (buffer base 16-byte aligned);
+// boundary vectors are scalar.  Returns the validity mask (bit j: item j
+// holds a key).
+template <typename K, int THREADS, int ITEMS>
+struct TileLoad {
+    static constexpr int V = 16 / static_cast<int>(sizeof(K));
+    static constexpr int G = ITEMS / V;
+    static_assert(ITEMS % V == 0, "items must be whole vectors");
+
+    __device__ static uint32_t load(const K *__restrict__ src, uint64_t wstart, uint32_t lo_r, uint32_t hi_r,
+                                    bool vec_ok, K (&k)[ITEMS]) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const K *w = src + wstart;
+        uint32_t vmask = 0;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const uint32_t r0 = static_cast<uint32_t>(((warp * G + g) * 32 + lane) * V);
+            if (vec_ok && r0 >= lo_r && r0 + V <= hi_r) {
+                const uint4 q = __ldcs(reinterpret_cast<const uint4 *>(w + r0));
+                memcpy(&k[g * V], &q, 16);
+                vmask |= ((1u << V) - 1) << (g * V);
+            } else {
+#pragma unroll
+                for (int e = 0; e < V; ++e) {
+                    const uint32_t r = r0 + e;
+                    const bool ok = r >= lo_r && r < hi_r;
+                    k[g * V + e] = ok ? w[r] : K(0);
+                    vmask |= static_cast<uint32_t>(ok) << (g * V + e);
+                }
+            }
+        }
+        return vmask;
+    }
+};
+
+// Validity mask of warp-striped items whose tile index is below n_valid.
+template <int ITEMS>
+__device__ __forceinline__ uint32_t striped_mask(int n_valid) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int rem = n_valid - warp * 32 * ITEMS - lane;  // item j valid iff j*32 < rem
+    uint32_t m = 0;
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) m |= static_cast<uint32_t>(j * 32 < rem) << j;
+    return m;
+}
+
+// AND / OR of one key per thread (key width), broadcast to every thread.
+template <typename K, int THREADS>
+__device__ __forceinline__ void block_and_or_k(K &a, K &o, K *ta, K *to) {
+    constexpr int WARPS = THREADS / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        a &= __shfl_xor_sync(kFull, a, s);
+        o |= __shfl_xor_sync(kFull, o, s);
+    }
+    if (lane == 0) {
+        ta[warp] = a;
+        to[warp] = o;
+    }
+    __syncthreads();
+    a = static_cast<K>(~K(0));
+    o = 0;
+#pragma unroll
+    for (int w = 0; w < WARPS; ++w) {
+        a &= ta[w];
+        o |= to[w];
+    }
+    __syncthreads();
+}
 
 template <typename K>
 __device__ __forceinline__ const K *src_of(const Work &wk, int src) {
@@ -268,10 +437,14 @@ __global__ void k_init(Work wk, uint32_t n_chunks0, int direct_unit) {
 }
 
 // Per-chunk digit histogram (one shared-memory row per warp) and AND/OR.
+// Reads 16-byte vectors over the aligned window around the chunk.  A vector
+// whose keys share one digit adds once; a warp whose vectors all share one
+// digit adds once per warp (sorted and skewed inputs).
 template <typename K, int THREADS>
 __global__ void __launch_bounds__(THREADS) k_hist(Work wk, int level) {
     constexpr int WARPS = THREADS / 32;
-    constexpr int U = 8;
+    constexpr int V = 16 / static_cast<int>(sizeof(K));
+    constexpr int U = 4;  // vectors in flight per thread
     __shared__ uint32_t sh[WARPS * kBins];
     __shared__ unsigned long long ta[WARPS], to[WARPS];
     const int p = level & 1;
@@ -292,32 +465,56 @@ __global__ void __launch_bounds__(THREADS) k_hist(Work wk, int level) {
         __syncthreads();
         uint32_t *my = sh + warp * kBins;
         K a = static_cast<K>(~K(0)), o = 0;
-        const K *s = src_of<K>(wk, b.src) + ch.start;
-        const uint32_t len = ch.len;
+        const K *src = src_of<K>(wk, b.src);
+        const bool vec_ok = b.src ? true : wk.keys_vec_ok;
+        const uint64_t lo = ch.start, hi = ch.start + ch.len;
+        const uint64_t w0 = lo - lo % V;
         const bool raw = b.raw;
-        for (uint32_t base = 0; base < len; base += THREADS * U) {
-            K kk[U];
+        for (uint64_t base = w0; base < hi; base += static_cast<uint64_t>(THREADS) * V * U) {
+            K kk[U * V];
+            uint32_t vm = 0;
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const uint32_t i = base + u * THREADS + threadIdx.x;
-                kk[u] = i < len ? s[i] : K(0);
+                const uint64_t i0 = base + static_cast<uint64_t>((u * THREADS + threadIdx.x) * V);
+                if (vec_ok && i0 >= lo && i0 + V <= hi) {
+                    const uint4 q = __ldcs(reinterpret_cast<const uint4 *>(src + i0));
+                    memcpy(&kk[u * V], &q, 16);
+                    vm |= ((1u << V) - 1) << (u * V);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < V; ++e) {
+                        const uint64_t i = i0 + e;
+                        const bool ok = i >= lo && i < hi;
+                        kk[u * V + e] = ok ? src[i] : K(0);
+                        vm |= static_cast<uint32_t>(ok) << (u * V + e);
+                    }
+                }
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const uint32_t i = base + u * THREADS + threadIdx.x;
-                const bool valid = i < len;
-                K key = kk[u];
-                if (raw) key = encode_key(key, wk.codec);
-                const uint32_t d = valid ? (static_cast<uint32_t>(key >> shift) & mask) : 0xffffffffu;
-                if (valid) {
-                    a &= key;
-                    o |= key;
+                uint32_t d[V];
+                bool same = true;
+#pragma unroll
+                for (int e = 0; e < V; ++e) {
+                    K key = kk[u * V + e];
+                    if (raw) key = encode_key(key, wk.codec);
+                    const bool ok = (vm >> (u * V + e)) & 1u;
+                    if (ok) {
+                        a &= key;
+                        o |= key;
+                    }
+                    d[e] = ok ? (static_cast<uint32_t>(key >> shift) & mask) : 0xffffffffu;
+                    same = same && d[e] == d[0];
                 }
-                const uint32_t d0 = __shfl_sync(kFull, d, 0);
-                if (__all_sync(kFull, d == d0)) {
-                    if (lane == 0 && d0 != 0xffffffffu) atomicAdd(&my[d0], 32u);
-                } else if (valid) {
-                    atomicAdd(&my[d], 1u);
+                const uint32_t d0 = __shfl_sync(kFull, d[0], 0);
+                if (__all_sync(kFull, same && d[0] == d0)) {
+                    if (lane == 0 && d0 != 0xffffffffu) atomicAdd(&my[d0], 32u * V);
+                } else if (same) {
+                    if (d[0] != 0xffffffffu) atomicAdd(&my[d[0]], static_cast<uint32_t>(V));
+                } else {
+#pragma unroll
+                    for (int e = 0; e < V; ++e)
+                        if (d[e] != 0xffffffffu) atomicAdd(&my[d[e]], 1u);
                 }
             }
         }
@@ -372,7 +569,7 @@ __global__ void __launch_bounds__(THREADS) k_colscan(Work wk, int level) {
         if (in) {
             const uint32_t out = static_cast<uint32_t>(ex_global - seg0);
             col[c] = out;
-            if (last) wk.bucket_base[static_cast<size_t>(b) * kBins + d] = static_cast<unsigned long long>(out) + v;
+            if (last) wk.bucket_base[static_cast<size_t>(b) * kBins + d] = out + v;
         }
         if (threadIdx.x == THREADS - 1) sh_last = seg0;
         __syncthreads();
@@ -388,7 +585,12 @@ __global__ void __launch_bounds__(THREADS) k_colscan(Work wk, int level) {
 template <int THREADS>
 __device__ void emit_buckets(const Work &wk, int q, bool take, uint64_t start, uint64_t len, int h, int src, int raw,
                              uint32_t *tmp, uint32_t *sh_choff, uint32_t *sh_slot, uint32_t *sh_bases) {
-    const uint32_t nchunks = take ? static_cast<uint32_t>((len + wk.chunk_keys - 1) / wk.chunk_keys) : 0;
+    // chunk boundaries sit on 16-byte boundaries of the buffer except the
+    // bucket's own start, so every tile after the first is an aligned window
+    const uint64_t vk = 128u / static_cast<uint32_t>(wk.w);
+    const uint64_t abase = start - start % vk;
+    const uint32_t nchunks =
+        take ? static_cast<uint32_t>((start + len - abase + wk.chunk_keys - 1) / wk.chunk_keys) : 0;
     uint32_t nb_total, nc_total;
     const uint32_t slot_off = block_exclusive_scan<THREADS>(take ? 1u : 0u, tmp, nb_total);
     const uint32_t ch_off = block_exclusive_scan<THREADS>(nchunks, tmp, nc_total);
@@ -433,10 +635,13 @@ __device__ void emit_buckets(const Work &wk, int q, bool take, uint64_t start, u
             const int d = lo;
             const Bucket &nbk = wk.buckets[q][b0 + sh_slot[d]];
             const uint32_t i = k - sh_choff[d];
+            const uint64_t nb_base = nbk.start - nbk.start % vk;
+            const uint64_t cs = i == 0 ? nbk.start : nb_base + static_cast<uint64_t>(i) * wk.chunk_keys;
+            const uint64_t ce_lim = nb_base + static_cast<uint64_t>(i + 1) * wk.chunk_keys;
+            const uint64_t ce = ce_lim < nbk.start + nbk.len ? ce_lim : nbk.start + nbk.len;
             Chunk ch;
-            ch.start = nbk.start + static_cast<uint64_t>(i) * wk.chunk_keys;
-            const uint64_t rem = nbk.len - static_cast<uint64_t>(i) * wk.chunk_keys;
-            ch.len = static_cast<uint32_t>(rem < wk.chunk_keys ? rem : wk.chunk_keys);
+            ch.start = cs;
+            ch.len = static_cast<uint32_t>(ce - cs);
             ch.bucket = b0 + sh_slot[d];
             wk.chunks[q][c0 + k] = ch;
         }
@@ -464,22 +669,6 @@ __device__ void emit_fill(const Work &wk, uint64_t start, uint64_t len, uint64_t
     }
 }
 
-__device__ void emit_unit(const Work &wk, uint64_t start, uint32_t len, int src) {
-    const uint32_t u = atomicAdd(&wk.ctl->n_units, 1u);
-    if (u >= wk.max_units) {
-        set_error(wk.ctl, kErrCapacity);
-        return;
-    }
-    atomicAdd(&wk.ctl->finish_keys, static_cast<unsigned long long>(len));
-    Unit un;
-    un.start = start;
-    un.len = len;
-    un.src = static_cast<uint8_t>(src);
-    un.raw = 0;
-    un.pad[0] = un.pad[1] = 0;
-    wk.units[u] = un;
-}
-
 // Per bucket of this level: common-prefix test, digit bases, child classes.
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS) k_classify(Work wk, int level) {
@@ -489,6 +678,8 @@ __global__ void __launch_bounds__(THREADS) k_classify(Work wk, int level) {
     __shared__ uint32_t tmp[THREADS / 32 + 1];
     __shared__ uint32_t sh_choff[THREADS], sh_slot[THREADS], sh_bases[2];
     __shared__ unsigned long long sh_len[THREADS], sh_base[THREADS];
+    __shared__ int itmp[THREADS / 32 + 1], sh_i2[THREADS];
+    __shared__ uint32_t sh_u[THREADS], sh_u2[THREADS];
     const int p = level & 1, q = p ^ 1;
     if (wk.ctl->error) return;
     const uint32_t nb = wk.ctl->n_buckets[p];
@@ -525,7 +716,7 @@ __global__ void __launch_bounds__(THREADS) k_classify(Work wk, int level) {
         unsigned long long total;
         const unsigned long long ex = block_exclusive_scan64<THREADS>(tot, tmp64, total);
         const unsigned long long base = b.start + ex;
-        if (static_cast<uint32_t>(d) <= mask) wk.bucket_base[static_cast<size_t>(i) * kBins + d] = base;
+        if (static_cast<uint32_t>(d) <= mask) wk.bucket_base[static_cast<size_t>(i) * kBins + d] = static_cast<uint32_t>(ex);
         if (threadIdx.x == 0) {
             wk.buckets[p][i].scatter = 1;
             atomicAdd(&wk.ctl->scatter_keys[level], static_cast<unsigned long long>(b.len));
@@ -541,43 +732,83 @@ __global__ void __launch_bounds__(THREADS) k_classify(Work wk, int level) {
             emit_fill(wk, base, tot, (a & hi_mask) | static_cast<unsigned long long>(d));
         }
         emit_buckets<THREADS>(wk, q, big && hc > 0, base, tot, hc, dst, 0, tmp, sh_choff, sh_slot, sh_bases);
-        // small children: adjacent ones merge into units up to merge_cap keys
-        if (threadIdx.x == 0) {
-            unsigned long long run_start = 0;
-            uint32_t run_len = 0;
-            for (uint32_t e = 0; e <= mask; ++e) {
-                const unsigned long long len = sh_len[e];
-                if (len == 0) continue;
-                if (len > wk.unit_cap) {
-                    if (run_len) emit_unit(wk, run_start, run_len, dst);
-                    run_len = 0;
-                    continue;
-                }
-                if (run_len && run_len + len <= wk.merge_cap) {
-                    run_len += static_cast<uint32_t>(len);
-                } else {
-                    if (run_len) emit_unit(wk, run_start, run_len, dst);
-                    run_start = sh_base[e];
-                    run_len = static_cast<uint32_t>(len);
-                }
+        // Small children become finish units.  Children of at most
+        // merge_cap / 4 keys ("tiny") merge with their tiny neighbours: inside a
+        // run of adjacent tiny children (empty children do not break a run),
+        // child e joins group floor(P_e / merge_cap) of the run, P_e being the
+        // keys of the run before it, so a group holds < 1.25 * merge_cap keys.
+        {
+            const uint32_t len = static_cast<uint32_t>(tot);
+            const bool small = tot > 0 && tot <= wk.unit_cap;
+            const bool tiny = small && len <= wk.merge_cap / 4;
+            const bool solid = tot > 0 && !tiny;  // breaks runs
+            // latest solid child before e, latest tiny child before e
+            const int last_solid = block_inclusive_max<THREADS>(solid ? d : -1, itmp);
+            const int last_tiny_incl = block_inclusive_max<THREADS>(tiny ? d : -1, itmp);
+            sh_i2[d] = last_tiny_incl;
+            __syncthreads();
+            const int prev_tiny = d > 0 ? sh_i2[d - 1] : -1;
+            const bool run_start = tiny && (prev_tiny < 0 || prev_tiny < last_solid);
+            uint32_t dummy;
+            const uint32_t g_ex = block_exclusive_scan<THREADS>(tiny ? len : 0u, tmp, dummy);
+            sh_u[d] = g_ex;
+            const int rs_idx = block_inclusive_max<THREADS>(run_start ? d : -1, itmp);
+            // (barriers inside the scans publish sh_u)
+            const uint32_t pre = tiny ? g_ex - sh_u[rs_idx] : 0u;
+            const uint32_t gid = pre / wk.merge_cap;
+            sh_u2[d] = gid;
+            __syncthreads();
+            const bool head = tiny && (run_start || sh_u2[prev_tiny] != gid);
+            const int head_idx = block_inclusive_max<THREADS>(head ? d : -1, itmp);
+            sh_u[d] = 0;
+            __syncthreads();
+            if (tiny) atomicAdd(&sh_u[head_idx], len);
+            __syncthreads();
+            const bool emit = (small && !tiny) || head;
+            const uint32_t ulen = head ? sh_u[d] : len;
+            uint32_t n_emit;
+            const uint32_t slot = block_exclusive_scan<THREADS>(emit ? 1u : 0u, tmp, n_emit);
+            uint32_t keys_total;
+            (void)block_exclusive_scan<THREADS>(emit ? ulen : 0u, tmp, keys_total);
+            if (threadIdx.x == 0 && n_emit) {
+                const uint32_t u0 = atomicAdd(&wk.ctl->n_units, n_emit);
+                sh_bases[0] = u0;
+                if (u0 + n_emit > wk.max_units) set_error(wk.ctl, kErrCapacity);
+                atomicAdd(&wk.ctl->finish_keys, static_cast<unsigned long long>(keys_total));
             }
-            if (run_len) emit_unit(wk, run_start, run_len, dst);
+            __syncthreads();
+            if (emit && n_emit && sh_bases[0] + n_emit <= wk.max_units) {
+                Unit un;
+                un.start = base;
+                un.len = ulen;
+                un.src = static_cast<uint8_t>(dst);
+                un.raw = 0;
+                un.pad[0] = un.pad[1] = 0;
+                wk.units[sh_bases[0] + slot] = un;
+            }
         }
         __syncthreads();
     }
 }
 
-// Stable shared-memory digit ranking of each tile, then coalesced runs to
-// the digit offsets of the chunk.
+// Per chunk: digit ranking of each tile in shared memory (unstable: equal
+// digits need no order in an MSD pass), then the digit runs are written to
+// the chunk's digit offsets.  Tiles are 16-byte-aligned windows; the global
+// address of a run is checked against the bucket once per digit and tile.
 template <typename K, int THREADS, int ITEMS>
 __global__ void __launch_bounds__(THREADS, 2) k_scatter(Work wk, int level) {
     using R = Ranker<K, THREADS, ITEMS>;
+    using L = TileLoad<K, THREADS, ITEMS>;
     constexpr int TILE = R::TILE;
-    __shared__ typename R::Smem rs;
-    __shared__ K sm_keys[TILE];
-    __shared__ unsigned long long off[kBins];
+    constexpr int V = L::V;
+    extern __shared__ __align__(16) unsigned char smem[];
+    K *sm_keys = reinterpret_cast<K *>(smem);
+    unsigned long long *off = reinterpret_cast<unsigned long long *>(smem + sizeof(K) * TILE);
+    unsigned long long *adj = off + kBins;
+    int *bad = reinterpret_cast<int *>(adj + kBins);
+    const RankSmem<THREADS> rs =
+        RankSmem<THREADS>::carve(smem + sizeof(K) * TILE + 2 * sizeof(unsigned long long) * kBins + 16, false);
     const int p = level & 1;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (wk.ctl->error) return;
     const uint32_t nch = wk.ctl->n_chunks[p];
     for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) {
@@ -585,104 +816,131 @@ __global__ void __launch_bounds__(THREADS, 2) k_scatter(Work wk, int level) {
         const Bucket b = wk.buckets[p][ch.bucket];
         if (!b.scatter) continue;  // block-uniform
         const uint64_t lo_pos = b.start, hi_pos = b.start + b.len;
-        const K *src = src_of<K>(wk, b.src);
-        K *dst = dst_of<K>(wk, b.src);
+        const K *__restrict__ src = src_of<K>(wk, b.src);
+        K *__restrict__ dst = dst_of<K>(wk, b.src);
+        const bool vec_ok = b.src ? true : wk.keys_vec_ok;
         const int r_eff = min(kRadixBits, b.h);
         const int shift = b.h - r_eff;
         const uint32_t mask = (1u << r_eff) - 1;
         for (int d = threadIdx.x; d <= static_cast<int>(mask); d += THREADS)
-            off[d] = wk.bucket_base[static_cast<size_t>(ch.bucket) * kBins + d] +
+            off[d] = b.start + wk.bucket_base[static_cast<size_t>(ch.bucket) * kBins + d] +
                      wk.hist[static_cast<size_t>(d) * wk.max_chunks + c];
+        if (threadIdx.x == 0) *bad = 0;
         __syncthreads();
-        for (uint32_t t0 = 0; t0 < ch.len; t0 += TILE) {
-            const int nv = static_cast<int>(min(static_cast<uint32_t>(TILE), ch.len - t0));
-            const K *s = src + ch.start + t0;
+        const uint64_t cend = ch.start + ch.len;
+        for (uint64_t pos = ch.start; pos < cend;) {
+            const uint64_t wstart = pos - pos % V;
+            const uint64_t thi = min(cend, wstart + TILE);
+            const uint32_t lo_r = static_cast<uint32_t>(pos - wstart);
+            const uint32_t hi_r = static_cast<uint32_t>(thi - wstart);
+            const int nv = static_cast<int>(hi_r - lo_r);
             K k[ITEMS];
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j) {
-                const int idx = warp * 32 * ITEMS + j * 32 + lane;
-                k[j] = idx < nv ? s[idx] : K(0);
-            }
+            const uint32_t vmask = L::load(src, wstart, lo_r, hi_r, vec_ok, k);
             if (b.raw) {
 #pragma unroll
                 for (int j = 0; j < ITEMS; ++j) k[j] = encode_key(k[j], wk.codec);
             }
-            R::rank_and_place(k, nv, shift, mask, rs, sm_keys);
-            bool oob = false;
+            R::template rank_and_place<false>(k, vmask, shift, mask, rs, sm_keys);
+            // per digit: where the tile's run goes, checked against the bucket
+            for (int d = threadIdx.x; d <= static_cast<int>(mask); d += THREADS) {
+                const uint32_t cnt = rs.dcount[d];
+                const unsigned long long o = off[d];
+                adj[d] = o - rs.dstart[d];
+                if (cnt && (o < lo_pos || o + cnt > hi_pos)) *bad = 1;  // never write outside the bucket
+                off[d] = o + cnt;
+            }
+            __syncthreads();
+            if (*bad) {
+                if (threadIdx.x == 0) set_error(wk.ctl, kErrBounds);
+                return;  // block-uniform
+            }
             for (int i = threadIdx.x; i < nv; i += THREADS) {
                 const K key = sm_keys[i];
-                const uint32_t d = static_cast<uint32_t>(key >> shift) & mask;
-                const uint64_t pos = off[d] + (i - rs.dstart[d]);
-                if (pos >= lo_pos && pos < hi_pos) dst[pos] = key;  // bounds check: never write outside the bucket
-                else oob = true;
+                dst[adj[static_cast<uint32_t>(key >> shift) & mask] + i] = key;
             }
-            if (oob) set_error(wk.ctl, kErrBounds);
             __syncthreads();
-            for (int d = threadIdx.x; d <= static_cast<int>(mask); d += THREADS) off[d] += rs.dcount[d];
-            __syncthreads();
+            pos = thi;
         }
     }
 }
 
-// Shared-memory finish of every unit: LSD passes over the unit's varying
-// bits (bits above its highest varying bit are common to the whole run),
-// then the decoded keys go to their final place in the caller's buffer.
 template <typename K, int THREADS, int ITEMS>
-__global__ void __launch_bounds__(THREADS, 2) k_finish(Work wk) {
+constexpr size_t scatter_smem() {
+    return sizeof(K) * THREADS * ITEMS + 2 * sizeof(unsigned long long) * kBins + 16 +
+           RankSmem<THREADS>::bytes(false);
+}
+
+// Shared-memory finish of every unit: LSD passes over the unit's varying
+// bits (bits above its highest varying bit are common to the whole run; a
+// run with no varying bit is one repeated key), then the decoded keys go to
+// their final place in the caller's buffer.  The first pass needs no
+// stability (input order is arbitrary); later passes keep tile order.
+template <typename K, int THREADS, int ITEMS>
+__global__ void __launch_bounds__(THREADS, 4) k_finish(Work wk) {
     using R = Ranker<K, THREADS, ITEMS>;
-    __shared__ typename R::Smem rs;
-    __shared__ K sm_keys[R::TILE];
-    __shared__ unsigned long long ta[THREADS / 32], to[THREADS / 32];
+    using L = TileLoad<K, THREADS, ITEMS>;
+    constexpr int TILE = R::TILE;
+    constexpr int V = L::V;
+    constexpr int WARPS = THREADS / 32;
+    extern __shared__ __align__(16) unsigned char smem[];
+    K *sm_keys = reinterpret_cast<K *>(smem);
+    K *ta = reinterpret_cast<K *>(smem + sizeof(K) * TILE);
+    K *to = ta + WARPS;
+    const RankSmem<THREADS> rs = RankSmem<THREADS>::carve(smem + sizeof(K) * (TILE + 2 * WARPS), true);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (wk.ctl->error) return;
+    for (int i = threadIdx.x; i < 2 * WARPS * kBins; i += THREADS) rs.wm[i] = 0;  // peer masks start clear
     const uint32_t nu = wk.ctl->n_units;
-    K *out = static_cast<K *>(wk.keys);
+    K *__restrict__ out = static_cast<K *>(wk.keys);
     for (uint32_t u = blockIdx.x; u < nu; u += gridDim.x) {
         const Unit un = wk.units[u];
-        const K *s = src_of<K>(wk, un.src) + un.start;
+        const K *__restrict__ src = src_of<K>(wk, un.src);
+        const bool vec_ok = un.src ? true : wk.keys_vec_ok;
         const int len = static_cast<int>(un.len);
+        const uint64_t wstart = un.start - un.start % V;
+        const uint32_t lo_r = static_cast<uint32_t>(un.start - wstart);
         K k[ITEMS];
-        unsigned long long a = ~0ull, o = 0;
+        uint32_t vmask = L::load(src, wstart, lo_r, lo_r + un.len, vec_ok, k);
+        K a = static_cast<K>(~K(0)), o = 0;
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) {
-            const int idx = warp * 32 * ITEMS + j * 32 + lane;
-            K key = idx < len ? s[idx] : K(0);
-            if (un.raw) key = encode_key(key, wk.codec);
-            k[j] = key;
-            if (idx < len) {
-                a &= key;
-                o |= key;
+            if (un.raw) k[j] = encode_key(k[j], wk.codec);
+            if ((vmask >> j) & 1u) {
+                a &= k[j];
+                o |= k[j];
             }
         }
-        block_and_or<THREADS>(a, o, ta, to);
-        const unsigned long long v = a ^ o;
-        if (v == 0) {
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j) {
-                const int idx = warp * 32 * ITEMS + j * 32 + lane;
-                if (idx < len) out[un.start + idx] = decode_key(k[j], wk.codec);
-            }
+        block_and_or_k<K, THREADS>(a, o, ta, to);
+        K *__restrict__ dstp = out + un.start;
+        const unsigned long long v = static_cast<unsigned long long>(a ^ o);
+        if (v == 0) {  // one repeated key: write it len times
+            const K val = decode_key(a, wk.codec);
+            for (int i = threadIdx.x; i < len; i += THREADS) dstp[i] = val;
             continue;
         }
         const int lo = __ffsll(static_cast<long long>(v)) - 1;
         const int hi = 64 - __clzll(v);
         const int passes = (hi - lo + kRadixBits - 1) / kRadixBits;
         const int width = (hi - lo + passes - 1) / passes;
-        for (int ps = 0, sh = lo; ps < passes; ++ps, sh += width) {
-            const int bits = min(width, hi - sh);
-            R::rank_and_place(k, len, sh, (1u << bits) - 1, rs, sm_keys);
-            if (ps + 1 < passes) {
+        R::template rank_and_place<false>(k, vmask, lo, (1u << min(width, hi - lo)) - 1, rs, sm_keys);
+        if (passes > 1) {
+            vmask = striped_mask<ITEMS>(len);
+            for (int ps = 1, sh = lo + width; ps < passes; ++ps, sh += width) {
+                const K *row = sm_keys + warp * 32 * ITEMS + lane;
 #pragma unroll
-                for (int j = 0; j < ITEMS; ++j) {
-                    const int idx = warp * 32 * ITEMS + j * 32 + lane;
-                    if (idx < len) k[j] = sm_keys[idx];
-                }
+                for (int j = 0; j < ITEMS; ++j) k[j] = (vmask >> j) & 1u ? row[j * 32] : K(0);
                 __syncthreads();
+                R::template rank_and_place<true>(k, vmask, sh, (1u << min(width, hi - sh)) - 1, rs, sm_keys);
             }
         }
-        for (int i = threadIdx.x; i < len; i += THREADS) out[un.start + i] = decode_key(sm_keys[i], wk.codec);
+        for (int i = threadIdx.x; i < len; i += THREADS) dstp[i] = decode_key(sm_keys[i], wk.codec);
         __syncthreads();
     }
+}
+
+template <typename K, int THREADS, int ITEMS>
+constexpr size_t finish_smem() {
+    return sizeof(K) * (THREADS * ITEMS + 2 * (THREADS / 32)) + RankSmem<THREADS>::bytes(true);
 }
 
 template <typename K>
@@ -705,35 +963,54 @@ template <typename K>
 struct Cfg;
 template <>
 struct Cfg<uint32_t> {
-    static constexpr int kThreads = 512;
+    static constexpr int kThreads = 512;  // scatter tile: 512 x 16 = 8192 keys
     static constexpr int kItems = 16;
+    static constexpr int kFinThreads = 256;  // finish tile: 256 x 20 = 5120 keys, 4 CTAs per SM
+    static constexpr int kFinItems = 20;
 };
 template <>
 struct Cfg<uint64_t> {
-    static constexpr int kThreads = 512;
+    static constexpr int kThreads = 512;  // 512 x 8 = 4096 keys
     static constexpr int kItems = 8;
+    static constexpr int kFinThreads = 256;  // 256 x 10 = 2560 keys
+    static constexpr int kFinItems = 10;
 };
 
 }  // namespace
 
 MsdShape msd_shape(int key_bytes) {
     MsdShape s;
+    uint32_t fin;
     if (key_bytes == 4) {
         s.tile = Cfg<uint32_t>::kThreads * Cfg<uint32_t>::kItems;
+        fin = Cfg<uint32_t>::kFinThreads * Cfg<uint32_t>::kFinItems;
         s.levels = 4;
     } else {
         s.tile = Cfg<uint64_t>::kThreads * Cfg<uint64_t>::kItems;
+        fin = Cfg<uint64_t>::kFinThreads * Cfg<uint64_t>::kFinItems;
         s.levels = 8;
     }
     s.chunk = 2 * s.tile;
-    s.unit_cap = s.tile;
-    s.merge_cap = s.tile / 2;
+    s.unit_cap = fin - 16;  // a unit plus its misalignment fits one aligned finish window
+    // tiny buckets (<= merge_cap / 4) group below 1.25 * merge_cap <= unit_cap
+    s.merge_cap = (s.unit_cap * 4 / 5) & ~63u;
     return s;
 }
 
 template <typename K>
 void launch_msd(const Work &wk, cudaStream_t st, Recorder &rec, int num_sms) {
     constexpr int T = Cfg<K>::kThreads, I = Cfg<K>::kItems;
+    constexpr int FT = Cfg<K>::kFinThreads, FI = Cfg<K>::kFinItems;
+    constexpr size_t kScatterSmem = scatter_smem<K, T, I>();
+    constexpr size_t kFinishSmem = finish_smem<K, FT, FI>();
+    static bool attrs = false;
+    if (!attrs) {
+        cudaFuncSetAttribute(k_scatter<K, T, I>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kScatterSmem));
+        cudaFuncSetAttribute(k_finish<K, FT, FI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kFinishSmem));
+        attrs = true;
+    }
     const MsdShape shape = msd_shape(sizeof(K));
     const bool direct = wk.n <= shape.unit_cap;
     const uint32_t nc0 = direct ? 0u : static_cast<uint32_t>((wk.n + wk.chunk_keys - 1) / wk.chunk_keys);
@@ -752,12 +1029,12 @@ void launch_msd(const Work &wk, cudaStream_t st, Recorder &rec, int num_sms) {
             k_classify<kBins><<<num_sms * 4, kBins, 0, st>>>(wk, level);
             rec.end();
             rec.begin(BSORT_K_SCATTER, level);
-            k_scatter<K, T, I><<<num_sms * 2, T, 0, st>>>(wk, level);
+            k_scatter<K, T, I><<<num_sms * 2, T, kScatterSmem, st>>>(wk, level);
             rec.end();
         }
     }
     rec.begin(BSORT_K_FINISH, -1);
-    k_finish<K, T, I><<<num_sms * 2, T, 0, st>>>(wk);
+    k_finish<K, FT, FI><<<num_sms * 4, FT, kFinishSmem, st>>>(wk);
     rec.end();
     if (!direct) {
         rec.begin(BSORT_K_FILL, -1);

@@ -59,10 +59,11 @@ def test_workspace_sizes(lib):
         small = pkg.workspace_bytes(1000, dt)
         big = pkg.workspace_bytes(1 << 28, dt)
         assert 0 < small <= big
-    # ping-pong: the alternate buffer dominates for wide keys
+    # ping-pong: the alternate buffer dominates for wide keys; metadata is
+    # bounded by the worst case of buckets just above the finish threshold
     n = 1 << 28
-    assert n * 4 <= pkg.workspace_bytes(n, "int32") <= n * 4 * 1.2
-    assert n * 8 <= pkg.workspace_bytes(n, "float64") <= n * 8 * 1.2
+    assert n * 4 <= pkg.workspace_bytes(n, "int32") <= n * 4 * 1.25
+    assert n * 8 <= pkg.workspace_bytes(n, "float64") <= n * 8 * 1.25
     # counting path: no alternate buffer
     assert pkg.workspace_bytes(n, "uint8") < 1 << 20
     with pytest.raises(pkg.BsortError):

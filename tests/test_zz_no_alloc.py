@@ -45,9 +45,22 @@ def test_noalloc_matches_bsort_keys_two_calls_in_a_row(lib):
         assert np.array_equal(got.view(np.uint8), want.view(np.uint8)), x.dtype
 
 
+def _largest_n(dtype, cap=64 << 20):
+    """Largest n whose workspace fits the library's 64 MiB static array."""
+    import paper_2603_08929_gb300 as bs
+    lo, hi = 0, 1 << 34
+    while lo < hi:
+        mid = (lo + hi + 1) // 2
+        if bs.workspace_bytes(mid, dtype) <= cap:
+            lo = mid
+        else:
+            hi = mid - 1
+    return lo
+
+
 def test_noalloc_rejects_n_beyond_the_array(lib):
     import torch
-    n = 14975296 + 1  # one more 4-byte key than the 64 MiB array serves
+    n = _largest_n("int32") + 1  # one more 4-byte key than the array serves
     t = torch.zeros(n, dtype=torch.int32, device="cuda")
     t[0] = 5
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
