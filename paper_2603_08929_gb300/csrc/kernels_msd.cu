@@ -25,6 +25,9 @@ namespace bsort {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+// comparison finish: largest sub-bucket, and comparisons per key one LSD pass is worth
+constexpr uint32_t kCmpMaxBucket = 128;
+constexpr uint32_t kCmpKeysPerPass = 16;
 
 template <int THREADS>
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *tmp, uint32_t &total) {
@@ -137,44 +140,33 @@ __device__ __forceinline__ void block_and_or(unsigned long long &a, unsigned lon
     __syncthreads();
 }
 
-// Shared-memory buffers of one tile ranking, carved from dynamic shared
-// memory.  Unstable ranking uses one CTA-wide counter row; stable ranking
-// uses per-digit, per-warp counters laid out digit-major with one pad word
-// per digit (stride WARPS + 1: the banks of a warp's counters spread, and the
-// thread that scans digit d reads its WARPS counters at consecutive words)
-// and two sets of per-warp peer masks.
-template <int THREADS>
+// Dynamic shared memory of every kernel below; each kernel lays its buffers
+// out at compile-time offsets, so addresses are one base plus a constant.
+extern __shared__ __align__(16) unsigned char g_dyn_smem[];
+
+// Shared-memory buffers of one tile ranking, at byte offset BASE of dynamic
+// shared memory.  Unstable ranking uses one CTA-wide counter row; stable
+// ranking uses per-digit, per-warp counters laid out digit-major with one pad
+// word per digit (stride WARPS + 1: the banks of a warp's counters spread,
+// and the thread that scans digit d reads its WARPS counters at consecutive
+// words) and two sets of per-warp peer masks.
+template <int THREADS, size_t BASE, bool STABLE_BUFS>
 struct RankSmem {
     static constexpr int WARPS = THREADS / 32;
     static constexpr int STRIDE = WARPS + 1;
-    uint32_t *cnt;     // [kBins] (unstable)
-    uint32_t *wc;      // [kBins][STRIDE] (stable): counts, then absolute tile offsets
-    uint32_t *wm;      // [2][WARPS][kBins] (stable): peer masks, zero between items
-    uint32_t *dstart;  // [kBins]
-    uint32_t *dcount;  // [kBins]
-    uint32_t *scan;    // [WARPS + 1]
-    static constexpr size_t bytes(bool stable) {
-        return sizeof(uint32_t) * kBins * 3 + sizeof(uint32_t) * (WARPS + 1) +
-               (stable ? sizeof(uint32_t) * (kBins * STRIDE + 2 * WARPS * kBins) : 0);
-    }
-    __device__ static RankSmem carve(unsigned char *p, bool stable) {
-        RankSmem s;
-        s.cnt = reinterpret_cast<uint32_t *>(p);
-        p += sizeof(uint32_t) * kBins;
-        s.dstart = reinterpret_cast<uint32_t *>(p);
-        p += sizeof(uint32_t) * kBins;
-        s.dcount = reinterpret_cast<uint32_t *>(p);
-        p += sizeof(uint32_t) * kBins;
-        s.scan = reinterpret_cast<uint32_t *>(p);
-        p += sizeof(uint32_t) * (WARPS + 1);
-        s.wc = s.wm = nullptr;
-        if (stable) {
-            s.wc = reinterpret_cast<uint32_t *>(p);
-            p += sizeof(uint32_t) * kBins * STRIDE;
-            s.wm = reinterpret_cast<uint32_t *>(p);
-        }
-        return s;
-    }
+    static constexpr size_t kCnt = BASE;
+    static constexpr size_t kDstart = kCnt + 4 * kBins;
+    static constexpr size_t kDcount = kDstart + 4 * kBins;
+    static constexpr size_t kScan = kDcount + 4 * kBins;
+    static constexpr size_t kWc = kScan + 16 * ((4 * (WARPS + 1) + 15) / 16);
+    static constexpr size_t kWm = kWc + 16 * ((4 * kBins * STRIDE + 15) / 16);
+    static constexpr size_t kEnd = STABLE_BUFS ? kWm + 8 * WARPS * kBins : kWc;
+    __device__ static uint32_t *cnt() { return reinterpret_cast<uint32_t *>(g_dyn_smem + kCnt); }
+    __device__ static uint32_t *dstart() { return reinterpret_cast<uint32_t *>(g_dyn_smem + kDstart); }
+    __device__ static uint32_t *dcount() { return reinterpret_cast<uint32_t *>(g_dyn_smem + kDcount); }
+    __device__ static uint32_t *scan() { return reinterpret_cast<uint32_t *>(g_dyn_smem + kScan); }
+    __device__ static uint32_t *wc() { return reinterpret_cast<uint32_t *>(g_dyn_smem + kWc); }
+    __device__ static uint32_t *wm() { return reinterpret_cast<uint32_t *>(g_dyn_smem + kWm); }
 };
 
 // Rank of a tile of keys held in registers (ITEMS per thread, bit j of
@@ -195,7 +187,7 @@ struct RankSmem {
 //    a set is cleared before its next use without a third barrier); the rank
 //    is the number of lower lanes in the group plus the warp's count before
 //    the step, so equal digits keep tile order.
-template <typename K, int THREADS, int ITEMS>
+template <typename K, int THREADS, int ITEMS, typename RS>
 struct Ranker {
     static constexpr int WARPS = THREADS / 32;
     static constexpr int STRIDE = WARPS + 1;
@@ -203,8 +195,11 @@ struct Ranker {
     static_assert(THREADS >= kBins, "one thread per digit in the scans");
 
     template <bool STABLE>
-    __device__ static void rank_and_place(const K (&keys)[ITEMS], uint32_t vmask, int shift, uint32_t mask,
-                                          const RankSmem<THREADS> &s, K *out) {
+    __device__ static void rank_and_place(const K (&keys)[ITEMS], uint32_t vmask, int shift, uint32_t mask, K *out) {
+        struct {
+            uint32_t *cnt = RS::cnt(), *dstart = RS::dstart(), *dcount = RS::dcount(), *scan = RS::scan(),
+                     *wc = RS::wc(), *wm = RS::wm();
+        } s;
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         const int t = threadIdx.x;
         // rank of each item among equal digits (< TILE), two per register
@@ -354,6 +349,35 @@ __device__ __forceinline__ uint32_t striped_mask(int n_valid) {
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) m |= static_cast<uint32_t>(j * 32 < rem) << j;
     return m;
+}
+
+// Maximum / sum of one value per thread, broadcast to every thread.
+template <int THREADS>
+__device__ __forceinline__ uint32_t block_reduce_max(uint32_t v, uint32_t *tmp) {
+    constexpr int WARPS = THREADS / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = __reduce_max_sync(kFull, v);
+    if (lane == 0) tmp[warp] = v;
+    __syncthreads();
+    uint32_t r = 0;
+#pragma unroll
+    for (int w = 0; w < WARPS; ++w) r = max(r, tmp[w]);
+    __syncthreads();
+    return r;
+}
+
+template <int THREADS>
+__device__ __forceinline__ uint32_t block_reduce_sum(uint32_t v, uint32_t *tmp) {
+    constexpr int WARPS = THREADS / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = __reduce_add_sync(kFull, v);
+    if (lane == 0) tmp[warp] = v;
+    __syncthreads();
+    uint32_t r = 0;
+#pragma unroll
+    for (int w = 0; w < WARPS; ++w) r += tmp[w];
+    __syncthreads();
+    return r;
 }
 
 // AND / OR of one key per thread (key width), broadcast to every thread.
@@ -797,17 +821,18 @@ __global__ void __launch_bounds__(THREADS) k_classify(Work wk, int level) {
 // address of a run is checked against the bucket once per digit and tile.
 template <typename K, int THREADS, int ITEMS>
 __global__ void __launch_bounds__(THREADS, 2) k_scatter(Work wk, int level) {
-    using R = Ranker<K, THREADS, ITEMS>;
     using L = TileLoad<K, THREADS, ITEMS>;
-    constexpr int TILE = R::TILE;
+    constexpr int TILE = THREADS * ITEMS;
     constexpr int V = L::V;
-    extern __shared__ __align__(16) unsigned char smem[];
-    K *sm_keys = reinterpret_cast<K *>(smem);
-    unsigned long long *off = reinterpret_cast<unsigned long long *>(smem + sizeof(K) * TILE);
+    constexpr size_t kOff = sizeof(K) * TILE;
+    using RS = RankSmem<THREADS, kOff + 2 * sizeof(unsigned long long) * kBins + 16, false>;
+    using R = Ranker<K, THREADS, ITEMS, RS>;
+    K *sm_keys = reinterpret_cast<K *>(g_dyn_smem);
+    unsigned long long *off = reinterpret_cast<unsigned long long *>(g_dyn_smem + kOff);
     unsigned long long *adj = off + kBins;
     int *bad = reinterpret_cast<int *>(adj + kBins);
-    const RankSmem<THREADS> rs =
-        RankSmem<THREADS>::carve(smem + sizeof(K) * TILE + 2 * sizeof(unsigned long long) * kBins + 16, false);
+    uint32_t *const rs_dstart = RS::dstart();
+    uint32_t *const rs_dcount = RS::dcount();
     const int p = level & 1;
     if (wk.ctl->error) return;
     const uint32_t nch = wk.ctl->n_chunks[p];
@@ -840,12 +865,12 @@ __global__ void __launch_bounds__(THREADS, 2) k_scatter(Work wk, int level) {
 #pragma unroll
                 for (int j = 0; j < ITEMS; ++j) k[j] = encode_key(k[j], wk.codec);
             }
-            R::template rank_and_place<false>(k, vmask, shift, mask, rs, sm_keys);
+            R::template rank_and_place<false>(k, vmask, shift, mask, sm_keys);
             // per digit: where the tile's run goes, checked against the bucket
             for (int d = threadIdx.x; d <= static_cast<int>(mask); d += THREADS) {
-                const uint32_t cnt = rs.dcount[d];
+                const uint32_t cnt = rs_dcount[d];
                 const unsigned long long o = off[d];
-                adj[d] = o - rs.dstart[d];
+                adj[d] = o - rs_dstart[d];
                 if (cnt && (o < lo_pos || o + cnt > hi_pos)) *bad = 1;  // never write outside the bucket
                 off[d] = o + cnt;
             }
@@ -866,8 +891,8 @@ __global__ void __launch_bounds__(THREADS, 2) k_scatter(Work wk, int level) {
 
 template <typename K, int THREADS, int ITEMS>
 constexpr size_t scatter_smem() {
-    return sizeof(K) * THREADS * ITEMS + 2 * sizeof(unsigned long long) * kBins + 16 +
-           RankSmem<THREADS>::bytes(false);
+    return RankSmem<THREADS, sizeof(K) * THREADS * ITEMS + 2 * sizeof(unsigned long long) * kBins + 16,
+                    false>::kEnd;
 }
 
 // Shared-memory finish of every unit: LSD passes over the unit's varying
@@ -877,19 +902,18 @@ constexpr size_t scatter_smem() {
 // stability (input order is arbitrary); later passes keep tile order.
 template <typename K, int THREADS, int ITEMS>
 __global__ void __launch_bounds__(THREADS, 4) k_finish(Work wk) {
-    using R = Ranker<K, THREADS, ITEMS>;
     using L = TileLoad<K, THREADS, ITEMS>;
-    constexpr int TILE = R::TILE;
+    constexpr int TILE = THREADS * ITEMS;
     constexpr int V = L::V;
     constexpr int WARPS = THREADS / 32;
-    extern __shared__ __align__(16) unsigned char smem[];
-    K *sm_keys = reinterpret_cast<K *>(smem);
-    K *ta = reinterpret_cast<K *>(smem + sizeof(K) * TILE);
+    using RS = RankSmem<THREADS, sizeof(K) * (TILE + 2 * WARPS), true>;
+    using R = Ranker<K, THREADS, ITEMS, RS>;
+    K *sm_keys = reinterpret_cast<K *>(g_dyn_smem);
+    K *ta = reinterpret_cast<K *>(g_dyn_smem + sizeof(K) * TILE);
     K *to = ta + WARPS;
-    const RankSmem<THREADS> rs = RankSmem<THREADS>::carve(smem + sizeof(K) * (TILE + 2 * WARPS), true);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (wk.ctl->error) return;
-    for (int i = threadIdx.x; i < 2 * WARPS * kBins; i += THREADS) rs.wm[i] = 0;  // peer masks start clear
+    for (int i = threadIdx.x; i < 2 * WARPS * kBins; i += THREADS) RS::wm()[i] = 0;  // peer masks start clear
     const uint32_t nu = wk.ctl->n_units;
     K *__restrict__ out = static_cast<K *>(wk.keys);
     for (uint32_t u = blockIdx.x; u < nu; u += gridDim.x) {
@@ -920,18 +944,60 @@ __global__ void __launch_bounds__(THREADS, 4) k_finish(Work wk) {
         }
         const int lo = __ffsll(static_cast<long long>(v)) - 1;
         const int hi = 64 - __clzll(v);
+        if (hi - lo <= kRadixBits) {  // one pass settles the unit
+            R::template rank_and_place<false>(k, vmask, lo, (1u << (hi - lo)) - 1, sm_keys);
+            for (int i = threadIdx.x; i < len; i += THREADS) dstp[i] = decode_key(sm_keys[i], wk.codec);
+            __syncthreads();
+            continue;
+        }
+        // Three or more LSD passes: split on the top varying byte instead (MSD
+        // order, unstable), then rank each key inside its sub-bucket by direct
+        // comparison -- strict order by (key, position), so a sub-bucket's
+        // ranks are a permutation of it -- and write it to its final place.
+        // Comparison work per key is the size of its sub-bucket; when the
+        // sub-buckets are large (skewed units) LSD passes finish the unit.
         const int passes = (hi - lo + kRadixBits - 1) / kRadixBits;
-        const int width = (hi - lo + passes - 1) / passes;
-        R::template rank_and_place<false>(k, vmask, lo, (1u << min(width, hi - lo)) - 1, rs, sm_keys);
-        if (passes > 1) {
-            vmask = striped_mask<ITEMS>(len);
-            for (int ps = 1, sh = lo + width; ps < passes; ++ps, sh += width) {
-                const K *row = sm_keys + warp * 32 * ITEMS + lane;
-#pragma unroll
-                for (int j = 0; j < ITEMS; ++j) k[j] = (vmask >> j) & 1u ? row[j * 32] : K(0);
+        if (passes >= 3) {
+            const int top = hi - kRadixBits;
+            R::template rank_and_place<false>(k, vmask, top, kBins - 1, sm_keys);
+            const uint32_t c_own = RS::dcount()[threadIdx.x];
+            const uint32_t c_max = block_reduce_max<THREADS>(c_own, RS::scan());
+            const uint32_t c_sq = block_reduce_sum<THREADS>(c_own * c_own, RS::scan());
+            if (c_max <= kCmpMaxBucket && c_sq <= static_cast<uint32_t>(len) * kCmpKeysPerPass * (passes - 1)) {
+                for (int p2 = threadIdx.x; p2 < len; p2 += THREADS) {
+                    const K kp = sm_keys[p2];
+                    const uint32_t d = static_cast<uint32_t>(kp >> top) & (kBins - 1);
+                    const int s0 = static_cast<int>(RS::dstart()[d]);
+                    const int s1 = s0 + static_cast<int>(RS::dcount()[d]);
+                    int r = 0;
+                    for (int q = s0; q < s1; ++q) {
+                        const K kq = sm_keys[q];
+                        r += (kq < kp) | ((kq == kp) & (q < p2));
+                    }
+                    dstp[s0 + r] = decode_key(kp, wk.codec);
+                }
                 __syncthreads();
-                R::template rank_and_place<true>(k, vmask, sh, (1u << min(width, hi - sh)) - 1, rs, sm_keys);
+                continue;
             }
+            // skewed: reload and run the LSD passes below
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) {
+                const int idx = warp * 32 * ITEMS + j * 32 + lane;
+                k[j] = idx < len ? sm_keys[idx] : K(0);
+            }
+            vmask = striped_mask<ITEMS>(len);
+            __syncthreads();
+        }
+        // LSD passes over [lo, hi): the first needs no stability
+        const int width = (hi - lo + passes - 1) / passes;
+        R::template rank_and_place<false>(k, vmask, lo, (1u << width) - 1, sm_keys);
+        vmask = striped_mask<ITEMS>(len);
+        for (int ps = 1, sh = lo + width; ps < passes; ++ps, sh += width) {
+            const K *row = sm_keys + warp * 32 * ITEMS + lane;
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) k[j] = (vmask >> j) & 1u ? row[j * 32] : K(0);
+            __syncthreads();
+            R::template rank_and_place<true>(k, vmask, sh, (1u << min(width, hi - sh)) - 1, sm_keys);
         }
         for (int i = threadIdx.x; i < len; i += THREADS) dstp[i] = decode_key(sm_keys[i], wk.codec);
         __syncthreads();
@@ -940,7 +1006,7 @@ __global__ void __launch_bounds__(THREADS, 4) k_finish(Work wk) {
 
 template <typename K, int THREADS, int ITEMS>
 constexpr size_t finish_smem() {
-    return sizeof(K) * (THREADS * ITEMS + 2 * (THREADS / 32)) + RankSmem<THREADS>::bytes(true);
+    return RankSmem<THREADS, sizeof(K) * (THREADS * ITEMS + 2 * (THREADS / 32)), true>::kEnd;
 }
 
 template <typename K>
