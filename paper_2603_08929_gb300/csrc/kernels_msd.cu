@@ -26,8 +26,9 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 // comparison finish: largest sub-bucket, and comparisons per key one LSD pass is worth
-constexpr uint32_t kCmpMaxBucket = 128;
-constexpr uint32_t kCmpKeysPerPass = 16;
+constexpr uint32_t kCmpMaxBucket = 64;
+constexpr int kSplitBits = 12;  // finish split: up to 4096 sub-buckets per unit
+constexpr int kSplitCap = 1 << kSplitBits;
 
 template <int THREADS>
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *tmp, uint32_t &total) {
@@ -314,6 +315,16 @@ struct TileLoad {
     static constexpr int G = ITEMS / V;
     static_assert(ITEMS % V == 0, "items must be whole vectors");
 
+    // Whole window in range and 16-byte aligned: plain vector loads.
+    __device__ static void load_full(const K *__restrict__ w, K (&k)[ITEMS]) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const uint4 q = __ldcs(reinterpret_cast<const uint4 *>(w + ((warp * G + g) * 32 + lane) * V));
+            memcpy(&k[g * V], &q, 16);
+        }
+    }
+
     __device__ static uint32_t load(const K *__restrict__ src, uint64_t wstart, uint32_t lo_r, uint32_t hi_r,
                                     bool vec_ok, K (&k)[ITEMS]) {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -460,15 +471,74 @@ __global__ void k_init(Work wk, uint32_t n_chunks0, int direct_unit) {
     }
 }
 
+// Digit counts and AND/OR of the keys src[lo, hi) into the warp's
+// shared-memory row `my`.  The 16-byte-aligned middle is read as vectors,
+// U per thread in flight; a vector whose keys share one digit adds once.
+template <typename K, int THREADS, bool RAW>
+__device__ __forceinline__ void hist_range(const K *__restrict__ src, uint64_t lo, uint64_t hi, bool vec_ok,
+                                           int shift, uint32_t mask, const Codec &codec, uint32_t *my, K &a, K &o) {
+    constexpr int V = 16 / static_cast<int>(sizeof(K));
+    constexpr int U = 4;
+    auto one = [&](K key) {
+        if (RAW) key = encode_key(key, codec);
+        a &= key;
+        o |= key;
+        atomicAdd(&my[static_cast<uint32_t>(key >> shift) & mask], 1u);
+    };
+    if (!vec_ok) {  // buffer base not 16-byte aligned: scalar loads throughout
+        for (uint64_t i = lo + threadIdx.x; i < hi; i += THREADS) one(src[i]);
+        return;
+    }
+    uint64_t m0 = (lo + V - 1) / V * V;  // aligned middle [m0, m1)
+    uint64_t m1 = hi / V * V;
+    if (m0 > m1) m0 = m1 = hi;
+    // head and tail, scalar
+    for (uint64_t i = lo + threadIdx.x; i < m0; i += THREADS) one(src[i]);
+    for (uint64_t i = m1 + threadIdx.x; i < hi; i += THREADS) one(src[i]);
+    const uint4 *vec = reinterpret_cast<const uint4 *>(src + m0);
+    const uint32_t nvec = static_cast<uint32_t>((m1 - m0) / V);
+    uint32_t v = threadIdx.x;
+    for (; v + (U - 1) * THREADS < nvec; v += U * THREADS) {
+        uint4 q[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) q[u] = __ldcs(vec + v + u * THREADS);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            K kk[V];
+            memcpy(kk, &q[u], 16);
+            uint32_t d[V];
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                K key = kk[e];
+                if (RAW) key = encode_key(key, codec);
+                a &= key;
+                o |= key;
+                d[e] = static_cast<uint32_t>(key >> shift) & mask;
+            }
+            bool same = true;
+#pragma unroll
+            for (int e = 1; e < V; ++e) same &= d[e] == d[0];
+            if (same) {
+                atomicAdd(&my[d[0]], static_cast<uint32_t>(V));
+            } else {
+#pragma unroll
+                for (int e = 0; e < V; ++e) atomicAdd(&my[d[e]], 1u);
+            }
+        }
+    }
+    for (; v < nvec; v += THREADS) {
+        const uint4 q = __ldcs(vec + v);
+        K kk[V];
+        memcpy(kk, &q, 16);
+#pragma unroll
+        for (int e = 0; e < V; ++e) one(kk[e]);
+    }
+}
+
 // Per-chunk digit histogram (one shared-memory row per warp) and AND/OR.
-// Reads 16-byte vectors over the aligned window around the chunk.  A vector
-// whose keys share one digit adds once; a warp whose vectors all share one
-// digit adds once per warp (sorted and skewed inputs).
 template <typename K, int THREADS>
 __global__ void __launch_bounds__(THREADS) k_hist(Work wk, int level) {
     constexpr int WARPS = THREADS / 32;
-    constexpr int V = 16 / static_cast<int>(sizeof(K));
-    constexpr int U = 4;  // vectors in flight per thread
     __shared__ uint32_t sh[WARPS * kBins];
     __shared__ unsigned long long ta[WARPS], to[WARPS];
     const int p = level & 1;
@@ -477,7 +547,7 @@ __global__ void __launch_bounds__(THREADS) k_hist(Work wk, int level) {
         wk.ctl->n_buckets[p ^ 1] = 0;
         wk.ctl->n_chunks[p ^ 1] = 0;
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int warp = threadIdx.x >> 5;
     const uint32_t nch = wk.ctl->n_chunks[p];
     for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) {
         const Chunk ch = wk.chunks[p][c];
@@ -487,61 +557,15 @@ __global__ void __launch_bounds__(THREADS) k_hist(Work wk, int level) {
         const uint32_t mask = (1u << r_eff) - 1;
         for (int i = threadIdx.x; i < WARPS * kBins; i += THREADS) sh[i] = 0;
         __syncthreads();
-        uint32_t *my = sh + warp * kBins;
         K a = static_cast<K>(~K(0)), o = 0;
         const K *src = src_of<K>(wk, b.src);
         const bool vec_ok = b.src ? true : wk.keys_vec_ok;
-        const uint64_t lo = ch.start, hi = ch.start + ch.len;
-        const uint64_t w0 = lo - lo % V;
-        const bool raw = b.raw;
-        for (uint64_t base = w0; base < hi; base += static_cast<uint64_t>(THREADS) * V * U) {
-            K kk[U * V];
-            uint32_t vm = 0;
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const uint64_t i0 = base + static_cast<uint64_t>((u * THREADS + threadIdx.x) * V);
-                if (vec_ok && i0 >= lo && i0 + V <= hi) {
-                    const uint4 q = __ldcs(reinterpret_cast<const uint4 *>(src + i0));
-                    memcpy(&kk[u * V], &q, 16);
-                    vm |= ((1u << V) - 1) << (u * V);
-                } else {
-#pragma unroll
-                    for (int e = 0; e < V; ++e) {
-                        const uint64_t i = i0 + e;
-                        const bool ok = i >= lo && i < hi;
-                        kk[u * V + e] = ok ? src[i] : K(0);
-                        vm |= static_cast<uint32_t>(ok) << (u * V + e);
-                    }
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                uint32_t d[V];
-                bool same = true;
-#pragma unroll
-                for (int e = 0; e < V; ++e) {
-                    K key = kk[u * V + e];
-                    if (raw) key = encode_key(key, wk.codec);
-                    const bool ok = (vm >> (u * V + e)) & 1u;
-                    if (ok) {
-                        a &= key;
-                        o |= key;
-                    }
-                    d[e] = ok ? (static_cast<uint32_t>(key >> shift) & mask) : 0xffffffffu;
-                    same = same && d[e] == d[0];
-                }
-                const uint32_t d0 = __shfl_sync(kFull, d[0], 0);
-                if (__all_sync(kFull, same && d[0] == d0)) {
-                    if (lane == 0 && d0 != 0xffffffffu) atomicAdd(&my[d0], 32u * V);
-                } else if (same) {
-                    if (d[0] != 0xffffffffu) atomicAdd(&my[d[0]], static_cast<uint32_t>(V));
-                } else {
-#pragma unroll
-                    for (int e = 0; e < V; ++e)
-                        if (d[e] != 0xffffffffu) atomicAdd(&my[d[e]], 1u);
-                }
-            }
-        }
+        if (b.raw)
+            hist_range<K, THREADS, true>(src, ch.start, ch.start + ch.len, vec_ok, shift, mask, wk.codec,
+                                         sh + warp * kBins, a, o);
+        else
+            hist_range<K, THREADS, false>(src, ch.start, ch.start + ch.len, vec_ok, shift, mask, wk.codec,
+                                          sh + warp * kBins, a, o);
         __syncthreads();
         for (int d = threadIdx.x; d < kBins; d += THREADS) {
             uint32_t sum = 0;
@@ -815,84 +839,216 @@ __global__ void __launch_bounds__(THREADS) k_classify(Work wk, int level) {
     }
 }
 
-// Per chunk: digit ranking of each tile in shared memory (unstable: equal
-// digits need no order in an MSD pass), then the digit runs are written to
-// the chunk's digit offsets.  Tiles are 16-byte-aligned windows; the global
-// address of a run is checked against the bucket once per digit and tile.
+// Unstable rank of a tile by a digit of up to SPLIT_BITS bits (one CTA-wide
+// counter row of 2^SPLIT_BITS words, padded by one word per 16 so that the
+// thread scanning 16 consecutive counters hits 16 different banks), then
+// placement in digit order.  Afterwards cnt[pad(d)] is the start of digit d
+// in `out` and cnt[pad(2^bits)] the number of keys.
+__device__ __forceinline__ int split_pad(int d) { return d + (d >> 4); }
+
 template <typename K, int THREADS, int ITEMS>
+__device__ void split_rank(const K (&keys)[ITEMS], uint32_t vmask, int shift, int bits, uint32_t *cnt,
+                           uint32_t *scan_tmp, K *out) {
+    const int lane = threadIdx.x & 31;
+    const int nb = 1 << bits;                       // <= kSplitCap
+    const int e_per = nb > THREADS ? nb / THREADS : 1;  // counters per scanning thread (1..16)
+    const int owners = nb / e_per;
+    const uint32_t mask = static_cast<uint32_t>(nb - 1);
+    for (int i = threadIdx.x; i <= split_pad(nb); i += THREADS) cnt[i] = 0;
+    __syncthreads();
+    uint32_t local[(ITEMS + 1) / 2];
+#pragma unroll
+    for (int j = 0; j < (ITEMS + 1) / 2; ++j) local[j] = 0;
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        const bool valid = (vmask >> j) & 1u;
+        const int d = static_cast<int>(static_cast<uint32_t>(keys[j] >> shift) & mask);
+        const uint32_t r = valid ? atomicAdd(&cnt[split_pad(d)], 1u) : 0u;
+        local[j >> 1] |= r << ((j & 1) * 16);
+    }
+    __syncthreads();
+    const int g0 = split_pad(threadIdx.x * e_per);  // this thread's counters are contiguous after padding
+    uint32_t sum = 0;
+    if (threadIdx.x < owners)
+        for (int e = 0; e < e_per; ++e) sum += cnt[g0 + e];
+    uint32_t total;
+    uint32_t run = block_exclusive_scan<THREADS>(sum, scan_tmp, total);
+    if (threadIdx.x < owners) {
+        for (int e = 0; e < e_per; ++e) {
+            const uint32_t c = cnt[g0 + e];
+            cnt[g0 + e] = run;
+            run += c;
+        }
+    }
+    if (threadIdx.x == 0) cnt[split_pad(nb)] = total;
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        if ((vmask >> j) & 1u) {
+            const int d = static_cast<int>(static_cast<uint32_t>(keys[j] >> shift) & mask);
+            out[cnt[split_pad(d)] + ((local[j >> 1] >> ((j & 1) * 16)) & 0xffffu)] = keys[j];
+        }
+    }
+    __syncthreads();
+    (void)lane;
+}
+
+// Staging of one tile's keys: each key takes the next slot of its digit from
+// the cursor row (shared-memory atomicAdd).  FULL: every item is valid.
+// SKEW: a warp whose 32 keys share one digit takes its 32 slots with one
+// atomic (sorted and skewed inputs, where same-address atomics serialise).
+template <typename K, int ITEMS, bool FULL, bool SKEW>
+__device__ __forceinline__ void stage_keys(const K (&k)[ITEMS], uint32_t vmask, int shift, uint32_t mask,
+                                           uint32_t *cur, K *sm_keys, int cap, bool &overflow) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        const bool valid = FULL || ((vmask >> j) & 1u);
+        const uint32_t dg = static_cast<uint32_t>(k[j] >> shift) & mask;
+        uint32_t slot = 0;
+        if (SKEW) {
+            const uint32_t d0 = __shfl_sync(kFull, dg, 0);
+            if (__all_sync(kFull, valid && dg == d0)) {
+                uint32_t base = 0;
+                if (lane == 0) base = atomicAdd(&cur[d0], 32u);
+                slot = __shfl_sync(kFull, base, 0) + lane;
+            } else if (valid) {
+                slot = atomicAdd(&cur[dg], 1u);
+            }
+        } else if (valid) {
+            slot = atomicAdd(&cur[dg], 1u);
+        }
+        if (valid) {
+            overflow |= slot >= static_cast<uint32_t>(cap);
+            sm_keys[min(slot, static_cast<uint32_t>(cap - 1))] = k[j];
+        }
+    }
+}
+
+// Per chunk: the chunk's digit counts are known from the histogram pass
+// (difference of consecutive per-chunk exclusive offsets), so each key takes
+// its slot in the chunk's shared-memory staging area with one atomicAdd on
+// its digit's cursor (unstable: equal digits need no order in an MSD pass),
+// and the staged digit runs are then written to their bucket offsets, one
+// warp per run.  The whole chunk (CHUNK_TILES tiles) is staged before the
+// write-out, so runs are long and coalesced.  Every run's destination is
+// checked against the bucket before anything is written.
+template <typename K, int THREADS, int ITEMS, int CHUNK_TILES>
 __global__ void __launch_bounds__(THREADS, 2) k_scatter(Work wk, int level) {
     using L = TileLoad<K, THREADS, ITEMS>;
     constexpr int TILE = THREADS * ITEMS;
+    constexpr int CAP = TILE * CHUNK_TILES;
     constexpr int V = L::V;
-    constexpr size_t kOff = sizeof(K) * TILE;
-    using RS = RankSmem<THREADS, kOff + 2 * sizeof(unsigned long long) * kBins + 16, false>;
-    using R = Ranker<K, THREADS, ITEMS, RS>;
+    constexpr int WARPS = THREADS / 32;
     K *sm_keys = reinterpret_cast<K *>(g_dyn_smem);
-    unsigned long long *off = reinterpret_cast<unsigned long long *>(g_dyn_smem + kOff);
-    unsigned long long *adj = off + kBins;
-    int *bad = reinterpret_cast<int *>(adj + kBins);
-    uint32_t *const rs_dstart = RS::dstart();
-    uint32_t *const rs_dcount = RS::dcount();
+    unsigned long long *off = reinterpret_cast<unsigned long long *>(g_dyn_smem + sizeof(K) * CAP);
+    uint32_t *cur = reinterpret_cast<uint32_t *>(off + kBins);  // [kBins] staging cursors
+    uint32_t *sst = cur + kBins;                                 // [kBins] staging starts
+    uint32_t *scnt = sst + kBins;                                // [kBins] chunk counts
+    uint32_t *tmp = scnt + kBins;                                // [WARPS + 1]
+    int *bad = reinterpret_cast<int *>(tmp + WARPS + 1);
     const int p = level & 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (wk.ctl->error) return;
+    if (threadIdx.x == 0) *bad = 0;  // stays 0 unless a check fails (then the CTA stops)
+    __syncthreads();
     const uint32_t nch = wk.ctl->n_chunks[p];
     for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) {
         const Chunk ch = wk.chunks[p][c];
         const Bucket b = wk.buckets[p][ch.bucket];
         if (!b.scatter) continue;  // block-uniform
-        const uint64_t lo_pos = b.start, hi_pos = b.start + b.len;
         const K *__restrict__ src = src_of<K>(wk, b.src);
         K *__restrict__ dst = dst_of<K>(wk, b.src);
         const bool vec_ok = b.src ? true : wk.keys_vec_ok;
         const int r_eff = min(kRadixBits, b.h);
         const int shift = b.h - r_eff;
         const uint32_t mask = (1u << r_eff) - 1;
-        for (int d = threadIdx.x; d <= static_cast<int>(mask); d += THREADS)
-            off[d] = b.start + wk.bucket_base[static_cast<size_t>(ch.bucket) * kBins + d] +
-                     wk.hist[static_cast<size_t>(d) * wk.max_chunks + c];
-        if (threadIdx.x == 0) *bad = 0;
+        const bool next_same = c + 1 < nch && wk.chunks[p][c + 1].bucket == ch.bucket;
+        // chunk digit counts and destinations
+        const int d = threadIdx.x;
+        uint32_t n_d = 0;
+        if (d < kBins && static_cast<uint32_t>(d) <= mask) {
+            const uint32_t *bb = wk.bucket_base + static_cast<size_t>(ch.bucket) * kBins;
+            const uint32_t ex = wk.hist[static_cast<size_t>(d) * wk.max_chunks + c];
+            uint32_t ex_next;
+            if (next_same) {
+                ex_next = wk.hist[static_cast<size_t>(d) * wk.max_chunks + c + 1];
+            } else {  // last chunk of the bucket: the digit's bucket total
+                const uint32_t base_d = bb[d];
+                const uint32_t base_n = static_cast<uint32_t>(d) < mask ? bb[d + 1] : static_cast<uint32_t>(b.len);
+                ex_next = base_n - base_d;
+            }
+            n_d = ex_next - ex;
+            const unsigned long long o = b.start + bb[d] + ex;
+            off[d] = o;
+            if (n_d && o + n_d > b.start + b.len) *bad = 1;  // never write outside the bucket
+        }
         __syncthreads();
+        uint32_t total;
+        const uint32_t st = block_exclusive_scan<THREADS>(n_d, tmp, total);
+        if (d < kBins) {
+            sst[d] = st;
+            cur[d] = st;
+            scnt[d] = n_d;
+        }
+        if (total != ch.len && threadIdx.x == 0) *bad = 1;
+        __syncthreads();
+        if (*bad) {
+            if (threadIdx.x == 0) set_error(wk.ctl, kErrBounds);
+            return;  // block-uniform
+        }
+        // stage: every key takes the next slot of its digit.  The loop body
+        // is specialised per tile (block-uniform): keys still raw or already
+        // encoded, a whole aligned tile or a partial one, and -- from the
+        // chunk's known counts -- whether warps often share one digit.
         const uint64_t cend = ch.start + ch.len;
+        const bool skew = block_reduce_max<THREADS>(n_d, tmp) * 8u > ch.len;
+        bool overflow = false;
         for (uint64_t pos = ch.start; pos < cend;) {
             const uint64_t wstart = pos - pos % V;
             const uint64_t thi = min(cend, wstart + TILE);
-            const uint32_t lo_r = static_cast<uint32_t>(pos - wstart);
-            const uint32_t hi_r = static_cast<uint32_t>(thi - wstart);
-            const int nv = static_cast<int>(hi_r - lo_r);
             K k[ITEMS];
-            const uint32_t vmask = L::load(src, wstart, lo_r, hi_r, vec_ok, k);
+            const bool full = vec_ok && wstart == pos && thi - pos == static_cast<uint64_t>(TILE);
+            uint32_t vmask;
+            if (full) {
+                L::load_full(src + wstart, k);
+                vmask = (ITEMS == 32) ? 0xffffffffu : ((1u << ITEMS) - 1);
+            } else {
+                vmask = L::load(src, wstart, static_cast<uint32_t>(pos - wstart), static_cast<uint32_t>(thi - wstart),
+                                vec_ok, k);
+            }
             if (b.raw) {
 #pragma unroll
                 for (int j = 0; j < ITEMS; ++j) k[j] = encode_key(k[j], wk.codec);
             }
-            R::template rank_and_place<false>(k, vmask, shift, mask, sm_keys);
-            // per digit: where the tile's run goes, checked against the bucket
-            for (int d = threadIdx.x; d <= static_cast<int>(mask); d += THREADS) {
-                const uint32_t cnt = rs_dcount[d];
-                const unsigned long long o = off[d];
-                adj[d] = o - rs_dstart[d];
-                if (cnt && (o < lo_pos || o + cnt > hi_pos)) *bad = 1;  // never write outside the bucket
-                off[d] = o + cnt;
-            }
-            __syncthreads();
-            if (*bad) {
-                if (threadIdx.x == 0) set_error(wk.ctl, kErrBounds);
-                return;  // block-uniform
-            }
-            for (int i = threadIdx.x; i < nv; i += THREADS) {
-                const K key = sm_keys[i];
-                dst[adj[static_cast<uint32_t>(key >> shift) & mask] + i] = key;
-            }
-            __syncthreads();
+            if (full && !skew)
+                stage_keys<K, ITEMS, true, false>(k, vmask, shift, mask, cur, sm_keys, CAP, overflow);
+            else if (full)
+                stage_keys<K, ITEMS, true, true>(k, vmask, shift, mask, cur, sm_keys, CAP, overflow);
+            else
+                stage_keys<K, ITEMS, false, true>(k, vmask, shift, mask, cur, sm_keys, CAP, overflow);
             pos = thi;
         }
+        if (__syncthreads_or(overflow)) {
+            if (threadIdx.x == 0) set_error(wk.ctl, kErrBounds);
+            return;
+        }
+        // write-out: one warp per digit run
+        for (int dd = warp; dd <= static_cast<int>(mask); dd += WARPS) {
+            const uint32_t n = scnt[dd];
+            if (n == 0) continue;
+            const K *s0 = sm_keys + sst[dd];
+            K *g0 = dst + off[dd];
+            for (uint32_t i = lane; i < n; i += 32) g0[i] = s0[i];
+        }
+        __syncthreads();
     }
 }
 
-template <typename K, int THREADS, int ITEMS>
+template <typename K, int THREADS, int ITEMS, int CHUNK_TILES>
 constexpr size_t scatter_smem() {
-    return RankSmem<THREADS, sizeof(K) * THREADS * ITEMS + 2 * sizeof(unsigned long long) * kBins + 16,
-                    false>::kEnd;
+    return sizeof(K) * THREADS * ITEMS * CHUNK_TILES + sizeof(unsigned long long) * kBins +
+           sizeof(uint32_t) * (3 * kBins + THREADS / 32 + 1) + 16;
 }
 
 // Shared-memory finish of every unit: LSD passes over the unit's varying
@@ -913,7 +1069,8 @@ __global__ void __launch_bounds__(THREADS, 4) k_finish(Work wk) {
     K *to = ta + WARPS;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (wk.ctl->error) return;
-    for (int i = threadIdx.x; i < 2 * WARPS * kBins; i += THREADS) RS::wm()[i] = 0;  // peer masks start clear
+    uint32_t *const spl = RS::wc();  // the split counter row shares the stable-pass buffers
+    static_assert(RS::kEnd - RS::kWc >= sizeof(uint32_t) * (kSplitCap + kSplitCap / 16 + 1), "split row fits");
     const uint32_t nu = wk.ctl->n_units;
     K *__restrict__ out = static_cast<K *>(wk.keys);
     for (uint32_t u = blockIdx.x; u < nu; u += gridDim.x) {
@@ -944,50 +1101,52 @@ __global__ void __launch_bounds__(THREADS, 4) k_finish(Work wk) {
         }
         const int lo = __ffsll(static_cast<long long>(v)) - 1;
         const int hi = 64 - __clzll(v);
-        if (hi - lo <= kRadixBits) {  // one pass settles the unit
-            R::template rank_and_place<false>(k, vmask, lo, (1u << (hi - lo)) - 1, sm_keys);
+        // Split on the top (up to kSplitBits) varying bits: one unstable pass
+        // with a CTA-wide counter row.  If that covers every varying bit the
+        // unit is sorted (equal digits are equal keys).  Otherwise each key is
+        // ranked inside its sub-bucket (a few keys) by direct comparison --
+        // strict order by (key, position), so a sub-bucket's ranks are a
+        // permutation of it -- and written to its final place.  A unit with a
+        // large sub-bucket (skewed) is finished by LSD passes instead.
+        // split width ~ log2(len): sub-buckets of about one key, and the
+        // counter row (zeroed and scanned per unit) no larger than needed
+        const int want = max(8, 32 - __clz(len - 1));
+        const int split_bits = min(hi - lo, min(want, kSplitBits));
+        const int top = hi - split_bits;
+        split_rank<K, THREADS, ITEMS>(k, vmask, top, split_bits, spl, RS::scan(), sm_keys);
+        if (split_bits == hi - lo) {
             for (int i = threadIdx.x; i < len; i += THREADS) dstp[i] = decode_key(sm_keys[i], wk.codec);
             __syncthreads();
             continue;
         }
-        // Three or more LSD passes: split on the top varying byte instead (MSD
-        // order, unstable), then rank each key inside its sub-bucket by direct
-        // comparison -- strict order by (key, position), so a sub-bucket's
-        // ranks are a permutation of it -- and write it to its final place.
-        // Comparison work per key is the size of its sub-bucket; when the
-        // sub-buckets are large (skewed units) LSD passes finish the unit.
-        const int passes = (hi - lo + kRadixBits - 1) / kRadixBits;
-        if (passes >= 3) {
-            const int top = hi - kRadixBits;
-            R::template rank_and_place<false>(k, vmask, top, kBins - 1, sm_keys);
-            const uint32_t c_own = RS::dcount()[threadIdx.x];
-            const uint32_t c_max = block_reduce_max<THREADS>(c_own, RS::scan());
-            const uint32_t c_sq = block_reduce_sum<THREADS>(c_own * c_own, RS::scan());
-            if (c_max <= kCmpMaxBucket && c_sq <= static_cast<uint32_t>(len) * kCmpKeysPerPass * (passes - 1)) {
-                for (int p2 = threadIdx.x; p2 < len; p2 += THREADS) {
-                    const K kp = sm_keys[p2];
-                    const uint32_t d = static_cast<uint32_t>(kp >> top) & (kBins - 1);
-                    const int s0 = static_cast<int>(RS::dstart()[d]);
-                    const int s1 = s0 + static_cast<int>(RS::dcount()[d]);
-                    int r = 0;
-                    for (int q = s0; q < s1; ++q) {
-                        const K kq = sm_keys[q];
-                        r += (kq < kp) | ((kq == kp) & (q < p2));
-                    }
-                    dstp[s0 + r] = decode_key(kp, wk.codec);
-                }
-                __syncthreads();
+        bool too_big = false;
+        for (int p2 = threadIdx.x; p2 < len; p2 += THREADS) {
+            const K kp = sm_keys[p2];
+            const int d = static_cast<int>(static_cast<uint32_t>(kp >> top) & ((1u << split_bits) - 1));
+            const int s0 = static_cast<int>(spl[split_pad(d)]);
+            const int s1 = static_cast<int>(spl[split_pad(d + 1)]);
+            if (s1 - s0 > static_cast<int>(kCmpMaxBucket)) {
+                too_big = true;
                 continue;
             }
-            // skewed: reload and run the LSD passes below
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j) {
-                const int idx = warp * 32 * ITEMS + j * 32 + lane;
-                k[j] = idx < len ? sm_keys[idx] : K(0);
+            int r = 0;
+            for (int q = s0; q < s1; ++q) {
+                const K kq = sm_keys[q];
+                r += (kq < kp) | ((kq == kp) & (q < p2));
             }
-            vmask = striped_mask<ITEMS>(len);
-            __syncthreads();
+            dstp[s0 + r] = decode_key(kp, wk.codec);
         }
+        if (!__syncthreads_or(too_big)) continue;
+        // skewed unit: LSD passes from the keys as they now stand
+        const int passes = (hi - lo + kRadixBits - 1) / kRadixBits;
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            const int idx = warp * 32 * ITEMS + j * 32 + lane;
+            k[j] = idx < len ? sm_keys[idx] : K(0);
+        }
+        vmask = striped_mask<ITEMS>(len);
+        for (int i = threadIdx.x; i < 2 * WARPS * kBins; i += THREADS) RS::wm()[i] = 0;  // after the split row
+        __syncthreads();
         // LSD passes over [lo, hi): the first needs no stability
         const int width = (hi - lo + passes - 1) / passes;
         R::template rank_and_place<false>(k, vmask, lo, (1u << width) - 1, sm_keys);
@@ -1067,11 +1226,12 @@ template <typename K>
 void launch_msd(const Work &wk, cudaStream_t st, Recorder &rec, int num_sms) {
     constexpr int T = Cfg<K>::kThreads, I = Cfg<K>::kItems;
     constexpr int FT = Cfg<K>::kFinThreads, FI = Cfg<K>::kFinItems;
-    constexpr size_t kScatterSmem = scatter_smem<K, T, I>();
+    constexpr int CT = 2;  // tiles per chunk
+    constexpr size_t kScatterSmem = scatter_smem<K, T, I, CT>();
     constexpr size_t kFinishSmem = finish_smem<K, FT, FI>();
     static bool attrs = false;
     if (!attrs) {
-        cudaFuncSetAttribute(k_scatter<K, T, I>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_scatter<K, T, I, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(kScatterSmem));
         cudaFuncSetAttribute(k_finish<K, FT, FI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(kFinishSmem));
@@ -1095,7 +1255,7 @@ void launch_msd(const Work &wk, cudaStream_t st, Recorder &rec, int num_sms) {
             k_classify<kBins><<<num_sms * 4, kBins, 0, st>>>(wk, level);
             rec.end();
             rec.begin(BSORT_K_SCATTER, level);
-            k_scatter<K, T, I><<<num_sms * 2, T, kScatterSmem, st>>>(wk, level);
+            k_scatter<K, T, I, CT><<<num_sms * 2, T, kScatterSmem, st>>>(wk, level);
             rec.end();
         }
     }
