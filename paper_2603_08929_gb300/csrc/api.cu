@@ -60,7 +60,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 struct MsdLayout {
-    size_t alt, ctl, buckets0, buckets1, chunks0, chunks1, hist, cand, cor, bbase, units, fills, total;
+    size_t alt, ctl, buckets0, buckets1, chunks0, chunks1, hist, cand, cor, bbase, units, fb_units, fills, total;
     uint32_t max_buckets, max_chunks, max_units, max_fills;
 };
 
@@ -90,6 +90,7 @@ MsdLayout msd_layout(size_t n, int key_bytes) {
     L.cor = take(sizeof(uint64_t) * L.max_chunks);
     L.bbase = take(sizeof(uint32_t) * kBins * static_cast<size_t>(L.max_buckets));
     L.units = take(sizeof(Unit) * L.max_units);
+    L.fb_units = take(sizeof(Unit) * L.max_units);
     L.fills = take(sizeof(Fill) * L.max_fills);
     L.total = off;
     return L;
@@ -215,6 +216,7 @@ bsort_status run_sort(bsort_handle *h, void *keys, size_t n, const DtypeInfo &di
         wk.chunk_or = reinterpret_cast<uint64_t *>(ws + L.cor);
         wk.bucket_base = reinterpret_cast<uint32_t *>(ws + L.bbase);
         wk.units = reinterpret_cast<Unit *>(ws + L.units);
+        wk.fb_units = reinterpret_cast<Unit *>(ws + L.fb_units);
         wk.fills = reinterpret_cast<Fill *>(ws + L.fills);
         wk.keys = keys;
         wk.alt = ws + L.alt;

@@ -77,7 +77,7 @@ struct Ctl {
     uint32_t n_units;
     uint32_t n_fills;
     uint32_t error;
-    uint32_t pad;
+    uint32_t n_fb;  // units handed from the comparison finish to the LSD finish
     unsigned long long hist_keys[kMaxLevels];     // keys read by the histogram of a level
     unsigned long long scatter_keys[kMaxLevels];  // keys moved by the scatter of a level
     unsigned long long finish_keys;
@@ -95,6 +95,7 @@ struct Work {
     uint64_t *chunk_or;     // [max_chunks]
     uint32_t *bucket_base;  // [max_buckets][kBins]: digit totals, then digit bases relative to the bucket start
     Unit *units;
+    Unit *fb_units;  // [max_units] skewed units for the LSD finish
     Fill *fills;
     void *keys;
     void *alt;

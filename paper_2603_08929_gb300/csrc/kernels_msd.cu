@@ -1051,13 +1051,158 @@ constexpr size_t scatter_smem() {
            sizeof(uint32_t) * (3 * kBins + THREADS / 32 + 1) + 16;
 }
 
-// Shared-memory finish of every unit: LSD passes over the unit's varying
-// bits (bits above its highest varying bit are common to the whole run; a
-// run with no varying bit is one repeated key), then the decoded keys go to
-// their final place in the caller's buffer.  The first pass needs no
-// stability (input order is arbitrary); later passes keep tile order.
-template <typename K, int THREADS, int ITEMS>
+// Shared-memory finish of every unit, main path.  The unit's keys (at most
+// THREADS * ITEMS) are loaded warp-striped (item j of thread t is key
+// j*THREADS + t), and the varying bits of the unit (bits above its highest
+// varying bit are common to the whole run) are split on their top
+// log2(len)-ish bits in one unstable pass with a CTA-wide counter row.  If
+// that covers every varying bit the unit is sorted (equal digits are equal
+// keys).  Otherwise each key is ranked inside its sub-bucket -- a few keys
+// -- by direct comparison: strict order by (key, position), so a
+// sub-bucket's ranks are a permutation of it; the decoded key goes straight
+// to its final place.  A unit with a large sub-bucket (skewed data) is
+// handed to k_finish_lsd.  RAW: keys are still in the caller's encoding
+// (the single unit of an array that fits one tile).
+template <typename K, int THREADS, int ITEMS, bool RAW>
 __global__ void __launch_bounds__(THREADS, 4) k_finish(Work wk) {
+    constexpr int WARPS = THREADS / 32;
+    constexpr int TILE = THREADS * ITEMS;
+    K *sm_keys = reinterpret_cast<K *>(g_dyn_smem);
+    K *ta = reinterpret_cast<K *>(g_dyn_smem + sizeof(K) * TILE);
+    K *to = ta + WARPS;
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(g_dyn_smem + sizeof(K) * (TILE + 2 * WARPS));
+    uint32_t *scan_tmp = cnt + kSplitCap + kSplitCap / 16 + 4;
+    const int t = threadIdx.x;
+    if (wk.ctl->error) return;
+    const uint32_t nu = RAW ? 1u : wk.ctl->n_units;
+    K *__restrict__ out = static_cast<K *>(wk.keys);
+    for (uint32_t u = blockIdx.x; u < nu; u += gridDim.x) {
+        const Unit un = wk.units[u];
+        const K *__restrict__ src = src_of<K>(wk, un.src) + un.start;
+        K *__restrict__ dstp = out + un.start;
+        const int len = static_cast<int>(un.len);
+        const int jmax = (len + THREADS - 1) / THREADS;
+        K k[ITEMS];
+        K a = static_cast<K>(~K(0)), o = 0;
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            k[j] = 0;
+            if (j < jmax) {
+                const int idx = j * THREADS + t;
+                if (idx < len) {
+                    K key = src[idx];
+                    if (RAW) key = encode_key(key, wk.codec);
+                    k[j] = key;
+                    a &= key;
+                    o |= key;
+                }
+            }
+        }
+        block_and_or_k<K, THREADS>(a, o, ta, to);
+        const unsigned long long v = static_cast<unsigned long long>(a ^ o);
+        if (v == 0) {  // one repeated key: write it len times
+            const K val = decode_key(a, wk.codec);
+            for (int i = t; i < len; i += THREADS) dstp[i] = val;
+            continue;
+        }
+        const int lo = __ffsll(static_cast<long long>(v)) - 1;
+        const int hi = 64 - __clzll(v);
+        const int want = max(8, 32 - __clz(len - 1));
+        const int bits = min(hi - lo, min(want, kSplitBits));
+        const int top = hi - bits;
+        const int nb = 1 << bits;
+        const uint32_t dmask = static_cast<uint32_t>(nb - 1);
+        // split: count
+        for (int i = t; i <= split_pad(nb); i += THREADS) cnt[i] = 0;
+        __syncthreads();
+        uint32_t local[(ITEMS + 1) / 2];
+#pragma unroll
+        for (int j = 0; j < (ITEMS + 1) / 2; ++j) local[j] = 0;
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            if (j < jmax && j * THREADS + t < len) {
+                const int d = static_cast<int>(static_cast<uint32_t>(k[j] >> top) & dmask);
+                local[j >> 1] |= atomicAdd(&cnt[split_pad(d)], 1u) << ((j & 1) * 16);
+            }
+        }
+        __syncthreads();
+        // split: exclusive starts (thread t scans e_per consecutive counters);
+        // a sub-bucket too large for comparison ranking sends the unit to the
+        // LSD finish before anything is written
+        bool too_big = false;
+        {
+            const int e_per = nb > THREADS ? nb / THREADS : 1;
+            const int g0 = split_pad(t * e_per);
+            const bool owner = t * e_per < nb;
+            uint32_t sum = 0;
+            if (owner)
+                for (int e = 0; e < e_per; ++e) {
+                    const uint32_t c = cnt[g0 + e];
+                    sum += c;
+                    too_big |= c > kCmpMaxBucket;
+                }
+            uint32_t total;
+            uint32_t run = block_exclusive_scan<THREADS>(sum, scan_tmp, total);
+            if (owner)
+                for (int e = 0; e < e_per; ++e) {
+                    const uint32_t c = cnt[g0 + e];
+                    cnt[g0 + e] = run;
+                    run += c;
+                }
+            if (t == 0) cnt[split_pad(nb)] = total;
+        }
+        too_big = __syncthreads_or(too_big) && bits < hi - lo;
+        if (too_big) {
+            if (t == 0) {
+                const uint32_t f = atomicAdd(&wk.ctl->n_fb, 1u);
+                if (f < wk.max_units) wk.fb_units[f] = un;
+                else set_error(wk.ctl, kErrCapacity);
+            }
+            continue;
+        }
+        // split: place
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            if (j < jmax && j * THREADS + t < len) {
+                const int d = static_cast<int>(static_cast<uint32_t>(k[j] >> top) & dmask);
+                sm_keys[cnt[split_pad(d)] + ((local[j >> 1] >> ((j & 1) * 16)) & 0xffffu)] = k[j];
+            }
+        }
+        __syncthreads();
+        if (bits == hi - lo) {
+            for (int i = t; i < len; i += THREADS) dstp[i] = decode_key(sm_keys[i], wk.codec);
+            __syncthreads();
+            continue;
+        }
+        // rank inside sub-buckets by comparison, write to the final place
+        for (int p2 = t; p2 < len; p2 += THREADS) {
+            const K kp = sm_keys[p2];
+            const int d = static_cast<int>(static_cast<uint32_t>(kp >> top) & dmask);
+            const int s0 = static_cast<int>(cnt[split_pad(d)]);
+            const int s1 = static_cast<int>(cnt[split_pad(d + 1)]);
+            int r = 0;
+            for (int q = s0; q < s1; ++q) {
+                const K kq = sm_keys[q];
+                r += (kq < kp) | ((kq == kp) & (q < p2));
+            }
+            dstp[s0 + r] = decode_key(kp, wk.codec);
+        }
+        __syncthreads();
+    }
+}
+
+template <typename K, int THREADS, int ITEMS>
+constexpr size_t finish_smem() {
+    return sizeof(K) * (THREADS * ITEMS + 2 * (THREADS / 32)) +
+           sizeof(uint32_t) * (kSplitCap + kSplitCap / 16 + 4 + THREADS / 32 + 1);
+}
+
+// Finish of the units k_finish handed over (skewed: a sub-bucket too large
+// for comparison ranking): LSD passes over the unit's varying bits, the
+// first unstable (its input order is arbitrary), the later ones stable,
+// then the decoded keys go to their final place.
+template <typename K, int THREADS, int ITEMS>
+__global__ void __launch_bounds__(THREADS, 4) k_finish_lsd(Work wk) {
     using L = TileLoad<K, THREADS, ITEMS>;
     constexpr int TILE = THREADS * ITEMS;
     constexpr int V = L::V;
@@ -1069,12 +1214,11 @@ __global__ void __launch_bounds__(THREADS, 4) k_finish(Work wk) {
     K *to = ta + WARPS;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (wk.ctl->error) return;
-    uint32_t *const spl = RS::wc();  // the split counter row shares the stable-pass buffers
-    static_assert(RS::kEnd - RS::kWc >= sizeof(uint32_t) * (kSplitCap + kSplitCap / 16 + 1), "split row fits");
-    const uint32_t nu = wk.ctl->n_units;
+    for (int i = threadIdx.x; i < 2 * WARPS * kBins; i += THREADS) RS::wm()[i] = 0;  // peer masks start clear
+    const uint32_t nu = min(wk.ctl->n_fb, wk.max_units);
     K *__restrict__ out = static_cast<K *>(wk.keys);
     for (uint32_t u = blockIdx.x; u < nu; u += gridDim.x) {
-        const Unit un = wk.units[u];
+        const Unit un = wk.fb_units[u];
         const K *__restrict__ src = src_of<K>(wk, un.src);
         const bool vec_ok = un.src ? true : wk.keys_vec_ok;
         const int len = static_cast<int>(un.len);
@@ -1094,60 +1238,9 @@ __global__ void __launch_bounds__(THREADS, 4) k_finish(Work wk) {
         block_and_or_k<K, THREADS>(a, o, ta, to);
         K *__restrict__ dstp = out + un.start;
         const unsigned long long v = static_cast<unsigned long long>(a ^ o);
-        if (v == 0) {  // one repeated key: write it len times
-            const K val = decode_key(a, wk.codec);
-            for (int i = threadIdx.x; i < len; i += THREADS) dstp[i] = val;
-            continue;
-        }
-        const int lo = __ffsll(static_cast<long long>(v)) - 1;
-        const int hi = 64 - __clzll(v);
-        // Split on the top (up to kSplitBits) varying bits: one unstable pass
-        // with a CTA-wide counter row.  If that covers every varying bit the
-        // unit is sorted (equal digits are equal keys).  Otherwise each key is
-        // ranked inside its sub-bucket (a few keys) by direct comparison --
-        // strict order by (key, position), so a sub-bucket's ranks are a
-        // permutation of it -- and written to its final place.  A unit with a
-        // large sub-bucket (skewed) is finished by LSD passes instead.
-        // split width ~ log2(len): sub-buckets of about one key, and the
-        // counter row (zeroed and scanned per unit) no larger than needed
-        const int want = max(8, 32 - __clz(len - 1));
-        const int split_bits = min(hi - lo, min(want, kSplitBits));
-        const int top = hi - split_bits;
-        split_rank<K, THREADS, ITEMS>(k, vmask, top, split_bits, spl, RS::scan(), sm_keys);
-        if (split_bits == hi - lo) {
-            for (int i = threadIdx.x; i < len; i += THREADS) dstp[i] = decode_key(sm_keys[i], wk.codec);
-            __syncthreads();
-            continue;
-        }
-        bool too_big = false;
-        for (int p2 = threadIdx.x; p2 < len; p2 += THREADS) {
-            const K kp = sm_keys[p2];
-            const int d = static_cast<int>(static_cast<uint32_t>(kp >> top) & ((1u << split_bits) - 1));
-            const int s0 = static_cast<int>(spl[split_pad(d)]);
-            const int s1 = static_cast<int>(spl[split_pad(d + 1)]);
-            if (s1 - s0 > static_cast<int>(kCmpMaxBucket)) {
-                too_big = true;
-                continue;
-            }
-            int r = 0;
-            for (int q = s0; q < s1; ++q) {
-                const K kq = sm_keys[q];
-                r += (kq < kp) | ((kq == kp) & (q < p2));
-            }
-            dstp[s0 + r] = decode_key(kp, wk.codec);
-        }
-        if (!__syncthreads_or(too_big)) continue;
-        // skewed unit: LSD passes from the keys as they now stand
+        const int lo = v ? __ffsll(static_cast<long long>(v)) - 1 : 0;
+        const int hi = v ? 64 - __clzll(v) : 1;
         const int passes = (hi - lo + kRadixBits - 1) / kRadixBits;
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            const int idx = warp * 32 * ITEMS + j * 32 + lane;
-            k[j] = idx < len ? sm_keys[idx] : K(0);
-        }
-        vmask = striped_mask<ITEMS>(len);
-        for (int i = threadIdx.x; i < 2 * WARPS * kBins; i += THREADS) RS::wm()[i] = 0;  // after the split row
-        __syncthreads();
-        // LSD passes over [lo, hi): the first needs no stability
         const int width = (hi - lo + passes - 1) / passes;
         R::template rank_and_place<false>(k, vmask, lo, (1u << width) - 1, sm_keys);
         vmask = striped_mask<ITEMS>(len);
@@ -1164,7 +1257,7 @@ __global__ void __launch_bounds__(THREADS, 4) k_finish(Work wk) {
 }
 
 template <typename K, int THREADS, int ITEMS>
-constexpr size_t finish_smem() {
+constexpr size_t finish_lsd_smem() {
     return RankSmem<THREADS, sizeof(K) * (THREADS * ITEMS + 2 * (THREADS / 32)), true>::kEnd;
 }
 
@@ -1229,12 +1322,17 @@ void launch_msd(const Work &wk, cudaStream_t st, Recorder &rec, int num_sms) {
     constexpr int CT = 2;  // tiles per chunk
     constexpr size_t kScatterSmem = scatter_smem<K, T, I, CT>();
     constexpr size_t kFinishSmem = finish_smem<K, FT, FI>();
+    constexpr size_t kFinishLsdSmem = finish_lsd_smem<K, FT, FI>();
     static bool attrs = false;
     if (!attrs) {
         cudaFuncSetAttribute(k_scatter<K, T, I, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(kScatterSmem));
-        cudaFuncSetAttribute(k_finish<K, FT, FI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_finish<K, FT, FI, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(kFinishSmem));
+        cudaFuncSetAttribute(k_finish<K, FT, FI, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kFinishSmem));
+        cudaFuncSetAttribute(k_finish_lsd<K, FT, FI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kFinishLsdSmem));
         attrs = true;
     }
     const MsdShape shape = msd_shape(sizeof(K));
@@ -1260,7 +1358,11 @@ void launch_msd(const Work &wk, cudaStream_t st, Recorder &rec, int num_sms) {
         }
     }
     rec.begin(BSORT_K_FINISH, -1);
-    k_finish<K, FT, FI><<<num_sms * 4, FT, kFinishSmem, st>>>(wk);
+    if (direct)
+        k_finish<K, FT, FI, true><<<1, FT, kFinishSmem, st>>>(wk);
+    else
+        k_finish<K, FT, FI, false><<<num_sms * 4, FT, kFinishSmem, st>>>(wk);
+    k_finish_lsd<K, FT, FI><<<num_sms * 4, FT, kFinishLsdSmem, st>>>(wk);
     rec.end();
     if (!direct) {
         rec.begin(BSORT_K_FILL, -1);
