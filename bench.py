@@ -69,6 +69,27 @@ def dist_env():
     return rank, world, local
 
 
+def measured_traffic(kind, dtype, keys_per_launch):
+    """DRAM bytes per launch of kernel `kind` from the committed ncu record, or
+    None when there is no record for it or the kernel sources changed since."""
+    import glob
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_%s_traffic_%s.json" % (kind, dtype))
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        rec = json.load(fh)
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_2603_08929_gb300", "csrc", "*")))
+    files.append(os.path.join(ROOT, "include", "bsort.h"))
+    for f in files:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != rec.get("sources_sha256"):
+        return None
+    return rec["dram_bytes_per_key"] * keys_per_launch
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -296,7 +317,10 @@ def main():
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "kernel": dom_kind, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
-                     "traffic": None},
+                     "traffic": measured_traffic(
+                         dom_kind, args.dtype,
+                         dk["bytes"] / (2 * esize) / max(dk["launches"], 1)) if dom_kind in (
+                             "finish", "scatter") else None},
         "sort_roofline": {"counted_bytes_per_step": total_bytes, "achieved": sort_gbs,
                           "frac": sort_gbs / peak, "peak": peak,
                           "fixed_2nb_frac": 2 * n * esize / (ms_per_step * 1e-3) / 1e9 / peak},
