@@ -119,6 +119,47 @@ bsort_status bsort_keys_ws(bsort_handle *handle, void *keys, size_t n, bsort_dty
  */
 bsort_status bsort_keys_host(void *host_keys, size_t n, bsort_dtype dt, int descending, void *stream);
 
+/* ---- segmented and graph forms -------------------------------------------
+ *
+ * Segmented sort: the segments [d_offsets[s], d_offsets[s+1]), s <
+ * num_segments, of one keys buffer of n keys are each sorted in place and
+ * independently (the paper's functions applied to every segment).  d_offsets
+ * is a DEVICE array of num_segments + 1 uint64 offsets, non-decreasing, the
+ * last <= n; it is read on the device, and a decreasing or out-of-range
+ * offset sets the device error word (BSORT_ERR_INTERNAL via
+ * bsort_get_error), after which the call's remaining device work stops and
+ * the keys are left partly unsorted (never written outside [0, n)).  4- and
+ * 8-byte keys
+ * (1/2-byte keys: BSORT_ERR_UNSUPPORTED).  All segments run in one fixed
+ * launch sequence: segments become the initial buckets (or, up to the
+ * shared-memory finish size, finish units) of the MSD levels.
+ */
+bsort_status bsort_segmented_workspace_bytes(size_t n, size_t num_segments, bsort_dtype dt, size_t *bytes);
+bsort_status bsort_keys_segmented_ws(bsort_handle *handle, void *keys, size_t n, const uint64_t *d_offsets,
+                                     size_t num_segments, bsort_dtype dt, int descending, void *workspace,
+                                     size_t ws_bytes, void *stream);
+/* As above with the per-device default handle (workspace cached, grown with cudaMalloc). */
+bsort_status bsort_keys_segmented(void *keys, size_t n, const uint64_t *d_offsets, size_t num_segments,
+                                  bsort_dtype dt, int descending, void *stream);
+
+/*
+ * CUDA graphs of a whole sort, for callers that repeat the same sort on the
+ * same buffers: the launch sequence (with its device-side work lists) is
+ * captured once and replayed with one cudaGraphLaunch.  The graph is bound
+ * to keys / offsets / workspace; their contents may change between launches.
+ * bsort_graph_error waits for `stream` and reads the device error word of the
+ * graph's last run.
+ */
+typedef struct bsort_graph bsort_graph;
+bsort_status bsort_graph_create(bsort_handle *handle, void *keys, size_t n, bsort_dtype dt, int descending,
+                                void *workspace, size_t ws_bytes, bsort_graph **graph);
+bsort_status bsort_graph_create_segmented(bsort_handle *handle, void *keys, size_t n, const uint64_t *d_offsets,
+                                          size_t num_segments, bsort_dtype dt, int descending, void *workspace,
+                                          size_t ws_bytes, bsort_graph **graph);
+bsort_status bsort_graph_launch(bsort_graph *graph, void *stream);
+bsort_status bsort_graph_error(bsort_graph *graph, void *stream);
+bsort_status bsort_graph_destroy(bsort_graph *graph);
+
 /*
  * The paper has no counterpart of this entry point.  bsort_keys() for callers
  * that may not allocate device memory while they run -- code under CUDA

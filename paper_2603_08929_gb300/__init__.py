@@ -17,6 +17,7 @@ from . import build as _build
 
 __all__ = [
     "DTYPES", "BsortError", "lib", "bsort_keys", "bsort_keys_ws", "bsort_keys_host", "bsort_keys_noalloc",
+    "bsort_keys_segmented", "segmented_workspace_bytes", "Graph",
     "workspace_bytes", "Handle", "sort_", "status_string",
 ]
 
@@ -88,6 +89,22 @@ def lib():
         L.bsort_last_launch_count.restype = i
         L.bsort_keys_noalloc.argtypes = [vp, sz, i, i, vp]
         L.bsort_keys_noalloc.restype = i
+        L.bsort_segmented_workspace_bytes.argtypes = [sz, sz, i, ctypes.POINTER(sz)]
+        L.bsort_segmented_workspace_bytes.restype = i
+        L.bsort_keys_segmented_ws.argtypes = [vp, vp, sz, vp, sz, i, i, vp, sz, vp]
+        L.bsort_keys_segmented_ws.restype = i
+        L.bsort_keys_segmented.argtypes = [vp, sz, vp, sz, i, i, vp]
+        L.bsort_keys_segmented.restype = i
+        L.bsort_graph_create.argtypes = [vp, vp, sz, i, i, vp, sz, ctypes.POINTER(vp)]
+        L.bsort_graph_create.restype = i
+        L.bsort_graph_create_segmented.argtypes = [vp, vp, sz, vp, sz, i, i, vp, sz, ctypes.POINTER(vp)]
+        L.bsort_graph_create_segmented.restype = i
+        L.bsort_graph_launch.argtypes = [vp, vp]
+        L.bsort_graph_launch.restype = i
+        L.bsort_graph_error.argtypes = [vp, vp]
+        L.bsort_graph_error.restype = i
+        L.bsort_graph_destroy.argtypes = [vp]
+        L.bsort_graph_destroy.restype = i
         _lib = L
     return _lib
 
@@ -208,6 +225,79 @@ def bsort_keys_noalloc(keys, descending: bool = False, stream=None) -> None:
     _check(lib().bsort_keys_noalloc(ctypes.c_void_p(keys.data_ptr()), keys.numel(),
                                     _dtype_code(keys.dtype), int(bool(descending)), _stream_ptr(stream)),
            "bsort_keys_noalloc")
+
+
+def segmented_workspace_bytes(n: int, num_segments: int, dtype) -> int:
+    out = ctypes.c_size_t(0)
+    _check(lib().bsort_segmented_workspace_bytes(int(n), int(num_segments), _dtype_code(dtype), ctypes.byref(out)),
+           "bsort_segmented_workspace_bytes")
+    return int(out.value)
+
+
+def _offsets(offsets):
+    _device_tensor(offsets)
+    if offsets.element_size() != 8:
+        raise TypeError("segment offsets must be a 64-bit integer CUDA tensor")
+    return ctypes.c_void_p(offsets.data_ptr()), offsets.numel() - 1
+
+
+def bsort_keys_segmented(keys, offsets, descending: bool = False, stream=None, handle=None, workspace=None) -> None:
+    """Sorts every segment keys[offsets[s]:offsets[s+1]] in place (C ABI
+    ``bsort_keys_segmented``; with ``handle`` and ``workspace``:
+    ``bsort_keys_segmented_ws``).  ``offsets``: int64 CUDA tensor, S + 1 entries."""
+    _device_tensor(keys)
+    op, nseg = _offsets(offsets)
+    if handle is None:
+        _check(lib().bsort_keys_segmented(ctypes.c_void_p(keys.data_ptr()), keys.numel(), op, nseg,
+                                          _dtype_code(keys.dtype), int(bool(descending)), _stream_ptr(stream)),
+               "bsort_keys_segmented")
+    else:
+        _device_tensor(workspace)
+        _check(lib().bsort_keys_segmented_ws(handle.ptr, ctypes.c_void_p(keys.data_ptr()), keys.numel(), op, nseg,
+                                             _dtype_code(keys.dtype), int(bool(descending)),
+                                             ctypes.c_void_p(workspace.data_ptr()),
+                                             workspace.numel() * workspace.element_size(), _stream_ptr(stream)),
+               "bsort_keys_segmented_ws")
+
+
+class Graph:
+    """A captured CUDA graph of one sort (plain or segmented) on fixed buffers."""
+
+    def __init__(self, handle: Handle, keys, workspace, descending: bool = False, offsets=None):
+        _device_tensor(keys)
+        _device_tensor(workspace)
+        g = ctypes.c_void_p()
+        wsb = workspace.numel() * workspace.element_size()
+        if offsets is None:
+            _check(lib().bsort_graph_create(handle.ptr, ctypes.c_void_p(keys.data_ptr()), keys.numel(),
+                                            _dtype_code(keys.dtype), int(bool(descending)),
+                                            ctypes.c_void_p(workspace.data_ptr()), wsb, ctypes.byref(g)),
+                   "bsort_graph_create")
+        else:
+            op, nseg = _offsets(offsets)
+            _check(lib().bsort_graph_create_segmented(handle.ptr, ctypes.c_void_p(keys.data_ptr()), keys.numel(),
+                                                      op, nseg, _dtype_code(keys.dtype), int(bool(descending)),
+                                                      ctypes.c_void_p(workspace.data_ptr()), wsb, ctypes.byref(g)),
+                   "bsort_graph_create_segmented")
+        self._g = g
+        self._keep = (keys, workspace, offsets)
+
+    def launch(self, stream=None):
+        _check(lib().bsort_graph_launch(self._g, _stream_ptr(stream)), "bsort_graph_launch")
+
+    def error(self, stream=None) -> int:
+        return int(lib().bsort_graph_error(self._g, _stream_ptr(stream)))
+
+    def close(self):
+        if self._g:
+            lib().bsort_graph_destroy(self._g)
+            self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
 
 
 def bsort_keys_host(keys, descending: bool = False, stream=None) -> None:

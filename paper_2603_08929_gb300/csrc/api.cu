@@ -64,14 +64,14 @@ struct MsdLayout {
     uint32_t max_buckets, max_chunks, max_units, max_fills;
 };
 
-MsdLayout msd_layout(size_t n, int key_bytes) {
+MsdLayout msd_layout(size_t n, int key_bytes, size_t nseg = 0) {
     const MsdShape s = msd_shape(key_bytes);
     MsdLayout L;
     const uint64_t per_t = n / s.unit_cap + 1;
     L.max_buckets = static_cast<uint32_t>(n / (s.unit_cap + 1) + 2);
     // a bucket of len keys spans ceil((len + misalignment) / chunk) <= 1 + (len + 16) / chunk chunks
     L.max_chunks = static_cast<uint32_t>(L.max_buckets + (n + 16ull * L.max_buckets) / s.chunk + 2);
-    L.max_units = static_cast<uint32_t>((4 + 2 * static_cast<uint64_t>(s.levels)) * per_t + 16);
+    L.max_units = static_cast<uint32_t>((4 + 2 * static_cast<uint64_t>(s.levels)) * per_t + 16 + nseg);
     L.max_fills = static_cast<uint32_t>(n / kFillPiece + per_t + 16);
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -167,20 +167,66 @@ bsort_status check_args(const void *keys, size_t n, bsort_dtype dt, DtypeInfo *d
     return BSORT_OK;
 }
 
+Work make_work(const MsdLayout &L, char *ws, void *keys, size_t n, const DtypeInfo &di, const Codec &codec) {
+    const MsdShape s = msd_shape(di.bytes);
+    Work wk;
+    wk.ctl = reinterpret_cast<Ctl *>(ws + L.ctl);
+    wk.buckets[0] = reinterpret_cast<Bucket *>(ws + L.buckets0);
+    wk.buckets[1] = reinterpret_cast<Bucket *>(ws + L.buckets1);
+    wk.chunks[0] = reinterpret_cast<Chunk *>(ws + L.chunks0);
+    wk.chunks[1] = reinterpret_cast<Chunk *>(ws + L.chunks1);
+    wk.hist = reinterpret_cast<uint32_t *>(ws + L.hist);
+    wk.chunk_and = reinterpret_cast<uint64_t *>(ws + L.cand);
+    wk.chunk_or = reinterpret_cast<uint64_t *>(ws + L.cor);
+    wk.bucket_base = reinterpret_cast<uint32_t *>(ws + L.bbase);
+    wk.units = reinterpret_cast<Unit *>(ws + L.units);
+    wk.fb_units = reinterpret_cast<Unit *>(ws + L.fb_units);
+    wk.fills = reinterpret_cast<Fill *>(ws + L.fills);
+    wk.keys = keys;
+    wk.alt = ws + L.alt;
+    wk.n = n;
+    wk.codec = codec;
+    wk.max_buckets = L.max_buckets;
+    wk.max_chunks = L.max_chunks;
+    wk.max_units = L.max_units;
+    wk.max_fills = L.max_fills;
+    wk.chunk_keys = s.chunk;
+    wk.unit_cap = s.unit_cap;
+    wk.merge_cap = s.merge_cap;
+    wk.w = di.bytes * 8;
+    wk.keys_vec_ok = (reinterpret_cast<uintptr_t>(keys) & 15) == 0;
+    return wk;
+}
+
+void begin_call(bsort_handle *h, cudaStream_t st) {
+    h->rec.enabled = h->profiling;
+    h->rec.launches = 0;
+    h->rec.stream = st;
+    h->rec.active = h->profiling && h->events && h->rec.calls < BSORT_PROFILE_MAX_CALLS;
+}
+
+void end_call(bsort_handle *h, cudaStream_t st, size_t n, int key_bytes) {
+    if (h->rec.active) {
+        const int c = h->rec.calls;
+        h->prof_path[c] = h->last_path;
+        h->prof_key_bytes[c] = key_bytes;
+        h->prof_n[c] = n;
+        if (h->last_ctl) cudaMemcpyAsync(h->prof_ctl + c, h->last_ctl, sizeof(Ctl), cudaMemcpyDeviceToDevice, st);
+        ++h->rec.calls;
+    }
+}
+
 bsort_status run_sort(bsort_handle *h, void *keys, size_t n, const DtypeInfo &di, int descending,
                       void *workspace, size_t ws_bytes, cudaStream_t st) {
     (void)cudaGetLastError();  // clear a stale non-sticky error
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return BSORT_ERR_CUDA;
     const int sms = num_sms_of(dev);
-    h->rec.enabled = h->profiling;
-    h->rec.launches = 0;
-    h->rec.stream = st;
     if (h->profiling) {
         const bsort_status es = ensure_events(h);
         if (es != BSORT_OK) return es;
     }
-    h->rec.active = h->profiling && h->rec.calls < BSORT_PROFILE_MAX_CALLS;
+    begin_call(h, st);
     const Codec codec = codec_for(di, descending);
     char *ws = static_cast<char *>(workspace);
     h->last_stream = st;
@@ -204,49 +250,55 @@ bsort_status run_sort(bsort_handle *h, void *keys, size_t n, const DtypeInfo &di
     } else {
         const MsdLayout L = msd_layout(n, di.bytes);
         if (ws_bytes < L.total) return BSORT_ERR_WORKSPACE_TOO_SMALL;
-        const MsdShape s = msd_shape(di.bytes);
-        Work wk;
-        wk.ctl = reinterpret_cast<Ctl *>(ws + L.ctl);
-        wk.buckets[0] = reinterpret_cast<Bucket *>(ws + L.buckets0);
-        wk.buckets[1] = reinterpret_cast<Bucket *>(ws + L.buckets1);
-        wk.chunks[0] = reinterpret_cast<Chunk *>(ws + L.chunks0);
-        wk.chunks[1] = reinterpret_cast<Chunk *>(ws + L.chunks1);
-        wk.hist = reinterpret_cast<uint32_t *>(ws + L.hist);
-        wk.chunk_and = reinterpret_cast<uint64_t *>(ws + L.cand);
-        wk.chunk_or = reinterpret_cast<uint64_t *>(ws + L.cor);
-        wk.bucket_base = reinterpret_cast<uint32_t *>(ws + L.bbase);
-        wk.units = reinterpret_cast<Unit *>(ws + L.units);
-        wk.fb_units = reinterpret_cast<Unit *>(ws + L.fb_units);
-        wk.fills = reinterpret_cast<Fill *>(ws + L.fills);
-        wk.keys = keys;
-        wk.alt = ws + L.alt;
-        wk.n = n;
-        wk.codec = codec;
-        wk.max_buckets = L.max_buckets;
-        wk.max_chunks = L.max_chunks;
-        wk.max_units = L.max_units;
-        wk.max_fills = L.max_fills;
-        wk.chunk_keys = s.chunk;
-        wk.unit_cap = s.unit_cap;
-        wk.merge_cap = s.merge_cap;
-        wk.w = di.bytes * 8;
-        wk.keys_vec_ok = (reinterpret_cast<uintptr_t>(keys) & 15) == 0;
+        const Work wk = make_work(L, ws, keys, n, di, codec);
         if (di.bytes == 4) launch_msd<uint32_t>(wk, st, h->rec, sms);
         else launch_msd<uint64_t>(wk, st, h->rec, sms);
         h->last_path = 2;
         h->last_ctl = wk.ctl;
     }
-    if (h->rec.active) {
-        const int c = h->rec.calls;
-        h->prof_path[c] = h->last_path;
-        h->prof_key_bytes[c] = di.bytes;
-        h->prof_n[c] = n;
-        if (h->last_ctl)
-            cudaMemcpyAsync(h->prof_ctl + c, h->last_ctl, sizeof(Ctl), cudaMemcpyDeviceToDevice, st);
-        ++h->rec.calls;
-    }
+    end_call(h, st, n, di.bytes);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? BSORT_OK : BSORT_ERR_CUDA;
+}
+
+bsort_status check_segmented(const void *keys, size_t n, const uint64_t *d_offsets, size_t nseg, bsort_dtype dt,
+                             DtypeInfo *di) {
+    if (!dtype_info(dt, di)) return BSORT_ERR_INVALID_ARG;
+    if (di->bytes < 4) return BSORT_ERR_UNSUPPORTED;  // segmented 1/2-byte keys: not in this build
+    if (nseg == 0 || n == 0) return BSORT_OK;
+    if (!keys || !d_offsets) return BSORT_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(keys) % di->bytes || reinterpret_cast<uintptr_t>(d_offsets) % 8)
+        return BSORT_ERR_MISALIGNED;
+    if (n >= (1ull << 32) || nseg >= (1ull << 31)) return BSORT_ERR_UNSUPPORTED;
+    return BSORT_OK;
+}
+
+// Enqueues the segmented sort (offsets checked on the device).
+bsort_status run_segmented(bsort_handle *h, void *keys, size_t n, const uint64_t *d_offsets, size_t nseg,
+                           const DtypeInfo &di, int descending, void *workspace, size_t ws_bytes, cudaStream_t st,
+                           bool record) {
+    (void)cudaGetLastError();
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return BSORT_ERR_CUDA;
+    const int sms = num_sms_of(dev);
+    if (record && h->profiling) {
+        const bsort_status es = ensure_events(h);
+        if (es != BSORT_OK) return es;
+    }
+    begin_call(h, st);
+    if (!record) h->rec.active = false;
+    const MsdLayout L = msd_layout(n, di.bytes, nseg);
+    if (ws_bytes < L.total) return BSORT_ERR_WORKSPACE_TOO_SMALL;
+    const Work wk = make_work(L, static_cast<char *>(workspace), keys, n, di, codec_for(di, descending));
+    if (di.bytes == 4) launch_msd_segmented<uint32_t>(wk, d_offsets, static_cast<uint32_t>(nseg), st, h->rec, sms);
+    else launch_msd_segmented<uint64_t>(wk, d_offsets, static_cast<uint32_t>(nseg), st, h->rec, sms);
+    h->last_path = 2;
+    h->last_ctl = wk.ctl;
+    h->last_stream = st;
+    h->last_n = n;
+    h->last_key_bytes = di.bytes;
+    if (record) end_call(h, st, n, di.bytes);
+    return cudaGetLastError() == cudaSuccess ? BSORT_OK : BSORT_ERR_CUDA;
 }
 
 bsort_status grow(void **buf, size_t *have, size_t need) {
@@ -381,6 +433,140 @@ bsort_status bsort_keys_host(void *host_keys, size_t n, bsort_dtype dt, int desc
         if (err & kErrTimeout) return BSORT_ERR_TIMEOUT;
         if (err & kErrBounds) return BSORT_ERR_INTERNAL;
     }
+    return BSORT_OK;
+}
+
+bsort_status bsort_segmented_workspace_bytes(size_t n, size_t num_segments, bsort_dtype dt, size_t *bytes) {
+    DtypeInfo di;
+    if (!bytes || !dtype_info(dt, &di)) return BSORT_ERR_INVALID_ARG;
+    if (di.bytes < 4) return BSORT_ERR_UNSUPPORTED;
+    *bytes = msd_layout(n, di.bytes, num_segments).total;
+    return BSORT_OK;
+}
+
+bsort_status bsort_keys_segmented_ws(bsort_handle *handle, void *keys, size_t n, const uint64_t *d_offsets,
+                                     size_t num_segments, bsort_dtype dt, int descending, void *workspace,
+                                     size_t ws_bytes, void *stream) {
+    if (!handle) return BSORT_ERR_INVALID_ARG;
+    DtypeInfo di;
+    const bsort_status st = check_segmented(keys, n, d_offsets, num_segments, dt, &di);
+    if (st != BSORT_OK || num_segments == 0 || n == 0) return st;
+    if (!workspace) return BSORT_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(workspace) % kAlign) return BSORT_ERR_MISALIGNED;
+    std::lock_guard<std::mutex> lk(handle->mu);
+    return run_segmented(handle, keys, n, d_offsets, num_segments, di, descending, workspace, ws_bytes,
+                         static_cast<cudaStream_t>(stream), true);
+}
+
+bsort_status bsort_keys_segmented(void *keys, size_t n, const uint64_t *d_offsets, size_t num_segments,
+                                  bsort_dtype dt, int descending, void *stream) {
+    DtypeInfo di;
+    const bsort_status st = check_segmented(keys, n, d_offsets, num_segments, dt, &di);
+    if (st != BSORT_OK || num_segments == 0 || n == 0) return st;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return BSORT_ERR_CUDA;
+    bsort_handle *h = default_handle(dev);
+    if (!h) return BSORT_ERR_NO_MEMORY;
+    std::lock_guard<std::mutex> lk(h->mu);
+    const bsort_status gs = grow(&h->ws, &h->ws_bytes, msd_layout(n, di.bytes, num_segments).total);
+    if (gs != BSORT_OK) return gs;
+    return run_segmented(h, keys, n, d_offsets, num_segments, di, descending, h->ws, h->ws_bytes,
+                         static_cast<cudaStream_t>(stream), true);
+}
+
+struct bsort_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    Ctl *ctl = nullptr;
+};
+
+namespace {
+// Captures one sort (plain: d_offsets == NULL) into an executable graph.
+bsort_status capture(bsort_handle *h, void *keys, size_t n, const uint64_t *d_offsets, size_t nseg,
+                     const DtypeInfo &di, int descending, void *ws, size_t ws_bytes, bsort_graph **out) {
+    if (di.bytes == 4) msd_prepare<uint32_t>();
+    else if (di.bytes == 8) msd_prepare<uint64_t>();
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return BSORT_ERR_CUDA;
+    bsort_graph *g = new (std::nothrow) bsort_graph();
+    if (!g) {
+        cudaStreamDestroy(cs);
+        return BSORT_ERR_NO_MEMORY;
+    }
+    bsort_status st = BSORT_OK;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = BSORT_ERR_CUDA;
+    if (st == BSORT_OK) {
+        const bool prof = h->profiling;
+        h->profiling = false;
+        st = d_offsets ? run_segmented(h, keys, n, d_offsets, nseg, di, descending, ws, ws_bytes, cs, false)
+                       : run_sort(h, keys, n, di, descending, ws, ws_bytes, cs);
+        h->profiling = prof;
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(cs, &graph);
+        if (st == BSORT_OK && e != cudaSuccess) st = BSORT_ERR_CUDA;
+        g->graph = graph;
+        if (st == BSORT_OK && cudaGraphInstantiate(&g->exec, graph, 0) != cudaSuccess) st = BSORT_ERR_CUDA;
+    }
+    g->ctl = h->last_ctl;
+    cudaStreamDestroy(cs);
+    if (st != BSORT_OK) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        delete g;
+        (void)cudaGetLastError();
+        return st;
+    }
+    *out = g;
+    return BSORT_OK;
+}
+}  // namespace
+
+bsort_status bsort_graph_create(bsort_handle *handle, void *keys, size_t n, bsort_dtype dt, int descending,
+                                void *workspace, size_t ws_bytes, bsort_graph **graph) {
+    if (!handle || !graph) return BSORT_ERR_INVALID_ARG;
+    DtypeInfo di;
+    const bsort_status st = check_args(keys, n, dt, &di);
+    if (st != BSORT_OK) return st;
+    if (n <= 1 || !workspace) return BSORT_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(handle->mu);
+    return capture(handle, keys, n, nullptr, 0, di, descending, workspace, ws_bytes, graph);
+}
+
+bsort_status bsort_graph_create_segmented(bsort_handle *handle, void *keys, size_t n, const uint64_t *d_offsets,
+                                          size_t num_segments, bsort_dtype dt, int descending, void *workspace,
+                                          size_t ws_bytes, bsort_graph **graph) {
+    if (!handle || !graph) return BSORT_ERR_INVALID_ARG;
+    DtypeInfo di;
+    const bsort_status st = check_segmented(keys, n, d_offsets, num_segments, dt, &di);
+    if (st != BSORT_OK) return st;
+    if (num_segments == 0 || n == 0 || !workspace) return BSORT_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(handle->mu);
+    return capture(handle, keys, n, d_offsets, num_segments, di, descending, workspace, ws_bytes, graph);
+}
+
+bsort_status bsort_graph_launch(bsort_graph *graph, void *stream) {
+    if (!graph || !graph->exec) return BSORT_ERR_INVALID_ARG;
+    return cudaGraphLaunch(graph->exec, static_cast<cudaStream_t>(stream)) == cudaSuccess ? BSORT_OK
+                                                                                          : BSORT_ERR_CUDA;
+}
+
+bsort_status bsort_graph_error(bsort_graph *graph, void *stream) {
+    if (!graph) return BSORT_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return BSORT_ERR_CUDA;
+    if (!graph->ctl) return BSORT_OK;
+    uint32_t err = 0;
+    if (cudaMemcpy(&err, &graph->ctl->error, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return BSORT_ERR_CUDA;
+    if (err & kErrCapacity) return BSORT_ERR_CAPACITY;
+    if (err & kErrTimeout) return BSORT_ERR_TIMEOUT;
+    if (err & kErrBounds) return BSORT_ERR_INTERNAL;
+    return BSORT_OK;
+}
+
+bsort_status bsort_graph_destroy(bsort_graph *graph) {
+    if (!graph) return BSORT_ERR_INVALID_ARG;
+    if (graph->exec) cudaGraphExecDestroy(graph->exec);
+    if (graph->graph) cudaGraphDestroy(graph->graph);
+    delete graph;
     return BSORT_OK;
 }
 

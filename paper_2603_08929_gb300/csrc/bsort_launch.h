@@ -58,6 +58,16 @@ MsdShape msd_shape(int key_bytes);
 template <typename K>
 void launch_msd(const Work &wk, cudaStream_t st, Recorder &rec, int num_sms);
 
+// Segmented form: segments [off[s], off[s+1]) (device offsets) are sorted
+// independently in one launch sequence.
+template <typename K>
+void launch_msd_segmented(const Work &wk, const uint64_t *d_offsets, uint32_t nseg, cudaStream_t st, Recorder &rec,
+                          int num_sms);
+
+// Sets kernel attributes (call before stream capture).
+template <typename K>
+void msd_prepare();
+
 // Counting sort of 1- or 2-byte keys: histogram of all key bits, bin starts,
 // and a write-only fill of the output.  Scratch comes from `ws`.
 struct CountWork {

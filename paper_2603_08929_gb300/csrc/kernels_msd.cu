@@ -471,6 +471,74 @@ __global__ void k_init(Work wk, uint32_t n_chunks0, int direct_unit) {
     }
 }
 
+// Clears the work lists and counters.
+__global__ void k_zero_ctl(Work wk) {
+    uint32_t *words = reinterpret_cast<uint32_t *>(wk.ctl);
+    for (size_t i = threadIdx.x; i < sizeof(Ctl) / 4; i += blockDim.x) words[i] = 0;
+}
+
+// Segmented sort: every segment [off[s], off[s+1]) of the keys buffer becomes
+// an initial bucket (more than unit_cap keys) or finish unit (2..unit_cap
+// keys); segments of 0 or 1 key are already sorted.  Offsets that decrease
+// or pass n set the bounds error and the segment is skipped.
+__global__ void k_seg_init(Work wk, const uint64_t *__restrict__ off, uint32_t nseg) {
+    const uint64_t vk = 128u / static_cast<uint32_t>(wk.w);
+    for (uint32_t sg = blockIdx.x * blockDim.x + threadIdx.x; sg < nseg; sg += gridDim.x * blockDim.x) {
+        const uint64_t a = off[sg], b = off[sg + 1];
+        if (b < a || b > wk.n) {
+            set_error(wk.ctl, kErrBounds);
+            continue;
+        }
+        const uint64_t len = b - a;
+        if (len <= 1) continue;
+        if (len <= wk.unit_cap) {
+            const uint32_t u = atomicAdd(&wk.ctl->n_units, 1u);
+            if (u >= wk.max_units) {
+                set_error(wk.ctl, kErrCapacity);
+                continue;
+            }
+            atomicAdd(&wk.ctl->finish_keys, static_cast<unsigned long long>(len));
+            Unit un;
+            un.start = a;
+            un.len = static_cast<uint32_t>(len);
+            un.src = 0;
+            un.raw = 1;
+            un.pad[0] = un.pad[1] = 0;
+            wk.units[u] = un;
+            continue;
+        }
+        const uint64_t abase = a - a % vk;
+        const uint32_t nch = static_cast<uint32_t>((b - abase + wk.chunk_keys - 1) / wk.chunk_keys);
+        const uint32_t bi = atomicAdd(&wk.ctl->n_buckets[0], 1u);
+        const uint32_t c0 = atomicAdd(&wk.ctl->n_chunks[0], nch);
+        if (bi >= wk.max_buckets || c0 + nch > wk.max_chunks) {
+            set_error(wk.ctl, kErrCapacity);
+            continue;
+        }
+        Bucket bk;
+        bk.start = a;
+        bk.len = len;
+        bk.first_chunk = c0;
+        bk.num_chunks = nch;
+        bk.h = wk.w;
+        bk.src = 0;
+        bk.raw = 1;
+        bk.scatter = 0;
+        bk.pad = 0;
+        wk.buckets[0][bi] = bk;
+        for (uint32_t i = 0; i < nch; ++i) {
+            const uint64_t cs = i == 0 ? a : abase + static_cast<uint64_t>(i) * wk.chunk_keys;
+            const uint64_t cl = abase + static_cast<uint64_t>(i + 1) * wk.chunk_keys;
+            const uint64_t ce = cl < b ? cl : b;
+            Chunk ch;
+            ch.start = cs;
+            ch.len = static_cast<uint32_t>(ce - cs);
+            ch.bucket = bi;
+            wk.chunks[0][c0 + i] = ch;
+        }
+    }
+}
+
 // Digit counts and AND/OR of the keys src[lo, hi) into the warp's
 // shared-memory row `my`.  The 16-byte-aligned middle is read as vectors,
 // U per thread in flight; a vector whose keys share one digit adds once.
@@ -1061,9 +1129,9 @@ constexpr size_t scatter_smem() {
 // -- by direct comparison: strict order by (key, position), so a
 // sub-bucket's ranks are a permutation of it; the decoded key goes straight
 // to its final place.  A unit with a large sub-bucket (skewed data) is
-// handed to k_finish_lsd.  RAW: keys are still in the caller's encoding
-// (the single unit of an array that fits one tile).
-template <typename K, int THREADS, int ITEMS, bool RAW>
+// handed to k_finish_lsd.  A unit marked raw still holds the caller's
+// encoding (an array or segment that fits one tile).
+template <typename K, int THREADS, int ITEMS>
 __global__ void __launch_bounds__(THREADS, 4) k_finish(Work wk) {
     constexpr int WARPS = THREADS / 32;
     constexpr int TILE = THREADS * ITEMS;
@@ -1074,10 +1142,11 @@ __global__ void __launch_bounds__(THREADS, 4) k_finish(Work wk) {
     uint32_t *scan_tmp = cnt + kSplitCap + kSplitCap / 16 + 4;
     const int t = threadIdx.x;
     if (wk.ctl->error) return;
-    const uint32_t nu = RAW ? 1u : wk.ctl->n_units;
+    const uint32_t nu = min(wk.ctl->n_units, wk.max_units);
     K *__restrict__ out = static_cast<K *>(wk.keys);
     for (uint32_t u = blockIdx.x; u < nu; u += gridDim.x) {
         const Unit un = wk.units[u];
+        const bool raw = un.raw;
         const K *__restrict__ src = src_of<K>(wk, un.src) + un.start;
         K *__restrict__ dstp = out + un.start;
         const int len = static_cast<int>(un.len);
@@ -1091,7 +1160,7 @@ __global__ void __launch_bounds__(THREADS, 4) k_finish(Work wk) {
                 const int idx = j * THREADS + t;
                 if (idx < len) {
                     K key = src[idx];
-                    if (RAW) key = encode_key(key, wk.codec);
+                    if (raw) key = encode_key(key, wk.codec);
                     k[j] = key;
                     a &= key;
                     o |= key;
@@ -1316,32 +1385,29 @@ MsdShape msd_shape(int key_bytes) {
 }
 
 template <typename K>
-void launch_msd(const Work &wk, cudaStream_t st, Recorder &rec, int num_sms) {
+void msd_prepare() {
+    constexpr int T = Cfg<K>::kThreads, I = Cfg<K>::kItems;
+    constexpr int FT = Cfg<K>::kFinThreads, FI = Cfg<K>::kFinItems;
+    static bool attrs = false;
+    if (!attrs) {
+        cudaFuncSetAttribute(k_scatter<K, T, I, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(scatter_smem<K, T, I, 2>()));
+        cudaFuncSetAttribute(k_finish<K, FT, FI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(finish_smem<K, FT, FI>()));
+        cudaFuncSetAttribute(k_finish_lsd<K, FT, FI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(finish_lsd_smem<K, FT, FI>()));
+        attrs = true;
+    }
+}
+
+// The MSD levels, the finish and the fills, after the level-0 lists exist.
+template <typename K>
+void msd_levels_and_finish(const Work &wk, cudaStream_t st, Recorder &rec, int num_sms, bool levels) {
     constexpr int T = Cfg<K>::kThreads, I = Cfg<K>::kItems;
     constexpr int FT = Cfg<K>::kFinThreads, FI = Cfg<K>::kFinItems;
     constexpr int CT = 2;  // tiles per chunk
-    constexpr size_t kScatterSmem = scatter_smem<K, T, I, CT>();
-    constexpr size_t kFinishSmem = finish_smem<K, FT, FI>();
-    constexpr size_t kFinishLsdSmem = finish_lsd_smem<K, FT, FI>();
-    static bool attrs = false;
-    if (!attrs) {
-        cudaFuncSetAttribute(k_scatter<K, T, I, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(kScatterSmem));
-        cudaFuncSetAttribute(k_finish<K, FT, FI, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(kFinishSmem));
-        cudaFuncSetAttribute(k_finish<K, FT, FI, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(kFinishSmem));
-        cudaFuncSetAttribute(k_finish_lsd<K, FT, FI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(kFinishLsdSmem));
-        attrs = true;
-    }
     const MsdShape shape = msd_shape(sizeof(K));
-    const bool direct = wk.n <= shape.unit_cap;
-    const uint32_t nc0 = direct ? 0u : static_cast<uint32_t>((wk.n + wk.chunk_keys - 1) / wk.chunk_keys);
-    rec.begin(BSORT_K_INIT, -1);
-    k_init<<<direct ? 1 : max(1u, min(1024u, (nc0 + 255) / 256)), 256, 0, st>>>(wk, nc0, direct ? 1 : 0);
-    rec.end();
-    if (!direct) {
+    if (levels) {
         for (int level = 0; level < shape.levels; ++level) {
             rec.begin(BSORT_K_HIST, level);
             k_hist<K, 512><<<num_sms * 4, 512, 0, st>>>(wk, level);
@@ -1353,24 +1419,49 @@ void launch_msd(const Work &wk, cudaStream_t st, Recorder &rec, int num_sms) {
             k_classify<kBins><<<num_sms * 4, kBins, 0, st>>>(wk, level);
             rec.end();
             rec.begin(BSORT_K_SCATTER, level);
-            k_scatter<K, T, I, CT><<<num_sms * 2, T, kScatterSmem, st>>>(wk, level);
+            k_scatter<K, T, I, CT><<<num_sms * 2, T, scatter_smem<K, T, I, CT>(), st>>>(wk, level);
             rec.end();
         }
     }
     rec.begin(BSORT_K_FINISH, -1);
-    if (direct)
-        k_finish<K, FT, FI, true><<<1, FT, kFinishSmem, st>>>(wk);
-    else
-        k_finish<K, FT, FI, false><<<num_sms * 4, FT, kFinishSmem, st>>>(wk);
-    k_finish_lsd<K, FT, FI><<<num_sms * 4, FT, kFinishLsdSmem, st>>>(wk);
+    k_finish<K, FT, FI><<<num_sms * 8, FT, finish_smem<K, FT, FI>(), st>>>(wk);
+    k_finish_lsd<K, FT, FI><<<num_sms * 4, FT, finish_lsd_smem<K, FT, FI>(), st>>>(wk);
     rec.end();
-    if (!direct) {
+    if (levels) {
         rec.begin(BSORT_K_FILL, -1);
         k_fill<K><<<num_sms * 2, 256, 0, st>>>(wk);
         rec.end();
     }
 }
 
+template <typename K>
+void launch_msd(const Work &wk, cudaStream_t st, Recorder &rec, int num_sms) {
+    msd_prepare<K>();
+    const MsdShape shape = msd_shape(sizeof(K));
+    const bool direct = wk.n <= shape.unit_cap;
+    const uint32_t nc0 = direct ? 0u : static_cast<uint32_t>((wk.n + wk.chunk_keys - 1) / wk.chunk_keys);
+    rec.begin(BSORT_K_INIT, -1);
+    k_init<<<direct ? 1 : max(1u, min(1024u, (nc0 + 255) / 256)), 256, 0, st>>>(wk, nc0, direct ? 1 : 0);
+    rec.end();
+    msd_levels_and_finish<K>(wk, st, rec, num_sms, !direct);
+}
+
+template <typename K>
+void launch_msd_segmented(const Work &wk, const uint64_t *d_offsets, uint32_t nseg, cudaStream_t st, Recorder &rec,
+                          int num_sms) {
+    msd_prepare<K>();
+    rec.begin(BSORT_K_INIT, -1);
+    k_zero_ctl<<<1, 256, 0, st>>>(wk);
+    k_seg_init<<<max(1u, min(static_cast<uint32_t>(num_sms) * 4, (nseg + 255) / 256)), 256, 0, st>>>(wk, d_offsets,
+                                                                                                      nseg);
+    rec.end();
+    msd_levels_and_finish<K>(wk, st, rec, num_sms, true);
+}
+
+template void msd_prepare<uint32_t>();
+template void msd_prepare<uint64_t>();
+template void launch_msd_segmented<uint32_t>(const Work &, const uint64_t *, uint32_t, cudaStream_t, Recorder &, int);
+template void launch_msd_segmented<uint64_t>(const Work &, const uint64_t *, uint32_t, cudaStream_t, Recorder &, int);
 template void launch_msd<uint32_t>(const Work &, cudaStream_t, Recorder &, int);
 template void launch_msd<uint64_t>(const Work &, cudaStream_t, Recorder &, int);
 
