@@ -51,10 +51,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="bsort", choices=["bsort", "reference"])
-    ap.add_argument("--mode", default="plain", choices=["plain", "segmented"],
+    ap.add_argument("--mode", default="plain", choices=["plain", "segmented", "serve"],
                     help="plain: one 2^log2n array; segmented: the batched workload (see run_segmented)")
     ap.add_argument("--segments", type=int, default=10000, help="segments per dtype (segmented mode)")
     ap.add_argument("--seg-max-log2", type=int, default=20, help="segment sizes floor(2^(k*u)), u uniform")
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrivals per second (serve mode)")
+    ap.add_argument("--serve-seconds", type=float, default=60.0, help="length of the arrival trace (serve mode)")
+    ap.add_argument("--serve-budget-gb", type=float, default=64.0, help="HBM admission budget (serve mode)")
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--no-fifo", action="store_true", help="serve mode: skip the one-slot FIFO arm")
     ap.add_argument("--dtype", default="int32")
     ap.add_argument("--dist", default="uniform")
     ap.add_argument("--log2n", type=int, default=28)
@@ -308,6 +313,101 @@ def run_segmented(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_serve(args, rank, world):
+    """Served workload: an open-loop Poisson trace (args.serve_rate requests/s
+    for args.serve_seconds; sizes log-uniform in [2^10, 2^24]; int16 25%,
+    int32 35%, float32 30%, float64 10%; uniform or normal(0, 1) values) sent
+    to the continuous-batching server under an HBM budget.  Each request's
+    payload is copied from a device-resident pool into a fresh buffer just
+    before submission (the request's arrival).  Latency is the server's
+    submit-to-completion time.  The same trace then goes through a one-slot,
+    one-request-at-a-time server (a plain FIFO queue) for comparison."""
+    import torch
+    import paper_2603_08929_gb300 as bs
+    from paper_2603_08929_gb300 import build as B
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    B.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    tr = W.serve_trace(args.seed + rank, args.serve_rate, args.serve_seconds)
+    count = len(tr["t"])
+    pool_n = 1 << 24
+    pool = {}
+    for d, name in enumerate(W.SERVE_DTYPES):
+        for k, dist in enumerate(("uniform", "normal01")):
+            pool[d, k] = torch.from_numpy(W.make(dist, name, pool_n, seed=args.seed + 7)).to(dev)
+    offs = (W.uniform01(args.seed + rank, 0xF11, count) * (pool_n - tr["n"] + 1)).astype(np.int64) & ~7
+    producer = torch.cuda.Stream()
+    torch.cuda.synchronize()
+
+    def serve(num_slots, max_batch, batch_keys, seconds):
+        srv = bs.Server(num_slots=num_slots, hbm_budget_bytes=int(args.serve_budget_gb * (1 << 30)),
+                        max_request_keys=pool_n, max_batch=max_batch, batch_keys=batch_keys)
+        last = int(np.searchsorted(tr["t"], seconds))
+        lat, wait, done_keys = [], [], 0
+        first_submit, last_done = None, 0
+        t0 = time.perf_counter()
+        i = 0
+        while i < last or len(lat) < last:
+            now = time.perf_counter() - t0
+            if i < last and now >= tr["t"][i]:
+                n = int(tr["n"][i])
+                src = pool[int(tr["dtype"][i]), int(tr["dist"][i])]
+                with torch.cuda.stream(producer):
+                    buf = torch.empty(n, dtype=src.dtype, device=dev)
+                    buf.copy_(src[int(offs[i]):int(offs[i]) + n])
+                producer.synchronize()
+                srv.submit(buf, tag=i)
+                i += 1
+                continue
+            comps = srv.poll()
+            for c in comps:
+                if c["status"] != 0:
+                    raise RuntimeError("request %d failed with status %d" % (c["tag"], c["status"]))
+                lat.append((c["t_done_ns"] - c["t_submit_ns"]) * 1e-6)
+                wait.append((c["t_admit_ns"] - c["t_submit_ns"]) * 1e-6)
+                done_keys += int(tr["n"][c["tag"]])
+                first_submit = c["t_submit_ns"] if first_submit is None else min(first_submit, c["t_submit_ns"])
+                last_done = max(last_done, c["t_done_ns"])
+            if not comps:
+                nxt = tr["t"][i] - (time.perf_counter() - t0) if i < last else 1e-4
+                time.sleep(min(max(nxt, 0.0), 1e-4))
+        st = srv.stats()
+        srv.close()
+        span = (last_done - first_submit) * 1e-9
+        lat = np.array(lat)
+        return {"requests": last, "keys": done_keys, "seconds": span, "value": done_keys / span / 1e9,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
+                "queue_p99_ms": float(np.percentile(np.array(wait), 99)),
+                "batches": st["batches"], "max_concurrent_slots": st["max_concurrent_slots"],
+                "peak_in_flight_gb": st["peak_in_flight_bytes"] / 1e9, "launches": st["launches"]}
+
+    serve(args.serve_slots, 16, 1 << 20, min(2.0, args.serve_seconds))  # warm-up
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    main_arm = serve(args.serve_slots, 16, 1 << 20, args.serve_seconds)
+    clock_info = clocks.stop()
+    fifo = None if args.no_fifo else serve(1, 1, 1, args.serve_seconds)
+    line = {
+        "metric": METRIC, "value": main_arm["value"], "unit": UNIT, "n_gpus": world, "steps": main_arm["requests"],
+        "warmup": 1, "ms_per_step": main_arm["mean_ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "i16+i32+f32+f64", "data": "synthetic",
+        "config": {"workload": "served sorting: Poisson %.0f requests/s for %.0f s, sizes log-uniform in "
+                               "[2^10, 2^24], int16 25%% / int32 35%% / float32 30%% / float64 10%%, uniform "
+                               "or normal(0, 1) values, %.0f GB HBM budget, %d slots"
+                               % (args.serve_rate, args.serve_seconds, args.serve_budget_gb, args.serve_slots),
+                   "l2": "each request sorts a fresh copy of a window of a 2^24-key device pool"},
+        "serve": main_arm,
+        "fifo_one_slot": fifo,
+        "gpu_launches": main_arm["launches"],
+        "note": "value = keys completed / (last completion - first submission): under an open-loop trace "
+                "it tracks the offered load; p50/p99 are submit-to-completion latencies",
+    }
+    if clock_info:
+        line["clocks"] = clock_info
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -316,6 +416,9 @@ def main():
         return
     if args.mode == "segmented":
         run_segmented(args, rank, world)
+        return
+    if args.mode == "serve":
+        run_serve(args, rank, world)
         return
     import torch
     import paper_2603_08929_gb300 as bs

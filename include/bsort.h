@@ -160,6 +160,56 @@ bsort_status bsort_graph_launch(bsort_graph *graph, void *stream);
 bsort_status bsort_graph_error(bsort_graph *graph, void *stream);
 bsort_status bsort_graph_destroy(bsort_graph *graph);
 
+/* ---- serving: continuous batching of sort requests ------------------------
+ *
+ * A server owns num_slots slots (a CUDA stream, a handle and a workspace of
+ * the largest request each) and a scheduler thread.  Requests queue in
+ * arrival order; the oldest waiting request is admitted when a slot is free
+ * and the HBM budget -- payload bytes plus the workspace a standalone sort of
+ * the request needs, summed over admitted requests -- has room (a request is
+ * always admitted when nothing else is in flight).  A slot takes up to
+ * max_batch requests at once while their keys stay <= batch_keys.  Requests
+ * in different slots overlap on the device.  Each request is sorted in place
+ * by the plain sort, so its result is the same alone and in the mix.
+ * Timestamps are host steady-clock nanoseconds.  The caller keeps each
+ * request's device buffer alive, and does not touch it, until its completion
+ * is polled.
+ */
+typedef struct bsort_server bsort_server;
+typedef struct {
+    int32_t num_slots;          /* 1..64 */
+    int32_t max_batch;          /* requests a slot takes at once, 1..4096 */
+    size_t hbm_budget_bytes;    /* admission budget */
+    size_t max_request_keys;    /* largest request accepted (sizes the slot workspaces) */
+    size_t batch_keys;          /* a slot batches requests while their total keys stay <= this */
+} bsort_server_config;
+typedef struct {
+    uint64_t tag;
+    int32_t status;             /* bsort_status of this request's sort */
+    int32_t slot;
+    uint64_t t_submit_ns, t_admit_ns, t_done_ns;
+} bsort_completion;
+typedef struct {
+    uint64_t submitted, completed, batches, pending;
+    size_t in_flight_bytes, peak_in_flight_bytes;
+    int32_t max_concurrent_slots;
+    int32_t pad;
+    size_t slot_workspace_bytes;
+    uint64_t launches;          /* kernel launches (and memsets) enqueued so far */
+} bsort_server_info;
+bsort_status bsort_server_create(const bsort_server_config *cfg, bsort_server **server);
+/* Queues a request (non-blocking).  n > max_request_keys: BSORT_ERR_UNSUPPORTED. */
+bsort_status bsort_server_submit(bsort_server *server, void *keys, size_t n, bsort_dtype dt, int descending,
+                                 uint64_t tag);
+/* Moves up to max completions into out; *count = how many. */
+bsort_status bsort_server_poll(bsort_server *server, bsort_completion *out, size_t max, size_t *count);
+bsort_status bsort_server_stats(bsort_server *server, bsort_server_info *out);
+/* Waits until every submitted request has completed (BSORT_ERR_TIMEOUT after timeout_s). */
+bsort_status bsort_server_drain(bsort_server *server, double timeout_s);
+/* paused != 0: admit nothing new (slots in flight still complete); 0: resume. */
+bsort_status bsort_server_pause(bsort_server *server, int paused);
+bsort_status bsort_server_destroy(bsort_server *server);
+
 /*
  * The paper has no counterpart of this entry point.  bsort_keys() for callers
  * that may not allocate device memory while they run -- code under CUDA

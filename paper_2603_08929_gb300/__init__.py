@@ -17,7 +17,7 @@ from . import build as _build
 
 __all__ = [
     "DTYPES", "BsortError", "lib", "bsort_keys", "bsort_keys_ws", "bsort_keys_host", "bsort_keys_noalloc",
-    "bsort_keys_segmented", "segmented_workspace_bytes", "Graph",
+    "bsort_keys_segmented", "segmented_workspace_bytes", "Graph", "Server",
     "workspace_bytes", "Handle", "sort_", "status_string",
 ]
 
@@ -44,6 +44,23 @@ class _Profile(ctypes.Structure):
     _fields_ = [("num_records", ctypes.c_int32), ("num_calls", ctypes.c_int32),
                 ("num_launches", ctypes.c_int32), ("pad", ctypes.c_int32),
                 ("rec", _Record * _PROFILE_MAX)]
+
+
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("num_slots", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_size_t),
+                ("max_request_keys", ctypes.c_size_t), ("batch_keys", ctypes.c_size_t)]
+
+
+class _Completion(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int32), ("slot", ctypes.c_int32),
+                ("t_submit_ns", ctypes.c_uint64), ("t_admit_ns", ctypes.c_uint64), ("t_done_ns", ctypes.c_uint64)]
+
+
+class _ServerInfo(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("pending", ctypes.c_uint64), ("in_flight_bytes", ctypes.c_size_t),
+                ("peak_in_flight_bytes", ctypes.c_size_t), ("max_concurrent_slots", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("slot_workspace_bytes", ctypes.c_size_t), ("launches", ctypes.c_uint64)]
 
 
 class BsortError(RuntimeError):
@@ -105,6 +122,20 @@ def lib():
         L.bsort_graph_error.restype = i
         L.bsort_graph_destroy.argtypes = [vp]
         L.bsort_graph_destroy.restype = i
+        L.bsort_server_create.argtypes = [ctypes.POINTER(_ServerConfig), ctypes.POINTER(vp)]
+        L.bsort_server_create.restype = i
+        L.bsort_server_submit.argtypes = [vp, vp, sz, i, i, ctypes.c_uint64]
+        L.bsort_server_submit.restype = i
+        L.bsort_server_poll.argtypes = [vp, ctypes.POINTER(_Completion), sz, ctypes.POINTER(sz)]
+        L.bsort_server_poll.restype = i
+        L.bsort_server_stats.argtypes = [vp, ctypes.POINTER(_ServerInfo)]
+        L.bsort_server_stats.restype = i
+        L.bsort_server_drain.argtypes = [vp, ctypes.c_double]
+        L.bsort_server_drain.restype = i
+        L.bsort_server_pause.argtypes = [vp, i]
+        L.bsort_server_pause.restype = i
+        L.bsort_server_destroy.argtypes = [vp]
+        L.bsort_server_destroy.restype = i
         _lib = L
     return _lib
 
@@ -292,6 +323,63 @@ class Graph:
         if self._g:
             lib().bsort_graph_destroy(self._g)
             self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+
+class Server:
+    """Continuous-batching sort server (C ABI ``bsort_server_*``).  ``submit``
+    keeps a reference to each request's tensor until its completion is polled."""
+
+    def __init__(self, num_slots: int = 8, hbm_budget_bytes: int = 64 << 30, max_request_keys: int = 1 << 24,
+                 max_batch: int = 8, batch_keys: int = 1 << 20):
+        cfg = _ServerConfig(num_slots, max_batch, hbm_budget_bytes, max_request_keys, batch_keys)
+        srv = ctypes.c_void_p()
+        _check(lib().bsort_server_create(ctypes.byref(cfg), ctypes.byref(srv)), "bsort_server_create")
+        self._s = srv
+        self._live = {}
+        self._buf = (_Completion * 4096)()
+
+    def submit(self, keys, descending: bool = False, tag: int = 0) -> None:
+        _device_tensor(keys)
+        self._live[int(tag)] = keys
+        _check(lib().bsort_server_submit(self._s, ctypes.c_void_p(keys.data_ptr()), keys.numel(),
+                                         _dtype_code(keys.dtype), int(bool(descending)), int(tag)),
+               "bsort_server_submit")
+
+    def poll(self) -> list:
+        out = []
+        while True:
+            cnt = ctypes.c_size_t(0)
+            _check(lib().bsort_server_poll(self._s, self._buf, len(self._buf), ctypes.byref(cnt)),
+                   "bsort_server_poll")
+            for c in self._buf[: cnt.value]:
+                self._live.pop(int(c.tag), None)
+                out.append({"tag": int(c.tag), "status": int(c.status), "slot": int(c.slot),
+                            "t_submit_ns": int(c.t_submit_ns), "t_admit_ns": int(c.t_admit_ns),
+                            "t_done_ns": int(c.t_done_ns)})
+            if cnt.value < len(self._buf):
+                return out
+
+    def stats(self) -> dict:
+        info = _ServerInfo()
+        _check(lib().bsort_server_stats(self._s, ctypes.byref(info)), "bsort_server_stats")
+        return {f: int(getattr(info, f)) for f, _ in _ServerInfo._fields_ if f != "pad"}
+
+    def pause(self, paused: bool = True) -> None:
+        _check(lib().bsort_server_pause(self._s, int(bool(paused))), "bsort_server_pause")
+
+    def drain(self, timeout_s: float = 60.0) -> None:
+        _check(lib().bsort_server_drain(self._s, float(timeout_s)), "bsort_server_drain")
+
+    def close(self):
+        if self._s:
+            lib().bsort_server_destroy(self._s)
+            self._s = None
 
     def __del__(self):
         try:

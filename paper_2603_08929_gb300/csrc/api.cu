@@ -3,6 +3,7 @@
 // keys).  Every step of the sort runs in the library's own kernels.
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <new>
 
@@ -124,14 +125,14 @@ CountLayout count_layout(size_t n, int key_bytes) {
 }
 
 int num_sms_of(int device) {
-    static int cache[64] = {0};
+    static std::atomic<int> cache[64];
     if (device < 0 || device >= 64) return 148;
-    if (!cache[device]) {
-        int v = 0;
+    int v = cache[device].load(std::memory_order_relaxed);
+    if (!v) {
         if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || v <= 0) v = 148;
-        cache[device] = v;
+        cache[device].store(v, std::memory_order_relaxed);
     }
-    return cache[device];
+    return v;
 }
 
 std::mutex g_default_mu;
@@ -608,7 +609,7 @@ bsort_status bsort_handle_get_profile(bsort_handle *handle, bsort_profile *out) 
     std::memset(out, 0, sizeof(*out));
     if (cudaDeviceSynchronize() != cudaSuccess) return BSORT_ERR_CUDA;
     const int ncalls = handle->rec.calls;
-    static Ctl ctls[BSORT_PROFILE_MAX_CALLS];
+    Ctl ctls[BSORT_PROFILE_MAX_CALLS];
     if (ncalls > 0 && handle->prof_ctl &&
         cudaMemcpy(ctls, handle->prof_ctl, sizeof(Ctl) * ncalls, cudaMemcpyDeviceToHost) != cudaSuccess)
         return BSORT_ERR_CUDA;

@@ -270,11 +270,11 @@ void launch_count8(const CountWork &cw, cudaStream_t st, Recorder &rec, int num_
 }
 
 void launch_count16(const CountWork &cw, cudaStream_t st, Recorder &rec, int num_sms) {
-    static bool attr_set = false;
-    if (!attr_set) {
+    static const bool attr_set = [] {  // once per process; thread-safe static initialisation
         cudaFuncSetAttribute(k_count_hist16, cudaFuncAttributeMaxDynamicSharedMemorySize, 32768 * 4);
-        attr_set = true;
-    }
+        return true;
+    }();
+    (void)attr_set;
     rec.begin(BSORT_K_COUNT_HIST, -1);
     unsigned long long *corr = cw.hist;  // corrections accumulate in place, the reduce overwrites
     cudaMemsetAsync(corr, 0, 65536 * sizeof(unsigned long long), st);

@@ -1388,16 +1388,16 @@ template <typename K>
 void msd_prepare() {
     constexpr int T = Cfg<K>::kThreads, I = Cfg<K>::kItems;
     constexpr int FT = Cfg<K>::kFinThreads, FI = Cfg<K>::kFinItems;
-    static bool attrs = false;
-    if (!attrs) {
+    static const bool attrs = [] {  // once per process; thread-safe static initialisation
         cudaFuncSetAttribute(k_scatter<K, T, I, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(scatter_smem<K, T, I, 2>()));
         cudaFuncSetAttribute(k_finish<K, FT, FI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(finish_smem<K, FT, FI>()));
         cudaFuncSetAttribute(k_finish_lsd<K, FT, FI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(finish_lsd_smem<K, FT, FI>()));
-        attrs = true;
-    }
+        return true;
+    }();
+    (void)attrs;
 }
 
 // The MSD levels, the finish and the fills, after the level-0 lists exist.

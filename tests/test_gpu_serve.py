@@ -1,0 +1,84 @@
+"""The serving loop: every request's result equals the same request sorted
+alone, requests overlap on the device, and admission respects the budget."""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_util import assert_bit_exact, to_device
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    from paper_2603_08929_gb300 import build as b
+    b.build()
+    torch.cuda.set_device(0)
+
+
+def request_mix(count, seed):
+    rng = np.random.default_rng(seed)
+    dts = rng.choice(["int16", "int32", "float32", "float64"], size=count, p=[0.25, 0.35, 0.3, 0.1])
+    sizes = np.floor(2.0 ** (10 + 10 * rng.random(count))).astype(np.int64)
+    reqs = []
+    for i, (dt, n) in enumerate(zip(dts, sizes)):
+        dist = "normal" if i % 2 else "uniform"
+        reqs.append((W.make(dist, dt, int(n), seed=seed * 1000 + i), bool(i % 3 == 0)))
+    return reqs
+
+
+def test_same_alone_and_in_the_mix():
+    import torch
+    import paper_2603_08929_gb300 as bs
+    reqs = request_mix(120, 1)
+    alone = []
+    for x, desc in reqs:  # each request alone, plain sort
+        t = to_device(x)
+        bs.bsort_keys(t, descending=desc)
+        alone.append(t.cpu().numpy())
+    torch.cuda.synchronize()
+    srv = bs.Server(num_slots=6, max_request_keys=1 << 20, max_batch=4, batch_keys=1 << 14)
+    bufs = [to_device(x) for x, _ in reqs]
+    torch.cuda.synchronize()
+    srv.pause(True)  # queue everything first so that batching and overlap are deterministic
+    for i, (b, (_, desc)) in enumerate(zip(bufs, reqs)):
+        srv.submit(b, descending=desc, tag=i)
+    assert srv.stats()["pending"] == len(reqs)
+    srv.pause(False)
+    srv.drain(120)
+    done = srv.poll()
+    assert sorted(c["tag"] for c in done) == list(range(len(reqs)))
+    assert all(c["status"] == 0 for c in done)
+    for c in done:
+        assert c["t_submit_ns"] <= c["t_admit_ns"] <= c["t_done_ns"]
+    for i, b in enumerate(bufs):
+        assert_bit_exact(b.cpu().numpy(), alone[i], "request %d" % i)
+    st = srv.stats()
+    assert st["max_concurrent_slots"] > 1  # requests overlapped on the device
+    assert st["batches"] < len(reqs)       # small requests shared slots
+    srv.close()
+
+
+def test_budget_limits_requests_in_flight():
+    import torch
+    import paper_2603_08929_gb300 as bs
+    n = 1 << 20
+    ws = bs.workspace_bytes(n, "int32")
+    budget = 2 * (4 * n + ws) + 1  # room for two such requests
+    srv = bs.Server(num_slots=8, hbm_budget_bytes=budget, max_request_keys=n, max_batch=1)
+    xs = [W.make("uniform", "int32", n, seed=50 + i) for i in range(8)]
+    bufs = [to_device(x) for x in xs]
+    torch.cuda.synchronize()
+    for i, b in enumerate(bufs):
+        srv.submit(b, tag=i)
+    srv.drain(60)
+    assert len(srv.poll()) == 8
+    st = srv.stats()
+    assert st["peak_in_flight_bytes"] <= budget
+    assert st["max_concurrent_slots"] <= 2
+    for x, b in zip(xs, bufs):
+        assert np.array_equal(b.cpu().numpy(), np.sort(x))
+    with pytest.raises(bs.BsortError):
+        srv.submit(to_device(np.zeros(n + 1, np.int32)))  # beyond max_request_keys
+    srv.close()

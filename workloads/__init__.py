@@ -27,6 +27,8 @@ Table II's types and give no distribution; these stand in for them):
   reverse    `sorted` reversed
   float_edge floats only: 90% normal(0, 1e3), 2% +-0, 2% subnormal, 2% +-inf,
              4% NaN (half quiet, half signalling, random sign and payload)
+  normal01   normal(0, 1) by Box-Muller, rounded like `normal` (integers
+             collapse onto a handful of values near 0)
 """
 from __future__ import annotations
 
@@ -40,7 +42,7 @@ _M2 = np.uint64(0x94D049BB133111EB)
 
 DTYPES = ["uint8", "int8", "uint16", "int16", "float16", "uint32", "int32", "float32",
           "uint64", "int64", "float64"]
-DISTS = ["uniform", "zipf", "normal", "distinct8", "sorted", "reverse", "float_edge"]
+DISTS = ["uniform", "zipf", "normal", "distinct8", "sorted", "reverse", "float_edge", "normal01"]
 
 _UINT = {1: np.uint8, 2: np.uint16, 4: np.uint32, 8: np.uint64}
 _CHUNK = 1 << 22
@@ -133,6 +135,8 @@ def make(dist: str, dtype, n: int, seed: int = 0) -> np.ndarray:
         return x if dist == "sorted" else x[::-1].copy()
     if dist == "normal":
         return _round_to(normal(seed, stream_id(dist, name), n, 0.0, 1e3), dtype)
+    if dist == "normal01":
+        return _round_to(normal(seed, stream_id(dist, name), n, 0.0, 1.0), dtype)
     if dist == "distinct8":
         vals = _distinct_patterns(seed, stream_id(dist, name, 1), 8, dtype)
         pick = (words(seed, stream_id(dist, name, 2), 0, n) >> np.uint64(61)).astype(np.int64)
@@ -191,3 +195,25 @@ def segment_sizes(seed: int, count: int, max_log2: int = 20, min_size: int = 1,
     """Log-uniform sizes floor(2^(max_log2 * u)), at least ``min_size``."""
     u = uniform01(seed, stream, count)
     return np.maximum(np.floor(2.0 ** (max_log2 * u)).astype(np.int64), min_size)
+
+
+SERVE_DTYPES = ("int16", "int32", "float32", "float64")
+SERVE_MIX = (0.25, 0.35, 0.30, 0.10)
+
+
+def serve_trace(seed: int, rate: float, seconds: float, lo_log2: int = 10, hi_log2: int = 24,
+                stream: int = 0xF10) -> dict:
+    """An open-loop request trace: Poisson arrivals at ``rate`` per second over
+    ``seconds``; sizes floor(2^(lo + (hi - lo) u)); dtype drawn from
+    SERVE_DTYPES with probabilities SERVE_MIX; values "uniform" or "normal01"
+    with equal probability.  Arrays: t (arrival, s), n, dtype (index into
+    SERVE_DTYPES), dist (0 uniform, 1 normal01)."""
+    count = int(rate * seconds * 1.5) + 64
+    u = uniform01(seed, stream, 4 * count).reshape(count, 4)
+    gaps = -np.log(1.0 - u[:, 0]) / rate
+    t = np.cumsum(gaps)
+    keep = t < seconds
+    n = np.floor(2.0 ** (lo_log2 + (hi_log2 - lo_log2) * u[:, 1])).astype(np.int64)
+    dt = np.searchsorted(np.cumsum(SERVE_MIX), u[:, 2], side="right").clip(0, len(SERVE_DTYPES) - 1)
+    dist = (u[:, 3] >= 0.5).astype(np.int64)
+    return {"t": t[keep], "n": n[keep], "dtype": dt[keep], "dist": dist[keep]}
