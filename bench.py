@@ -531,6 +531,7 @@ def main():
                         "gbs": v["bytes"] / (v["ms"] * 1e-3) / 1e9 if v["ms"] > 0 else 0.0,
                         "launches_per_step": v["launches"] / args.steps}
                     for k, v in sorted(per_kind.items())},
+        "finish_units_per_step": {k: v / args.steps for k, v in prof["finish_units"].items()},
         "sorted_check": ok_sorted,
     }
     if clock_info:

@@ -277,6 +277,9 @@ typedef struct {
     int32_t num_calls;       /* calls covered by the records */
     int32_t num_launches;    /* kernels launched by those calls */
     int32_t pad;
+    /* shared-memory finish units of those calls, by method: one counting pass,
+     * split + comparison ranks, LSD passes */
+    uint64_t finish_units_counting, finish_units_compare, finish_units_lsd;
     bsort_profile_record rec[BSORT_PROFILE_MAX];
 } bsort_profile;
 

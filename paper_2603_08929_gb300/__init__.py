@@ -43,7 +43,8 @@ class _Record(ctypes.Structure):
 class _Profile(ctypes.Structure):
     _fields_ = [("num_records", ctypes.c_int32), ("num_calls", ctypes.c_int32),
                 ("num_launches", ctypes.c_int32), ("pad", ctypes.c_int32),
-                ("rec", _Record * _PROFILE_MAX)]
+                ("finish_units_counting", ctypes.c_uint64), ("finish_units_compare", ctypes.c_uint64),
+                ("finish_units_lsd", ctypes.c_uint64), ("rec", _Record * _PROFILE_MAX)]
 
 
 class _ServerConfig(ctypes.Structure):
@@ -230,7 +231,9 @@ class Handle:
             recs.append({"kind": KERNEL_KINDS[r.kind], "level": int(r.level), "call": int(r.call),
                          "ms": float(r.ms), "keys": int(r.keys),
                          "counted_bytes": int(r.counted_bytes)})
-        return {"calls": int(p.num_calls), "launches": int(p.num_launches), "records": recs}
+        return {"calls": int(p.num_calls), "launches": int(p.num_launches), "records": recs,
+                "finish_units": {"counting": int(p.finish_units_counting), "compare": int(p.finish_units_compare),
+                                 "lsd": int(p.finish_units_lsd)}}
 
     def get_error(self, stream=None) -> int:
         return int(lib().bsort_get_error(self._h, _stream_ptr(stream)))

@@ -615,6 +615,11 @@ bsort_status bsort_handle_get_profile(bsort_handle *handle, bsort_profile *out) 
         return BSORT_ERR_CUDA;
     out->num_calls = ncalls;
     out->num_launches = handle->rec.held_launches;
+    for (int c = 0; c < ncalls; ++c) {
+        out->finish_units_counting += ctls[c].fin_counting;
+        out->finish_units_compare += ctls[c].fin_compare;
+        out->finish_units_lsd += ctls[c].n_fb;
+    }
     const int nrec = handle->rec.count;
     for (int i = 0; i < nrec; ++i) {
         bsort_profile_record &r = out->rec[i];

@@ -83,6 +83,7 @@ struct Ctl {
     unsigned long long finish_keys;
     unsigned long long fill_keys;
     unsigned long long raw_reads;                 // keys read while still raw (diagnostic)
+    unsigned long long fin_counting, fin_compare; // finish units by method (diagnostic)
 };
 
 // Everything a launch needs, passed by value.

@@ -1119,27 +1119,71 @@ constexpr size_t scatter_smem() {
            sizeof(uint32_t) * (3 * kBins + THREADS / 32 + 1) + 16;
 }
 
-// Shared-memory finish of every unit, main path.  The unit's keys (at most
-// THREADS * ITEMS) are loaded warp-striped (item j of thread t is key
-// j*THREADS + t), and the varying bits of the unit (bits above its highest
-// varying bit are common to the whole run) are split on their top
-// log2(len)-ish bits in one unstable pass with a CTA-wide counter row.  If
-// that covers every varying bit the unit is sorted (equal digits are equal
-// keys).  Otherwise each key is ranked inside its sub-bucket -- a few keys
-// -- by direct comparison: strict order by (key, position), so a
-// sub-bucket's ranks are a permutation of it; the decoded key goes straight
-// to its final place.  A unit with a large sub-bucket (skewed data) is
-// handed to k_finish_lsd.  A unit marked raw still holds the caller's
-// encoding (an array or segment that fits one tile).
+// Shared-memory layout of k_finish.  Two alternatives share the first region:
+//   counting path: words[sb] (u64: sixteen 4-bit counters, one per value of
+//                  the unit's low 4 varying bits, in sub-bucket sb of the bits
+//                  above), totals[sb] and starts[sb] (u16), and the output
+//                  staging buffer over the words once positions are known;
+//   compare path:  keys[TILE] then the split counters cnt[split_pad(d)].
+// The per-warp AND/OR slots and the scan scratch follow the shared region.
+template <typename K, int THREADS, int ITEMS>
+struct FinLayout {
+    static constexpr int WARPS = THREADS / 32;
+    static constexpr int V = 16 / static_cast<int>(sizeof(K));
+    static constexpr size_t kTile = static_cast<size_t>(THREADS) * ITEMS;
+    static constexpr size_t kPadded = kSplitCap + kSplitCap / 16 + 4;
+    static constexpr size_t kWords = 0;                           // u64[kSplitCap]
+    static constexpr size_t kTotals = kWords + 8 * kSplitCap;     // u16[kSplitCap]
+    static constexpr size_t kStarts = kTotals + 2 * kSplitCap;    // u16[kSplitCap]
+    static constexpr size_t kNibEnd = kStarts + 2 * kSplitCap;
+    static constexpr size_t kStage = kWords;                      // K[kTile + V]
+    static constexpr size_t kCnt = sizeof(K) * kTile;
+    static constexpr size_t kCmpEnd = kCnt + 4 * kPadded;
+    static constexpr size_t kShared = ((kNibEnd > kCmpEnd ? kNibEnd : kCmpEnd) + 15) & ~size_t(15);
+    static constexpr size_t kTa = kShared;
+    static constexpr size_t kTo = kTa + sizeof(K) * WARPS;
+    static constexpr size_t kScan = kTo + sizeof(K) * WARPS;
+    static constexpr size_t kEnd = kScan + 4 * (WARPS + 1);
+    static_assert(sizeof(K) * (kTile + V) <= kTotals, "staging overlaps only the counter words");
+    static_assert(kSplitCap == 16 * THREADS, "the scan gives each thread 16 sub-buckets");
+};
+
+// Sum of the sixteen 4-bit counters of (x, y): bytes hold at most 4 * 15.
+__device__ __forceinline__ uint32_t nib_sum(uint32_t x, uint32_t y) {
+    constexpr uint32_t m = 0x0F0F0F0Fu;
+    const uint32_t b = (x & m) + ((x >> 4) & m) + (y & m) + ((y >> 4) & m);
+    return (b * 0x01010101u) >> 24;
+}
+
+// Sorts every unit in shared memory and writes it, decoded, to its final
+// place.  With at most 16 varying bits (and enough keys to fill the
+// sub-buckets) one counting pass finishes the unit: the bits above the low 4
+// select a sub-bucket, a 4-bit counter per (sub-bucket, low value) gives each
+// key its arrival rank, and a scan over the sub-bucket totals plus the
+// counters below the key's low value give its position -- the full
+// remaining-bit counting sort, which is exact because keys with equal bits are
+// identical.  Otherwise (more varying bits, or 16 equal keys overflowing a
+// counter) the unit is split on its top log2(len)-ish varying bits in one
+// unstable pass, and each key is ranked inside its sub-bucket -- a few keys --
+// by comparison: strict order by (key, position), so a sub-bucket's ranks are
+// a permutation of it.  A unit whose sub-buckets are too large for that goes
+// to k_finish_lsd before anything is written.  Keys are loaded warp-striped
+// (item j of thread t is key j*THREADS + t); a unit marked raw still holds the
+// caller's encoding (an array or segment that fits one tile).
 template <typename K, int THREADS, int ITEMS>
 __global__ void __launch_bounds__(THREADS, 4) k_finish(Work wk) {
-    constexpr int WARPS = THREADS / 32;
-    constexpr int TILE = THREADS * ITEMS;
+    using FL = FinLayout<K, THREADS, ITEMS>;
     K *sm_keys = reinterpret_cast<K *>(g_dyn_smem);
-    K *ta = reinterpret_cast<K *>(g_dyn_smem + sizeof(K) * TILE);
-    K *to = ta + WARPS;
-    uint32_t *cnt = reinterpret_cast<uint32_t *>(g_dyn_smem + sizeof(K) * (TILE + 2 * WARPS));
-    uint32_t *scan_tmp = cnt + kSplitCap + kSplitCap / 16 + 4;
+    K *ta = reinterpret_cast<K *>(g_dyn_smem + FL::kTa);
+    K *to = reinterpret_cast<K *>(g_dyn_smem + FL::kTo);
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(g_dyn_smem + FL::kCnt);
+    uint32_t *scan_tmp = reinterpret_cast<uint32_t *>(g_dyn_smem + FL::kScan);
+    uint64_t *words = reinterpret_cast<uint64_t *>(g_dyn_smem + FL::kWords);
+    uint32_t *w32 = reinterpret_cast<uint32_t *>(g_dyn_smem + FL::kWords);
+    uint32_t *tot32 = reinterpret_cast<uint32_t *>(g_dyn_smem + FL::kTotals);
+    uint32_t *st32 = reinterpret_cast<uint32_t *>(g_dyn_smem + FL::kStarts);
+    const uint16_t *st16 = reinterpret_cast<const uint16_t *>(g_dyn_smem + FL::kStarts);
+    K *stage = reinterpret_cast<K *>(g_dyn_smem + FL::kStage);
     const int t = threadIdx.x;
     if (wk.ctl->error) return;
     const uint32_t nu = min(wk.ctl->n_units, wk.max_units);
@@ -1151,20 +1195,22 @@ __global__ void __launch_bounds__(THREADS, 4) k_finish(Work wk) {
         K *__restrict__ dstp = out + un.start;
         const int len = static_cast<int>(un.len);
         const int jmax = (len + THREADS - 1) / THREADS;
+        // bit j: item j (key j*THREADS + t) exists
+        const int rem = len - t;
+        uint32_t vm = 0;
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) vm |= static_cast<uint32_t>(j * THREADS < rem) << j;
         K k[ITEMS];
         K a = static_cast<K>(~K(0)), o = 0;
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) {
             k[j] = 0;
-            if (j < jmax) {
-                const int idx = j * THREADS + t;
-                if (idx < len) {
-                    K key = src[idx];
-                    if (raw) key = encode_key(key, wk.codec);
-                    k[j] = key;
-                    a &= key;
-                    o |= key;
-                }
+            if ((vm >> j) & 1u) {
+                K key = src[j * THREADS + t];
+                if (raw) key = encode_key(key, wk.codec);
+                k[j] = key;
+                a &= key;
+                o |= key;
             }
         }
         block_and_or_k<K, THREADS>(a, o, ta, to);
@@ -1176,8 +1222,123 @@ __global__ void __launch_bounds__(THREADS, 4) k_finish(Work wk) {
         }
         const int lo = __ffsll(static_cast<long long>(v)) - 1;
         const int hi = 64 - __clzll(v);
+        const int span = hi - lo;
+        const int lbits = span < 4 ? span : 4;
+        const int sbits = span - lbits;
+        if (span <= kSplitBits + 4 && (1 << sbits) <= 4 * len) {
+            // counting path: count (every table entry is cleared and scanned:
+            // 16 sub-buckets per thread, unused ones stay zero)
+            {
+                uint4 *z = reinterpret_cast<uint4 *>(g_dyn_smem + FL::kWords);
+                for (int i = t; i < (10 * kSplitCap) / 16; i += THREADS) z[i] = make_uint4(0, 0, 0, 0);
+            }
+            __syncthreads();
+            const uint32_t fmask = (1u << span) - 1u, lmask = (1u << lbits) - 1u;
+            uint32_t arr[(ITEMS + 7) / 8];
+#pragma unroll
+            for (int j = 0; j < (ITEMS + 7) / 8; ++j) arr[j] = 0;
+            bool ovf = false;
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) {
+                if ((vm >> j) & 1u) {
+                    const uint32_t f = static_cast<uint32_t>(k[j] >> lo) & fmask;
+                    const uint32_t low = f & lmask, sb = f >> lbits;
+                    const int sh = 4 * static_cast<int>(low & 7u);
+                    const uint32_t old = atomicAdd(&w32[2 * sb + (low >> 3)], 1u << sh);
+                    atomicAdd(&tot32[sb >> 1], 1u << (16 * (sb & 1u)));
+                    const uint32_t r = (old >> sh) & 15u;
+                    ovf |= r == 15u;  // the 16th equal key: its counter wraps
+                    arr[j >> 3] |= r << (4 * (j & 7));
+                }
+            }
+            if (!__syncthreads_or(ovf)) {
+                // sub-bucket starts: thread t owns sub-buckets [16t, 16t + 16)
+                {
+                    const uint4 *tv = reinterpret_cast<const uint4 *>(tot32) + 2 * t;
+                    const uint4 q0 = tv[0], q1 = tv[1];
+                    const uint32_t c[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+                    uint32_t sum = 0;
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) sum += (c[e] & 0xffffu) + (c[e] >> 16);
+                    uint32_t total;
+                    uint32_t run = block_exclusive_scan<THREADS>(sum, scan_tmp, total);
+                    uint32_t o[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const uint32_t s0 = run;
+                        run += c[e] & 0xffffu;
+                        o[e] = s0 | (run << 16);
+                        run += c[e] >> 16;
+                    }
+                    uint4 *sv = reinterpret_cast<uint4 *>(st32) + 2 * t;
+                    sv[0] = make_uint4(o[0], o[1], o[2], o[3]);
+                    sv[1] = make_uint4(o[4], o[5], o[6], o[7]);
+                }
+                __syncthreads();
+                // positions: sub-bucket start + keys of lower low values + arrival rank
+                uint32_t posr[(ITEMS + 1) / 2];
+#pragma unroll
+                for (int j = 0; j < (ITEMS + 1) / 2; ++j) posr[j] = 0;
+#pragma unroll
+                for (int j = 0; j < ITEMS; ++j) {
+                    if ((vm >> j) & 1u) {
+                        const uint32_t f = static_cast<uint32_t>(k[j] >> lo) & fmask;
+                        const uint32_t low = f & lmask, sb = f >> lbits;
+                        const uint64_t wd = words[sb];
+                        const uint32_t x = static_cast<uint32_t>(wd), y = static_cast<uint32_t>(wd >> 32);
+                        const uint32_t mk = (1u << (4 * (low & 7u))) - 1u;
+                        const bool upper = low >= 8u;
+                        const uint32_t xm = x & (upper ? ~0u : mk), ym = y & (upper ? mk : 0u);
+                        constexpr uint32_t m4 = 0x0F0F0F0Fu;
+                        const uint32_t below =
+                            __dp4a((xm & m4) + ((xm >> 4) & m4) + (ym & m4) + ((ym >> 4) & m4), 0x01010101u, 0u);
+                        const uint32_t pos = st16[sb] + below + ((arr[j >> 3] >> (4 * (j & 7))) & 15u);
+                        posr[j >> 1] |= pos << ((j & 1) * 16);
+                    }
+                }
+                __syncthreads();
+                // keys to the staging buffer (slot lo_r + position), then out
+                const int lo_r = static_cast<int>(un.start % FL::V);
+                bool bad = false;
+#pragma unroll
+                for (int j = 0; j < ITEMS; ++j) {
+                    if ((vm >> j) & 1u) {
+                        const uint32_t pos = (posr[j >> 1] >> ((j & 1) * 16)) & 0xffffu;
+                        if (pos < static_cast<uint32_t>(len)) stage[lo_r + pos] = k[j];
+                        else bad = true;
+                    }
+                }
+                if (bad) set_error(wk.ctl, kErrBounds);
+                if (t == 0) atomicAdd(&wk.ctl->fin_counting, 1ull);
+                __syncthreads();
+                if (wk.keys_vec_ok) {
+                    constexpr int V = FL::V;
+                    const int a_i = (V - lo_r) % V;                        // first key of a whole 16-byte group
+                    const int nvec = (len - a_i) > 0 ? (len - a_i) / V : 0;
+                    const int b_i = a_i + nvec * V;
+                    const uint4 *sv = reinterpret_cast<const uint4 *>(stage + lo_r + a_i);
+                    uint4 *dv = reinterpret_cast<uint4 *>(dstp + a_i);
+                    for (int q = t; q < nvec; q += THREADS) {
+                        K kv[V];
+                        *reinterpret_cast<uint4 *>(kv) = sv[q];
+#pragma unroll
+                        for (int e = 0; e < V; ++e) kv[e] = decode_key(kv[e], wk.codec);
+                        dv[q] = *reinterpret_cast<uint4 *>(kv);
+                    }
+                    if (t < 2 * V) {
+                        const int i = t < V ? t : b_i + (t - V);
+                        if ((t < V && i < a_i && i < len) || (t >= V && i < len))
+                            dstp[i] = decode_key(stage[lo_r + i], wk.codec);
+                    }
+                } else {
+                    for (int i = t; i < len; i += THREADS) dstp[i] = decode_key(stage[lo_r + i], wk.codec);
+                }
+                __syncthreads();
+                continue;
+            }
+        }
         const int want = max(8, 32 - __clz(len - 1));
-        const int bits = min(hi - lo, min(want, kSplitBits));
+        const int bits = min(span, min(want, kSplitBits));
         const int top = hi - bits;
         const int nb = 1 << bits;
         const uint32_t dmask = static_cast<uint32_t>(nb - 1);
@@ -1220,7 +1381,7 @@ __global__ void __launch_bounds__(THREADS, 4) k_finish(Work wk) {
                 }
             if (t == 0) cnt[split_pad(nb)] = total;
         }
-        too_big = __syncthreads_or(too_big) && bits < hi - lo;
+        too_big = __syncthreads_or(too_big) && bits < span;
         if (too_big) {
             if (t == 0) {
                 const uint32_t f = atomicAdd(&wk.ctl->n_fb, 1u);
@@ -1229,6 +1390,7 @@ __global__ void __launch_bounds__(THREADS, 4) k_finish(Work wk) {
             }
             continue;
         }
+        if (t == 0) atomicAdd(&wk.ctl->fin_compare, 1ull);
         // split: place
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) {
@@ -1238,7 +1400,7 @@ __global__ void __launch_bounds__(THREADS, 4) k_finish(Work wk) {
             }
         }
         __syncthreads();
-        if (bits == hi - lo) {
+        if (bits == span) {
             for (int i = t; i < len; i += THREADS) dstp[i] = decode_key(sm_keys[i], wk.codec);
             __syncthreads();
             continue;
@@ -1262,8 +1424,7 @@ __global__ void __launch_bounds__(THREADS, 4) k_finish(Work wk) {
 
 template <typename K, int THREADS, int ITEMS>
 constexpr size_t finish_smem() {
-    return sizeof(K) * (THREADS * ITEMS + 2 * (THREADS / 32)) +
-           sizeof(uint32_t) * (kSplitCap + kSplitCap / 16 + 4 + THREADS / 32 + 1);
+    return FinLayout<K, THREADS, ITEMS>::kEnd;
 }
 
 // Finish of the units k_finish handed over (skewed: a sub-bucket too large

@@ -4,7 +4,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from gpu_util import assert_bit_exact, gpu_sort, to_device
+from gpu_util import assert_bit_exact, check_full_size, gpu_sort, to_device
 
 pytestmark = pytest.mark.gpu
 
@@ -121,3 +121,56 @@ def test_misaligned_and_offset_views():
     bs.bsort_keys(v)
     assert_bit_exact(v.cpu().numpy(), O.bsort(x), "offset view")
     assert int(t[0]) == 0
+
+
+def _sorted_with_profile(x, descending=False):
+    import torch
+    import paper_2603_08929_gb300 as bs
+    t = to_device(x)
+    h = bs.Handle()
+    h.set_profiling(True)
+    ws = torch.empty(bs.workspace_bytes(t.numel(), x.dtype.name), dtype=torch.uint8, device=t.device)
+    bs.bsort_keys_ws(h, t, ws, descending=descending)
+    prof = h.profile()
+    assert h.get_error() == 0
+    return t.cpu().numpy(), prof["finish_units"]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dtype,n,desc", [("uint32", 4096, False), ("int32", 5104, True), ("uint64", 2100, False),
+                                          ("uint32", 1023, False), ("float32", 4999, False)])
+def test_counting_finish(dtype, n, desc):
+    """One unit whose keys vary only in their low 16 bits (and enough keys to
+    fill 2^12 sub-buckets): the one-pass counting finish sorts it."""
+    rng = np.random.default_rng(n)
+    if dtype == "float32":
+        x = (1.0 + rng.integers(0, 1 << 16, n) * 2.0 ** -23).astype(np.float32)  # mantissa low 16 bits
+    else:
+        x = rng.integers(0, 1 << 16, n).astype(dtype)
+    got, fu = _sorted_with_profile(x, desc)
+    assert_bit_exact(got, O.bsort(x.copy(), descending=desc), dtype)
+    want = {"counting": 1 if n >= 1024 else 0}
+    assert fu["counting"] == want["counting"], fu
+
+
+@pytest.mark.gpu
+def test_counting_finish_overflow_falls_back():
+    """Sixteen equal keys overflow a 4-bit counter: the unit is ranked by the
+    split + comparison path instead, with the same result."""
+    rng = np.random.default_rng(5)
+    x = rng.integers(0, 1 << 16, 4000).astype(np.uint32)
+    x[:40] = 12345
+    rng.shuffle(x)
+    got, fu = _sorted_with_profile(x)
+    assert_bit_exact(got, O.bsort(x.copy()), "uint32")
+    assert fu["counting"] == 0 and fu["compare"] + fu["lsd"] == 1, fu
+
+
+@pytest.mark.gpu
+def test_counting_finish_full_size():
+    """2^27 uniform int32 keys: two 8-bit levels leave buckets of ~2048 keys
+    with 16 varying bits, all finished by the counting pass."""
+    x = W.make("uniform", "int32", 1 << 27, seed=78)
+    got, fu = _sorted_with_profile(x)
+    assert fu["counting"] > 0.99 * (fu["counting"] + fu["compare"] + fu["lsd"]), fu
+    check_full_size(x, got, False)
