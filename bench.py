@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--dist", default="uniform")
     ap.add_argument("--log2n", type=int, default=28)
     ap.add_argument("--desc", action="store_true")
+    ap.add_argument("--inplace", action="store_true", help="in-place mode (no alternate buffer); reports aux bytes")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -444,13 +445,14 @@ def main():
     base = torch.from_numpy(x).to(dev)
     bufs = [base.clone() for _ in range(total_steps)]
     del base
-    ws = torch.empty(bs.workspace_bytes(n, args.dtype), dtype=torch.uint8, device=dev)
+    mode = bs.MODE_INPLACE if args.inplace else bs.MODE_PINGPONG
+    ws = torch.empty(bs.workspace_bytes(n, args.dtype, mode=mode), dtype=torch.uint8, device=dev)
     h = bs.Handle()
     h.set_profiling(True)
     stream = torch.cuda.current_stream()
 
     for i in range(args.warmup):
-        bs.bsort_keys_ws(h, bufs[i], ws, descending=args.desc, stream=stream)
+        bs.bsort_keys_ws(h, bufs[i], ws, descending=args.desc, stream=stream, mode=mode)
     torch.cuda.synchronize()
     if h.get_error(stream) != 0:
         raise RuntimeError("device error word set during warm-up")
@@ -466,7 +468,7 @@ def main():
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for i in range(args.warmup, total_steps):
-        bs.bsort_keys_ws(h, bufs[i], ws, descending=args.desc, stream=stream)
+        bs.bsort_keys_ws(h, bufs[i], ws, descending=args.desc, stream=stream, mode=mode)
     ev1.record(stream)
     torch.cuda.synchronize()
     # per-launch CUDA-event times recorded by the library on the same stream
@@ -484,6 +486,7 @@ def main():
     clock_info = clocks.stop() if clocks else None
     if h.get_error(stream) != 0:
         raise RuntimeError("device error word set during the timed steps")
+    aux_bytes = h.last_aux_bytes()
 
     # step time: sum of each step's sort (events around every launch group)
     sort_ms = sum(k["ms"] for k in per_kind.values()) / args.steps
@@ -512,8 +515,9 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_TAG.get(args.dtype, args.dtype),
         "data": "synthetic",
-        "config": {"workload": "plain sort, %s %s, 2^%d keys, %s" % (
-            args.dtype, args.dist, args.log2n, "descending" if args.desc else "ascending"),
+        "config": {"workload": "plain sort, %s %s, 2^%d keys, %s%s" % (
+            args.dtype, args.dist, args.log2n, "descending" if args.desc else "ascending",
+            ", in-place mode" if args.inplace else ""),
             "n": n, "per_gpu_keys": n, "l2": "input 2^%d x %d B > L2; each step sorts its own copy"
                                             % (args.log2n, esize),
             "parallelism": "replicas%d" % world},
@@ -532,6 +536,10 @@ def main():
                         "launches_per_step": v["launches"] / args.steps}
                     for k, v in sorted(per_kind.items())},
         "finish_units_per_step": {k: v / args.steps for k, v in prof["finish_units"].items()},
+        "mode": "inplace" if args.inplace else "pingpong",
+        "aux": {"bytes": aux_bytes, "frac_of_keys": aux_bytes / (n * esize),
+                "workspace_reserved": ws.numel(),
+                "paper_bound": "O(w): the sequential in-place partition keeps only its recursion (Sec. III)"},
         "sorted_check": ok_sorted,
     }
     if clock_info:

@@ -71,7 +71,7 @@ typedef enum {
 
 typedef enum {
     BSORT_MODE_PINGPONG = 0,  /* default: an n-key alternate buffer in the workspace */
-    BSORT_MODE_INPLACE = 1    /* reserved: block permutation inside the caller's array */
+    BSORT_MODE_INPLACE = 1    /* digit permutation inside the caller's array (no alternate buffer) */
 } bsort_mode;
 
 typedef struct bsort_handle bsort_handle;
@@ -92,6 +92,10 @@ bsort_status bsort_keys(void *keys, size_t n, bsort_dtype dt, int descending, vo
  * Bytes of device workspace bsort_keys_ws() needs for n keys of `dt` in
  * `mode` (host-only computation, no CUDA call).  Ping-pong mode needs the
  * n-key alternate buffer plus metadata bounded by n / (finish-threshold).
+ * In-place mode needs no alternate buffer: its worst-case reservation is the
+ * metadata plus one 32 KB partial-block buffer per 1 MB stripe and per bucket
+ * larger than 192 KB, and one state word per 128-byte block; what a call
+ * really used is reported by bsort_last_aux_bytes().
  */
 bsort_status bsort_workspace_bytes(size_t n, bsort_dtype dt, bsort_mode mode, size_t *bytes);
 
@@ -107,9 +111,28 @@ bsort_status bsort_handle_destroy(bsort_handle *handle);
  * is a device pointer, 256-byte aligned, of at least
  * bsort_workspace_bytes(n, dt, mode) bytes; its contents need no
  * initialisation and are scratch after the call.
+ *
+ * mode BSORT_MODE_INPLACE: every digit pass permutes the keys inside `keys`
+ * instead of moving them to an alternate buffer (the paper sorts in place
+ * with O(w) extra memory, Sec. III; the GPU keeps counters and block buffers,
+ * see bsort_last_aux_bytes).  A bucket of at most 192 KB is read whole into
+ * shared memory and written back in digit order; a larger one is classified
+ * stripe by stripe into 128-byte blocks of one digit each, the blocks are
+ * carried to their digit's block slots, and partial blocks fill the rest.
+ * The result is bit-identical to ping-pong mode.
  */
 bsort_status bsort_keys_ws(bsort_handle *handle, void *keys, size_t n, bsort_dtype dt, int descending,
                            bsort_mode mode, void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * Auxiliary device bytes the last call on `handle` used beyond the keys:
+ * ping-pong mode, its whole workspace (the alternate buffer included);
+ * in-place mode, the metadata plus the largest block buffers, slot states
+ * and per-digit counters any level used (read from the device: synchronises
+ * with the last call's stream); 1- and 2-byte keys, the histogram.  Compare
+ * with the paper's O(w) bound for its sequential in-place partition.
+ */
+bsort_status bsort_last_aux_bytes(bsort_handle *handle, size_t *bytes);
 
 /*
  * End-to-end sort of a HOST array: copies host_keys[0, n) to the device,

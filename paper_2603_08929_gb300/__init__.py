@@ -123,6 +123,8 @@ def lib():
         L.bsort_graph_error.restype = i
         L.bsort_graph_destroy.argtypes = [vp]
         L.bsort_graph_destroy.restype = i
+        L.bsort_last_aux_bytes.argtypes = [vp, ctypes.POINTER(sz)]
+        L.bsort_last_aux_bytes.restype = i
         L.bsort_server_create.argtypes = [ctypes.POINTER(_ServerConfig), ctypes.POINTER(vp)]
         L.bsort_server_create.restype = i
         L.bsort_server_submit.argtypes = [vp, vp, sz, i, i, ctypes.c_uint64]
@@ -234,6 +236,12 @@ class Handle:
         return {"calls": int(p.num_calls), "launches": int(p.num_launches), "records": recs,
                 "finish_units": {"counting": int(p.finish_units_counting), "compare": int(p.finish_units_compare),
                                  "lsd": int(p.finish_units_lsd)}}
+
+    def last_aux_bytes(self) -> int:
+        """Auxiliary device bytes of the last call (``bsort_last_aux_bytes``)."""
+        out = ctypes.c_size_t(0)
+        _check(lib().bsort_last_aux_bytes(self._h, ctypes.byref(out)), "bsort_last_aux_bytes")
+        return int(out.value)
 
     def get_error(self, stream=None) -> int:
         return int(lib().bsort_get_error(self._h, _stream_ptr(stream)))

@@ -63,9 +63,13 @@ size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 struct MsdLayout {
     size_t alt, ctl, buckets0, buckets1, chunks0, chunks1, hist, cand, cor, bbase, units, fb_units, fills, total;
     uint32_t max_buckets, max_chunks, max_units, max_fills;
+    // in-place mode (alt is empty then)
+    bool inplace;
+    size_t ip_big, ip_stripes, ip_ncnt, ip_cursor, ip_rem, ip_part, ip_ovf, ip_state, lists_end;
+    uint32_t max_big, max_stripes, max_slots;
 };
 
-MsdLayout msd_layout(size_t n, int key_bytes, size_t nseg = 0) {
+MsdLayout msd_layout(size_t n, int key_bytes, size_t nseg = 0, bool inplace = false) {
     const MsdShape s = msd_shape(key_bytes);
     MsdLayout L;
     const uint64_t per_t = n / s.unit_cap + 1;
@@ -80,7 +84,8 @@ MsdLayout msd_layout(size_t n, int key_bytes, size_t nseg = 0) {
         off = align_up(off + bytes);
         return at;
     };
-    L.alt = take(n * key_bytes);
+    L.inplace = inplace;
+    L.alt = take(inplace ? 0 : n * key_bytes);
     L.ctl = take(sizeof(Ctl));
     L.buckets0 = take(sizeof(Bucket) * L.max_buckets);
     L.buckets1 = take(sizeof(Bucket) * L.max_buckets);
@@ -93,6 +98,26 @@ MsdLayout msd_layout(size_t n, int key_bytes, size_t nseg = 0) {
     L.units = take(sizeof(Unit) * L.max_units);
     L.fb_units = take(sizeof(Unit) * L.max_units);
     L.fills = take(sizeof(Fill) * L.max_fills);
+    L.lists_end = off;
+    L.max_big = L.max_stripes = L.max_slots = 0;
+    L.ip_big = L.ip_stripes = L.ip_ncnt = L.ip_cursor = L.ip_rem = L.ip_part = L.ip_ovf = L.ip_state = 0;
+    if (inplace) {
+        // a level's big buckets are disjoint and longer than the shared-memory capacity
+        const uint64_t blk = kIpBlockBytes / key_bytes;
+        const uint64_t cap = kIpSmemCapBytes / key_bytes;
+        const uint64_t stripe = kIpStripeBytes / key_bytes;
+        L.max_big = static_cast<uint32_t>(n / (cap + 1) + 1);
+        L.max_stripes = static_cast<uint32_t>(n / stripe + L.max_big + 1);
+        L.max_slots = static_cast<uint32_t>(n / blk + L.max_big + 1);
+        L.ip_big = take(sizeof(IpBig) * L.max_big);
+        L.ip_stripes = take(sizeof(IpStripe) * L.max_stripes);
+        L.ip_ncnt = take(sizeof(uint32_t) * kBins * static_cast<size_t>(L.max_big));
+        L.ip_cursor = take(sizeof(uint32_t) * kBins * static_cast<size_t>(L.max_big));
+        L.ip_rem = take(static_cast<size_t>(kBins) * L.max_stripes);
+        L.ip_part = take(static_cast<size_t>(kIpBlockBytes) * kBins * L.max_stripes);
+        L.ip_ovf = take(static_cast<size_t>(kIpBlockBytes) * kBins * L.max_big);
+        L.ip_state = take(sizeof(uint32_t) * static_cast<size_t>(L.max_slots));
+    }
     L.total = off;
     return L;
 }
@@ -196,6 +221,19 @@ Work make_work(const MsdLayout &L, char *ws, void *keys, size_t n, const DtypeIn
     wk.merge_cap = s.merge_cap;
     wk.w = di.bytes * 8;
     wk.keys_vec_ok = (reinterpret_cast<uintptr_t>(keys) & 15) == 0;
+    wk.inplace = L.inplace;
+    wk.ip_big = L.inplace ? reinterpret_cast<IpBig *>(ws + L.ip_big) : nullptr;
+    wk.ip_stripes = L.inplace ? reinterpret_cast<IpStripe *>(ws + L.ip_stripes) : nullptr;
+    wk.ip_ncnt = L.inplace ? reinterpret_cast<uint32_t *>(ws + L.ip_ncnt) : nullptr;
+    wk.ip_cursor = L.inplace ? reinterpret_cast<uint32_t *>(ws + L.ip_cursor) : nullptr;
+    wk.ip_rem = L.inplace ? reinterpret_cast<uint8_t *>(ws + L.ip_rem) : nullptr;
+    wk.ip_part = L.inplace ? static_cast<void *>(ws + L.ip_part) : nullptr;
+    wk.ip_ovf = L.inplace ? static_cast<void *>(ws + L.ip_ovf) : nullptr;
+    wk.ip_state = L.inplace ? reinterpret_cast<uint32_t *>(ws + L.ip_state) : nullptr;
+    wk.max_big = L.max_big;
+    wk.max_stripes = L.max_stripes;
+    wk.max_slots = L.max_slots;
+    if (L.inplace) wk.alt = nullptr;
     return wk;
 }
 
@@ -218,7 +256,7 @@ void end_call(bsort_handle *h, cudaStream_t st, size_t n, int key_bytes) {
 }
 
 bsort_status run_sort(bsort_handle *h, void *keys, size_t n, const DtypeInfo &di, int descending,
-                      void *workspace, size_t ws_bytes, cudaStream_t st) {
+                      void *workspace, size_t ws_bytes, cudaStream_t st, bool inplace = false) {
     (void)cudaGetLastError();  // clear a stale non-sticky error
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return BSORT_ERR_CUDA;
@@ -248,9 +286,13 @@ bsort_status run_sort(bsort_handle *h, void *keys, size_t n, const DtypeInfo &di
         else launch_count16(cw, st, h->rec, sms);
         h->last_path = 1;
         h->last_ctl = nullptr;
+        h->last_inplace = inplace;  // the counting path writes the keys from counts: in place either way
+        h->last_fixed_aux = L.total;
     } else {
-        const MsdLayout L = msd_layout(n, di.bytes);
+        const MsdLayout L = msd_layout(n, di.bytes, 0, inplace);
         if (ws_bytes < L.total) return BSORT_ERR_WORKSPACE_TOO_SMALL;
+        h->last_inplace = inplace;
+        h->last_fixed_aux = inplace ? L.lists_end - L.ctl : L.total;
         const Work wk = make_work(L, ws, keys, n, di, codec);
         if (di.bytes == 4) launch_msd<uint32_t>(wk, st, h->rec, sms);
         else launch_msd<uint64_t>(wk, st, h->rec, sms);
@@ -318,8 +360,8 @@ bsort_status grow(void **buf, size_t *have, size_t need) {
     return BSORT_OK;
 }
 
-size_t workspace_for(size_t n, const DtypeInfo &di) {
-    return di.bytes <= 2 ? count_layout(n, di.bytes).total : msd_layout(n, di.bytes).total;
+size_t workspace_for(size_t n, const DtypeInfo &di, bool inplace = false) {
+    return di.bytes <= 2 ? count_layout(n, di.bytes).total : msd_layout(n, di.bytes, 0, inplace).total;
 }
 
 }  // namespace
@@ -346,8 +388,7 @@ bsort_status bsort_workspace_bytes(size_t n, bsort_dtype dt, bsort_mode mode, si
     DtypeInfo di;
     if (!bytes || !dtype_info(dt, &di)) return BSORT_ERR_INVALID_ARG;
     if (mode != BSORT_MODE_PINGPONG && mode != BSORT_MODE_INPLACE) return BSORT_ERR_INVALID_ARG;
-    if (mode == BSORT_MODE_INPLACE) return BSORT_ERR_UNSUPPORTED;
-    *bytes = workspace_for(n, di);
+    *bytes = workspace_for(n, di, mode == BSORT_MODE_INPLACE);
     return BSORT_OK;
 }
 
@@ -383,12 +424,12 @@ bsort_status bsort_keys_ws(bsort_handle *handle, void *keys, size_t n, bsort_dty
     const bsort_status st = check_args(keys, n, dt, &di);
     if (st != BSORT_OK) return st;
     if (mode != BSORT_MODE_PINGPONG && mode != BSORT_MODE_INPLACE) return BSORT_ERR_INVALID_ARG;
-    if (mode == BSORT_MODE_INPLACE) return BSORT_ERR_UNSUPPORTED;
     if (n <= 1) return BSORT_OK;
     if (!workspace) return BSORT_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(workspace) % kAlign) return BSORT_ERR_MISALIGNED;
     std::lock_guard<std::mutex> lk(handle->mu);
-    return run_sort(handle, keys, n, di, descending, workspace, ws_bytes, static_cast<cudaStream_t>(stream));
+    return run_sort(handle, keys, n, di, descending, workspace, ws_bytes, static_cast<cudaStream_t>(stream),
+                    mode == BSORT_MODE_INPLACE);
 }
 
 bsort_status bsort_keys(void *keys, size_t n, bsort_dtype dt, int descending, void *stream) {
@@ -568,6 +609,23 @@ bsort_status bsort_graph_destroy(bsort_graph *graph) {
     if (graph->exec) cudaGraphExecDestroy(graph->exec);
     if (graph->graph) cudaGraphDestroy(graph->graph);
     delete graph;
+    return BSORT_OK;
+}
+
+bsort_status bsort_last_aux_bytes(bsort_handle *handle, size_t *bytes) {
+    if (!handle || !bytes) return BSORT_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(handle->mu);
+    *bytes = 0;
+    if (handle->last_path == 0) return BSORT_OK;
+    size_t used = handle->last_fixed_aux;
+    if (handle->last_path == 2 && handle->last_inplace && handle->last_ctl) {
+        if (cudaStreamSynchronize(handle->last_stream) != cudaSuccess) return BSORT_ERR_CUDA;
+        unsigned long long aux = 0;
+        if (cudaMemcpy(&aux, &handle->last_ctl->aux_used, sizeof(aux), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return BSORT_ERR_CUDA;
+        used += static_cast<size_t>(aux);
+    }
+    *bytes = used;
     return BSORT_OK;
 }
 

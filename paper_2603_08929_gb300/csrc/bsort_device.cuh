@@ -71,6 +71,26 @@ struct Fill {
     uint32_t pad;
 };
 
+// In-place mode: a bucket of this level too large for the whole-bucket
+// shared-memory pass, and one stripe (a contiguous, block-aligned piece of
+// it that one CTA classifies into blocks).
+struct IpBig {
+    uint64_t start;
+    uint64_t len;
+    uint32_t bucket;        // index in this level's bucket list
+    uint32_t first_stripe;  // its stripes are [first_stripe, first_stripe + num_stripes)
+    uint32_t num_stripes;
+    uint32_t state0;        // index of its slot 0 in the slot-state array
+};
+
+struct IpStripe {
+    uint64_t start;  // absolute key index (bucket start + slot0 * block keys)
+    uint32_t len;
+    uint32_t big;
+    uint32_t slot0;  // first slot, relative to the bucket start
+    uint32_t nfull;  // full blocks at the stripe's start after classification
+};
+
 struct Ctl {
     uint32_t n_buckets[2];
     uint32_t n_chunks[2];
@@ -84,6 +104,8 @@ struct Ctl {
     unsigned long long fill_keys;
     unsigned long long raw_reads;                 // keys read while still raw (diagnostic)
     unsigned long long fin_counting, fin_compare; // finish units by method (diagnostic)
+    uint32_t n_big, n_stripes, n_slots, ip_pad;   // in-place lists of the current level
+    unsigned long long aux_used;                  // in-place: largest auxiliary bytes any level used
 };
 
 // Everything a launch needs, passed by value.
@@ -108,6 +130,17 @@ struct Work {
     uint32_t merge_cap;   // adjacent small buckets merge while their sum stays <= this
     int32_t w;            // key bits
     bool keys_vec_ok;     // caller's buffer is 16-byte aligned (vector loads)
+    // in-place mode (digit permutation inside the caller's buffer)
+    bool inplace;
+    IpBig *ip_big;          // [max_big]
+    IpStripe *ip_stripes;   // [max_stripes]
+    uint32_t *ip_ncnt;      // [max_big][kBins] full blocks per digit
+    uint32_t *ip_cursor;    // [max_big][kBins] blocks placed per digit
+    uint8_t *ip_rem;        // [max_stripes][kBins] keys left in a partial block
+    void *ip_part;          // [max_stripes][kBins][block keys] partial blocks
+    void *ip_ovf;           // [max_big][kBins][block keys] overflow of a digit's last block
+    uint32_t *ip_state;     // [max_slots] slot states
+    uint32_t max_big, max_stripes, max_slots;
 };
 
 constexpr uint32_t kFillPiece = 1u << 16;  // keys per fill work item

@@ -68,6 +68,16 @@ void launch_msd_segmented(const Work &wk, const uint64_t *d_offsets, uint32_t ns
 template <typename K>
 void msd_prepare();
 
+// In-place mode: one level's digit permutation inside the caller's buffer
+// (replaces the ping-pong scatter of that level).
+constexpr int kIpBlockBytes = 128;                 // block of the permutation
+constexpr int kIpSmemCapBytes = 192 * 1024;        // buckets up to this size go through shared memory whole
+constexpr uint64_t kIpStripeBytes = 1ull << 20;    // stripe classified by one CTA
+template <typename K>
+void ip_prepare();
+template <typename K>
+void launch_ip_level(const Work &wk, cudaStream_t st, Recorder &rec, int num_sms, int level);
+
 // Counting sort of 1- or 2-byte keys: histogram of all key bits, bin starts,
 // and a write-only fill of the output.  Scratch comes from `ws`.
 struct CountWork {

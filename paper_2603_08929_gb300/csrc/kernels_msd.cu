@@ -840,7 +840,7 @@ __global__ void __launch_bounds__(THREADS) k_classify(Work wk, int level) {
         sh_len[d] = tot;
         sh_base[d] = base;
         const int hc = shift;  // bits left in the children
-        const int dst = b.src ^ 1;
+        const int dst = wk.inplace ? 0 : b.src ^ 1;
         const bool big = tot > wk.unit_cap;
         // children with no bits left are constant: value = common prefix | digit
         if (big && hc == 0) {
@@ -1549,6 +1549,7 @@ template <typename K>
 void msd_prepare() {
     constexpr int T = Cfg<K>::kThreads, I = Cfg<K>::kItems;
     constexpr int FT = Cfg<K>::kFinThreads, FI = Cfg<K>::kFinItems;
+    ip_prepare<K>();
     static const bool attrs = [] {  // once per process; thread-safe static initialisation
         cudaFuncSetAttribute(k_scatter<K, T, I, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(scatter_smem<K, T, I, 2>()));
@@ -1579,9 +1580,13 @@ void msd_levels_and_finish(const Work &wk, cudaStream_t st, Recorder &rec, int n
             rec.begin(BSORT_K_CLASSIFY, level);
             k_classify<kBins><<<num_sms * 4, kBins, 0, st>>>(wk, level);
             rec.end();
-            rec.begin(BSORT_K_SCATTER, level);
-            k_scatter<K, T, I, CT><<<num_sms * 2, T, scatter_smem<K, T, I, CT>(), st>>>(wk, level);
-            rec.end();
+            if (wk.inplace) {
+                launch_ip_level<K>(wk, st, rec, num_sms, level);
+            } else {
+                rec.begin(BSORT_K_SCATTER, level);
+                k_scatter<K, T, I, CT><<<num_sms * 2, T, scatter_smem<K, T, I, CT>(), st>>>(wk, level);
+                rec.end();
+            }
         }
     }
     rec.begin(BSORT_K_FINISH, -1);

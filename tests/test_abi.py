@@ -66,5 +66,13 @@ def test_workspace_sizes(lib):
     assert n * 8 <= pkg.workspace_bytes(n, "float64") <= n * 8 * 1.25
     # counting path: no alternate buffer
     assert pkg.workspace_bytes(n, "uint8") < 1 << 20
+    # in-place: no alternate buffer; the reservation (metadata, block buffers
+    # for the worst case of buckets just above the shared-memory capacity,
+    # slot states) stays well below one copy of the keys
+    for dt, b in (("int32", 4), ("float64", 8)):
+        ip = pkg.workspace_bytes(n, dt, mode=pkg.MODE_INPLACE)
+        assert ip < 0.75 * n * b, (dt, ip / (n * b))
+        assert ip < pkg.workspace_bytes(n, dt)
+    assert pkg.workspace_bytes(n, "uint16", mode=pkg.MODE_INPLACE) == pkg.workspace_bytes(n, "uint16")
     with pytest.raises(pkg.BsortError):
-        pkg.workspace_bytes(100, "int32", mode=pkg.MODE_INPLACE)
+        pkg.workspace_bytes(100, "int32", mode=7)
