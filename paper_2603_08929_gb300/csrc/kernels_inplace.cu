@@ -322,10 +322,16 @@ __global__ void __launch_bounds__(kIpStripeThreads, 2) k_ip_stripe(Work wk, int 
 }
 
 // ---------------------------------------------------------------------------
-// Block permutation.  One warp carries one block (lane l < B holds key l).
+// Block permutation.  A group of 8 lanes carries one block: lane gl of the
+// group holds keys gl, gl + 8, gl + 16, ... of it (B / 8 keys), so every
+// access of the group covers 32 contiguous bytes.  A warp runs four groups,
+// each with its own chain, so four carries are in flight per warp.
+
+constexpr int kGroup = 8;
 
 template <typename K>
 struct Carry {
+    static constexpr int B = IpCfg<K>::B, E = B / kGroup;  // keys per lane
     const Work &wk;
     const IpBig &big;
     uint32_t bb;
@@ -333,23 +339,35 @@ struct Carry {
     K *keys;
     K *ovf;
 
+    __device__ void load(uint32_t slot, int gl, K (&v)[E]) const {
+        const K *src = keys + big.start + static_cast<uint64_t>(slot) * B + gl;
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = src[e * kGroup];
+    }
+
     // Writes a block of digit d into slot `slot`; keys past D_{d+1} go to the
     // digit's overflow buffer.
-    __device__ void put(uint32_t d, uint32_t slot, K v, int lane) const {
-        constexpr int B = IpCfg<K>::B;
-        if (lane >= B) return;
+    __device__ void put(uint32_t d, uint32_t slot, const K (&v)[E], int gl) const {
         const uint64_t dend = dbase(wk, big.bucket, g, d + 1, big.len);
-        const uint64_t pos = static_cast<uint64_t>(slot) * B + lane;
-        if (pos < dend) keys[big.start + pos] = v;
-        else if (pos - dend < static_cast<uint64_t>(B)) ovf[(static_cast<size_t>(bb) * kBins + d) * B + (pos - dend)] = v;
-        else ip_error(wk, kErrBounds);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const uint64_t pos = static_cast<uint64_t>(slot) * B + gl + e * kGroup;
+            if (pos < dend) keys[big.start + pos] = v[e];
+            else if (pos - dend < static_cast<uint64_t>(B))
+                ovf[(static_cast<size_t>(bb) * kBins + d) * B + (pos - dend)] = v[e];
+            else ip_error(wk, kErrBounds);
+        }
     }
 };
 
 template <typename K>
 __global__ void __launch_bounds__(kIpPermuteThreads) k_ip_permute(Work wk, int level) {
-    constexpr int B = IpCfg<K>::B, WARPS = kIpPermuteThreads / 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    using C = Carry<K>;
+    constexpr int B = C::B, E = C::E, GROUPS = kIpPermuteThreads / kGroup;
+    const int lane = threadIdx.x & 31, gl = lane & (kGroup - 1);
+    const int grp = threadIdx.x / kGroup;  // group of this CTA
+    const int leader = lane & ~(kGroup - 1);
+    const unsigned gmask = 0xFFu << leader;
     const int p = level & 1;
     if (wk.ctl->error) return;
     const uint32_t ns = min(wk.ctl->n_stripes, wk.max_stripes);
@@ -359,25 +377,27 @@ __global__ void __launch_bounds__(kIpPermuteThreads) k_ip_permute(Work wk, int l
         const IpStripe s = wk.ip_stripes[si];
         const IpBig big = wk.ip_big[s.big];
         const Bucket b = wk.buckets[p][big.bucket];
-        const Carry<K> cy{wk, big, s.big, digit_geo(b), keys, ovf};
+        const C cy{wk, big, s.big, digit_geo(b), keys, ovf};
         uint32_t *state = wk.ip_state + big.state0;
-        for (uint32_t j = warp; j < s.nfull; j += WARPS) {
+        bool fail = false;
+        for (uint32_t j = grp; j < s.nfull && !fail; j += GROUPS) {
             const uint32_t seed = s.slot0 + j;
             uint32_t got = 0;
-            if (lane == 0) got = atomicCAS(&state[seed], kSlotFull, kSlotTaken) == kSlotFull;
-            if (!__shfl_sync(kFullMask, got, 0)) continue;
+            if (gl == 0) got = atomicCAS(&state[seed], kSlotFull, kSlotTaken) == kSlotFull;
+            if (!__shfl_sync(gmask, got, leader)) continue;
             // take the seed block out, then free its slot
-            K x = lane < B ? keys[big.start + static_cast<uint64_t>(seed) * B + lane] : K(0);
-            __syncwarp();
-            if (lane == 0) {
+            K x[E];
+            cy.load(seed, gl, x);
+            __syncwarp(gmask);
+            if (gl == 0) {
                 __threadfence();
                 atomicExch(&state[seed], kSlotHole);
             }
             // carry until the block lands on a slot that holds nothing to take
             for (int hop = 0;; ++hop) {
-                const uint32_t d = digit_of(__shfl_sync(kFullMask, x, 0), cy.g);
+                const uint32_t d = digit_of(__shfl_sync(gmask, x[0], leader), cy.g);
                 uint32_t dst = 0, st = kSlotHole, ok = 1;
-                if (lane == 0) {
+                if (gl == 0) {
                     const size_t di = static_cast<size_t>(s.big) * kBins + d;
                     const uint32_t c = atomicAdd(&wk.ip_cursor[di], 1u);
                     const uint64_t a_d = (dbase(wk, big.bucket, cy.g, d, big.len) + B - 1) / B;
@@ -385,25 +405,28 @@ __global__ void __launch_bounds__(kIpPermuteThreads) k_ip_permute(Work wk, int l
                     dst = static_cast<uint32_t>(a_d) + c;
                     if (ok) st = atomicCAS(&state[dst], kSlotFull, kSlotTaken);
                 }
-                ok = __shfl_sync(kFullMask, ok, 0);
+                ok = __shfl_sync(gmask, ok, leader);
                 if (!ok || hop > (1 << 26)) {
-                    if (lane == 0) ip_error(wk, kErrBounds);
+                    if (gl == 0) ip_error(wk, kErrBounds);
+                    fail = true;
                     break;
                 }
-                dst = __shfl_sync(kFullMask, dst, 0);
-                st = __shfl_sync(kFullMask, st, 0);
+                dst = __shfl_sync(gmask, dst, leader);
+                st = __shfl_sync(gmask, st, leader);
                 if (st == kSlotFull) {
                     // we took the block at dst: read it, put ours, carry it on
-                    const K y = lane < B ? keys[big.start + static_cast<uint64_t>(dst) * B + lane] : K(0);
-                    __syncwarp();
-                    cy.put(d, dst, x, lane);
-                    x = y;
+                    K y[E];
+                    cy.load(dst, gl, y);
+                    __syncwarp(gmask);
+                    cy.put(d, dst, x, gl);
+#pragma unroll
+                    for (int e = 0; e < E; ++e) x[e] = y[e];
                     continue;
                 }
                 if (st == kSlotTaken) {
-                    // a seeding warp is reading the block at dst out
+                    // a seeding group is reading the block at dst out
                     uint32_t ready = 0;
-                    if (lane == 0) {
+                    if (gl == 0) {
                         for (int i = 0; i < kSpinLimit; ++i) {
                             if (atomicAdd(&state[dst], 0u) == kSlotHole) {
                                 ready = 1;
@@ -413,12 +436,13 @@ __global__ void __launch_bounds__(kIpPermuteThreads) k_ip_permute(Work wk, int l
                         }
                         __threadfence();
                     }
-                    if (!__shfl_sync(kFullMask, ready, 0)) {
-                        if (lane == 0) ip_error(wk, kErrTimeout);
+                    if (!__shfl_sync(gmask, ready, leader)) {
+                        if (gl == 0) ip_error(wk, kErrTimeout);
+                        fail = true;
                         break;
                     }
                 }
-                cy.put(d, dst, x, lane);
+                cy.put(d, dst, x, gl);
                 break;
             }
         }
