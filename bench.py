@@ -79,6 +79,20 @@ def dist_env():
     return rank, world, local
 
 
+def whole_job(ms_per_step_local, keys_per_rank, world, device):
+    """Max step time over the ranks and the whole-job throughput (Gkeys/s):
+    every rank sorts its own keys_per_rank keys per step (independent
+    replicas), so the job does world * keys_per_rank keys per max step time."""
+    ms = float(ms_per_step_local)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, keys_per_rank * world / (ms * 1e-3) / 1e9
+
+
 def measured_traffic(kind, dtype, keys_per_launch):
     """DRAM bytes per launch of kernel `kind` from the committed ncu record, or
     None when there is no record for it or the kernel sources changed since."""
@@ -490,12 +504,7 @@ def main():
 
     # step time: sum of each step's sort (events around every launch group)
     sort_ms = sum(k["ms"] for k in per_kind.values()) / args.steps
-    ms_per_step = elapsed_ms / args.steps
-    if world > 1:
-        t = torch.tensor([ms_per_step], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_per_step = float(t.item())
-    value = n * world / (ms_per_step * 1e-3) / 1e9
+    ms_per_step, value = whole_job(elapsed_ms / args.steps, n, world, dev)
 
     # correctness of the last timed step (cheap properties at full size)
     out = bufs[-1]
