@@ -33,6 +33,7 @@ Table II's types and give no distribution; these stand in for them):
 from __future__ import annotations
 
 import math
+import os
 
 import numpy as np
 
@@ -59,11 +60,21 @@ def words(seed: int, stream: int, start: int, count: int) -> np.ndarray:
     """Words start..start+count-1 of (seed, stream) as uint64."""
     state = np.uint64((seed ^ (stream << 40)) & 0xFFFFFFFFFFFFFFFF)
     out = np.empty(count, dtype=np.uint64)
-    for c0 in range(0, count, _CHUNK):
+
+    def fill(c0):
         c1 = min(count, c0 + _CHUNK)
         i = np.arange(start + c0 + 1, start + c1 + 1, dtype=np.uint64)
         with np.errstate(over="ignore"):
             out[c0:c1] = _mix64(state + i * GAMMA)
+
+    starts = range(0, count, _CHUNK)
+    if count > 4 * _CHUNK:  # chunks are independent (counter-based): fill them in threads
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+            list(ex.map(fill, starts))
+    else:
+        for c0 in starts:
+            fill(c0)
     return out
 
 
@@ -72,12 +83,31 @@ def uniform01(seed: int, stream: int, count: int) -> np.ndarray:
     return (words(seed, stream, 0, count) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
 
 
+def _threaded(count: int, fill) -> None:
+    """Runs fill(c0, c1) over [0, count) in _CHUNK pieces, in threads when
+    large (numpy releases the GIL inside its array loops)."""
+    starts = range(0, count, _CHUNK)
+    if count > 4 * _CHUNK:
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+            list(ex.map(lambda c0: fill(c0, min(count, c0 + _CHUNK)), starts))
+    else:
+        for c0 in starts:
+            fill(c0, min(count, c0 + _CHUNK))
+
+
 def normal(seed: int, stream: int, count: int, mean: float = 0.0, std: float = 1.0) -> np.ndarray:
     """Box-Muller (cosine branch) on the pair of words (2i, 2i+1)."""
-    w = words(seed, stream, 0, 2 * count)
-    u1 = 1.0 - (w[0::2] >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)  # (0, 1]
-    u2 = (w[1::2] >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
-    return mean + std * np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)
+    out = np.empty(count, dtype=np.float64)
+
+    def fill(c0, c1):
+        w = words(seed, stream, 2 * c0, 2 * (c1 - c0))
+        u1 = 1.0 - (w[0::2] >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)  # (0, 1]
+        u2 = (w[1::2] >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+        out[c0:c1] = mean + std * np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)
+
+    _threaded(count, fill)
+    return out
 
 
 def stream_id(dist: str, dtype: str, sub: int = 0) -> int:
@@ -148,8 +178,14 @@ def make(dist: str, dtype, n: int, seed: int = 0) -> np.ndarray:
         cdf = np.cumsum(weights)
         cdf /= cdf[-1]
         u = uniform01(seed, stream_id(dist, name, 2), n)
-        r = np.minimum(np.searchsorted(cdf, u, side="right"), k - 1)
-        return vals[r].view(dtype)
+        out = np.empty(n, dtype=vals.dtype)
+
+        def fill(c0, c1):
+            r = np.minimum(np.searchsorted(cdf, u[c0:c1], side="right"), k - 1)
+            out[c0:c1] = vals[r]
+
+        _threaded(n, fill)
+        return out.view(dtype)
     if dist == "float_edge":
         return _float_edge(seed, n, dtype)
     raise ValueError("unknown distribution %r" % dist)
