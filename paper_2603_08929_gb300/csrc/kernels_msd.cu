@@ -1016,7 +1016,6 @@ __global__ void __launch_bounds__(THREADS, 2) k_scatter(Work wk, int level) {
     uint32_t *tmp = scnt + kBins;                                // [WARPS + 1]
     int *bad = reinterpret_cast<int *>(tmp + WARPS + 1);
     const int p = level & 1;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (wk.ctl->error) return;
     if (threadIdx.x == 0) *bad = 0;  // stays 0 unless a check fails (then the CTA stops)
     __syncthreads();
@@ -1101,13 +1100,13 @@ __global__ void __launch_bounds__(THREADS, 2) k_scatter(Work wk, int level) {
             if (threadIdx.x == 0) set_error(wk.ctl, kErrBounds);
             return;
         }
-        // write-out: one warp per digit run
-        for (int dd = warp; dd <= static_cast<int>(mask); dd += WARPS) {
-            const uint32_t n = scnt[dd];
-            if (n == 0) continue;
-            const K *s0 = sm_keys + sst[dd];
-            K *g0 = dst + off[dd];
-            for (uint32_t i = lane; i < n; i += 32) g0[i] = s0[i];
+        // write-out in staging order: the key at staging slot q belongs to
+        // digit d's run, so it goes to off[d] + (q - sst[d]); consecutive
+        // slots are consecutive addresses inside a run
+        for (uint32_t q = threadIdx.x; q < ch.len; q += THREADS) {
+            const K key = sm_keys[q];
+            const uint32_t dg = static_cast<uint32_t>(key >> shift) & mask;
+            dst[off[dg] + (q - sst[dg])] = key;
         }
         __syncthreads();
     }
