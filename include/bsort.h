@@ -125,6 +125,31 @@ bsort_status bsort_keys_ws(bsort_handle *handle, void *keys, size_t n, bsort_dty
                            bsort_mode mode, void *workspace, size_t ws_bytes, void *stream);
 
 /*
+ * Runtime tuning of the MSD path of a handle (used by bsort_keys_ws on that
+ * handle), per key width (key_bytes 4 or 8); 1- and 2-byte keys take the
+ * counting path and have nothing to tune.  Zero fields keep the defaults:
+ *   radix_bits  digit width of the MSD levels, 4..8 (default 8): r binary
+ *               partitions of Alg. 1 fused per pass; ceil(w / r) levels;
+ *   unit_keys   largest bucket the shared-memory finish takes, 256..default
+ *               (5104 for 4-byte keys, 2544 for 8-byte keys);
+ *   merge_keys  adjacent small buckets merge up to this many keys, 64..4/5 of
+ *               unit_keys (default 4/5 of unit_keys, rounded down to 64).
+ * The result never depends on the tuning, only the speed.  A workspace for a
+ * tuned handle must be sized with bsort_workspace_bytes_tuned (a smaller
+ * finish threshold needs longer work lists).  NULL restores the defaults.
+ * Invalid fields: BSORT_ERR_INVALID_ARG, nothing changed.
+ */
+typedef struct {
+    int32_t radix_bits;
+    int32_t unit_keys;
+    int32_t merge_keys;
+    int32_t pad;
+} bsort_tuning;
+bsort_status bsort_handle_set_tuning(bsort_handle *handle, int key_bytes, const bsort_tuning *tuning);
+bsort_status bsort_workspace_bytes_tuned(size_t n, bsort_dtype dt, bsort_mode mode, const bsort_tuning *tuning,
+                                         size_t *bytes);
+
+/*
  * Auxiliary device bytes the last call on `handle` used beyond the keys:
  * ping-pong mode, its whole workspace (the alternate buffer included);
  * in-place mode, the metadata plus the largest block buffers, slot states

@@ -64,6 +64,11 @@ class _ServerInfo(ctypes.Structure):
                 ("pad", ctypes.c_int32), ("slot_workspace_bytes", ctypes.c_size_t), ("launches", ctypes.c_uint64)]
 
 
+class _Tuning(ctypes.Structure):
+    _fields_ = [("radix_bits", ctypes.c_int32), ("unit_keys", ctypes.c_int32), ("merge_keys", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
+
+
 class BsortError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = status
@@ -123,6 +128,10 @@ def lib():
         L.bsort_graph_error.restype = i
         L.bsort_graph_destroy.argtypes = [vp]
         L.bsort_graph_destroy.restype = i
+        L.bsort_handle_set_tuning.argtypes = [vp, i, ctypes.POINTER(_Tuning)]
+        L.bsort_handle_set_tuning.restype = i
+        L.bsort_workspace_bytes_tuned.argtypes = [sz, i, i, ctypes.POINTER(_Tuning), ctypes.POINTER(sz)]
+        L.bsort_workspace_bytes_tuned.restype = i
         L.bsort_last_aux_bytes.argtypes = [vp, ctypes.POINTER(sz)]
         L.bsort_last_aux_bytes.restype = i
         L.bsort_server_create.argtypes = [ctypes.POINTER(_ServerConfig), ctypes.POINTER(vp)]
@@ -186,10 +195,23 @@ def bsort_keys(keys, descending: bool = False, stream=None) -> None:
 sort_ = bsort_keys
 
 
-def workspace_bytes(n: int, dtype, mode: int = MODE_PINGPONG) -> int:
+def _tuning(t):
+    if t is None:
+        return None
+    return ctypes.byref(_Tuning(int(t.get("radix_bits", 0)), int(t.get("unit_keys", 0)),
+                                int(t.get("merge_keys", 0)), 0))
+
+
+def workspace_bytes(n: int, dtype, mode: int = MODE_PINGPONG, tuning: dict = None) -> int:
+    """Workspace bytes for bsort_keys_ws; ``tuning`` (a dict with radix_bits,
+    unit_keys, merge_keys) sizes it for a handle tuned that way."""
     out = ctypes.c_size_t(0)
-    _check(lib().bsort_workspace_bytes(int(n), _dtype_code(dtype), int(mode), ctypes.byref(out)),
-           "bsort_workspace_bytes")
+    if tuning is None:
+        _check(lib().bsort_workspace_bytes(int(n), _dtype_code(dtype), int(mode), ctypes.byref(out)),
+               "bsort_workspace_bytes")
+    else:
+        _check(lib().bsort_workspace_bytes_tuned(int(n), _dtype_code(dtype), int(mode), _tuning(tuning),
+                                                 ctypes.byref(out)), "bsort_workspace_bytes_tuned")
     return int(out.value)
 
 
@@ -236,6 +258,11 @@ class Handle:
         return {"calls": int(p.num_calls), "launches": int(p.num_launches), "records": recs,
                 "finish_units": {"counting": int(p.finish_units_counting), "compare": int(p.finish_units_compare),
                                  "lsd": int(p.finish_units_lsd)}}
+
+    def set_tuning(self, key_bytes: int, tuning: dict = None) -> None:
+        """MSD tuning for 4- or 8-byte keys (``bsort_handle_set_tuning``);
+        None restores the defaults."""
+        _check(lib().bsort_handle_set_tuning(self._h, int(key_bytes), _tuning(tuning)), "bsort_handle_set_tuning")
 
     def last_aux_bytes(self) -> int:
         """Auxiliary device bytes of the last call (``bsort_last_aux_bytes``)."""

@@ -69,10 +69,14 @@ struct MsdLayout {
     uint32_t max_big, max_stripes, max_slots;
 };
 
-MsdLayout msd_layout(size_t n, int key_bytes, size_t nseg = 0, bool inplace = false) {
-    const MsdShape s = msd_shape(key_bytes);
+MsdLayout msd_layout(size_t n, int key_bytes, size_t nseg = 0, bool inplace = false, const Tuning &tune = Tuning()) {
+    const MsdShape s = msd_shape(key_bytes, tune);
     MsdLayout L;
-    const uint64_t per_t = n / s.unit_cap + 1;
+    // finish units hold at least merge_cap / 4 keys unless merged, and merged
+    // groups reach merge_cap unless a run ends: the unit count per level is
+    // bounded by n over the smaller of unit_cap and 5/4 merge_cap
+    const uint64_t unit_floor = s.unit_cap < 5ull * s.merge_cap / 4 ? s.unit_cap : 5ull * s.merge_cap / 4;
+    const uint64_t per_t = n / unit_floor + 1;
     L.max_buckets = static_cast<uint32_t>(n / (s.unit_cap + 1) + 2);
     // a bucket of len keys spans ceil((len + misalignment) / chunk) <= 1 + (len + 16) / chunk chunks
     L.max_chunks = static_cast<uint32_t>(L.max_buckets + (n + 16ull * L.max_buckets) / s.chunk + 2);
@@ -193,8 +197,9 @@ bsort_status check_args(const void *keys, size_t n, bsort_dtype dt, DtypeInfo *d
     return BSORT_OK;
 }
 
-Work make_work(const MsdLayout &L, char *ws, void *keys, size_t n, const DtypeInfo &di, const Codec &codec) {
-    const MsdShape s = msd_shape(di.bytes);
+Work make_work(const MsdLayout &L, char *ws, void *keys, size_t n, const DtypeInfo &di, const Codec &codec,
+               const Tuning &tune = Tuning()) {
+    const MsdShape s = msd_shape(di.bytes, tune);
     Work wk;
     wk.ctl = reinterpret_cast<Ctl *>(ws + L.ctl);
     wk.buckets[0] = reinterpret_cast<Bucket *>(ws + L.buckets0);
@@ -220,6 +225,8 @@ Work make_work(const MsdLayout &L, char *ws, void *keys, size_t n, const DtypeIn
     wk.unit_cap = s.unit_cap;
     wk.merge_cap = s.merge_cap;
     wk.w = di.bytes * 8;
+    wk.radix_bits = s.radix_bits;
+    wk.levels = s.levels;
     wk.keys_vec_ok = (reinterpret_cast<uintptr_t>(keys) & 15) == 0;
     wk.inplace = L.inplace;
     wk.ip_big = L.inplace ? reinterpret_cast<IpBig *>(ws + L.ip_big) : nullptr;
@@ -289,11 +296,12 @@ bsort_status run_sort(bsort_handle *h, void *keys, size_t n, const DtypeInfo &di
         h->last_inplace = inplace;  // the counting path writes the keys from counts: in place either way
         h->last_fixed_aux = L.total;
     } else {
-        const MsdLayout L = msd_layout(n, di.bytes, 0, inplace);
+        const Tuning &tune = h->tune[di.bytes == 8];
+        const MsdLayout L = msd_layout(n, di.bytes, 0, inplace, tune);
         if (ws_bytes < L.total) return BSORT_ERR_WORKSPACE_TOO_SMALL;
         h->last_inplace = inplace;
         h->last_fixed_aux = inplace ? L.lists_end - L.ctl : L.total;
-        const Work wk = make_work(L, ws, keys, n, di, codec);
+        const Work wk = make_work(L, ws, keys, n, di, codec, tune);
         if (di.bytes == 4) launch_msd<uint32_t>(wk, st, h->rec, sms);
         else launch_msd<uint64_t>(wk, st, h->rec, sms);
         h->last_path = 2;
@@ -360,8 +368,20 @@ bsort_status grow(void **buf, size_t *have, size_t need) {
     return BSORT_OK;
 }
 
-size_t workspace_for(size_t n, const DtypeInfo &di, bool inplace = false) {
-    return di.bytes <= 2 ? count_layout(n, di.bytes).total : msd_layout(n, di.bytes, 0, inplace).total;
+size_t workspace_for(size_t n, const DtypeInfo &di, bool inplace = false, const Tuning &tune = Tuning()) {
+    return di.bytes <= 2 ? count_layout(n, di.bytes).total : msd_layout(n, di.bytes, 0, inplace, tune).total;
+}
+
+bool to_tuning(const bsort_tuning *in, int key_bytes, Tuning *out) {
+    Tuning t;
+    if (in) {
+        t.radix_bits = in->radix_bits;
+        t.unit_keys = in->unit_keys;
+        t.merge_keys = in->merge_keys;
+    }
+    if (!tuning_valid(key_bytes, t)) return false;
+    *out = t;
+    return true;
 }
 
 }  // namespace
@@ -609,6 +629,26 @@ bsort_status bsort_graph_destroy(bsort_graph *graph) {
     if (graph->exec) cudaGraphExecDestroy(graph->exec);
     if (graph->graph) cudaGraphDestroy(graph->graph);
     delete graph;
+    return BSORT_OK;
+}
+
+bsort_status bsort_handle_set_tuning(bsort_handle *handle, int key_bytes, const bsort_tuning *tuning) {
+    if (!handle || (key_bytes != 4 && key_bytes != 8)) return BSORT_ERR_INVALID_ARG;
+    Tuning t;
+    if (!to_tuning(tuning, key_bytes, &t)) return BSORT_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(handle->mu);
+    handle->tune[key_bytes == 8] = t;
+    return BSORT_OK;
+}
+
+bsort_status bsort_workspace_bytes_tuned(size_t n, bsort_dtype dt, bsort_mode mode, const bsort_tuning *tuning,
+                                         size_t *bytes) {
+    DtypeInfo di;
+    if (!bytes || !dtype_info(dt, &di)) return BSORT_ERR_INVALID_ARG;
+    if (mode != BSORT_MODE_PINGPONG && mode != BSORT_MODE_INPLACE) return BSORT_ERR_INVALID_ARG;
+    Tuning t;
+    if (di.bytes >= 4 && !to_tuning(tuning, di.bytes, &t)) return BSORT_ERR_INVALID_ARG;
+    *bytes = workspace_for(n, di, mode == BSORT_MODE_INPLACE, t);
     return BSORT_OK;
 }
 

@@ -17,9 +17,10 @@
 
 namespace bsort {
 
-constexpr int kRadixBits = 8;
+constexpr int kRadixBits = 8;              // default digit width (and the widest one)
 constexpr int kBins = 1 << kRadixBits;
-constexpr int kMaxLevels = 8;  // ceil(64 / kRadixBits)
+constexpr int kMinRadixBits = 4;           // narrowest tunable digit width
+constexpr int kMaxLevels = 16;             // ceil(64 / kMinRadixBits)
 
 // device error word bits
 constexpr uint32_t kErrCapacity = 1u;
@@ -129,6 +130,8 @@ struct Work {
     uint32_t unit_cap;    // largest run the shared-memory finish sorts
     uint32_t merge_cap;   // adjacent small buckets merge while their sum stays <= this
     int32_t w;            // key bits
+    int32_t radix_bits;   // digit width of the MSD levels (kMinRadixBits..kRadixBits)
+    int32_t levels;       // host-launched MSD levels: ceil(w / radix_bits)
     bool keys_vec_ok;     // caller's buffer is 16-byte aligned (vector loads)
     // in-place mode (digit permutation inside the caller's buffer)
     bool inplace;

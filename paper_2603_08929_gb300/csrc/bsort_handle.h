@@ -24,6 +24,7 @@ struct bsort_handle {
     size_t last_fixed_aux = 0;  // bytes of the last call's workspace outside the in-place buffers
     int last_key_bytes = 0;
     uint64_t last_n = 0;
+    bsort::Tuning tune[2];  // MSD tuning for 4-byte [0] and 8-byte [1] keys (bsort_keys_ws)
     bool profiling = false;
     bool events = false;
     Ctl *prof_ctl = nullptr;  // device slots: work counters of each recorded call

@@ -50,9 +50,21 @@ struct MsdShape {
     uint32_t unit_cap;   // largest bucket finished in shared memory
     uint32_t merge_cap;  // adjacent small buckets merge up to this many keys
     int levels;          // host-side level launches (ceil(w / radix bits))
+    int radix_bits;      // digit width
 };
 
-MsdShape msd_shape(int key_bytes);
+// Runtime tuning of the MSD path (0 fields: defaults).  Digit width 4..8
+// bits; finish threshold between 256 keys and the compile-time tile; merge
+// threshold between 64 keys and the finish threshold.
+struct Tuning {
+    int radix_bits = 0;
+    int unit_keys = 0;
+    int merge_keys = 0;
+};
+
+// false: a field is out of range.
+bool tuning_valid(int key_bytes, const Tuning &t);
+MsdShape msd_shape(int key_bytes, const Tuning &t = Tuning());
 
 // Launches the whole MSD pipeline for 4- or 8-byte keys.
 template <typename K>

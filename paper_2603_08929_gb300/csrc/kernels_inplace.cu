@@ -61,8 +61,8 @@ struct DigitGeo {
     uint32_t mask;
 };
 
-__device__ __forceinline__ DigitGeo digit_geo(const Bucket &b) {
-    const int r_eff = b.h < kRadixBits ? b.h : kRadixBits;
+__device__ __forceinline__ DigitGeo digit_geo(const Bucket &b, int radix_bits) {
+    const int r_eff = b.h < radix_bits ? b.h : radix_bits;
     DigitGeo g;
     g.shift = b.h - r_eff;
     g.mask = (1u << r_eff) - 1u;
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(kIpSmemThreads) k_ip_smem(Work wk, int level) 
     for (uint32_t i = blockIdx.x; i < nb; i += gridDim.x) {
         const Bucket b = wk.buckets[p][i];
         if (!b.scatter || b.len > static_cast<uint64_t>(IpCfg<K>::kSmemCap)) continue;  // block-uniform
-        const DigitGeo g = digit_geo(b);
+        const DigitGeo g = digit_geo(b, wk.radix_bits);
         const int len = static_cast<int>(b.len);
         K *base = keys + b.start;
         for (int j = threadIdx.x; j < len; j += T) keys_s[j] = b.raw ? encode_key(base[j], wk.codec) : base[j];
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(kIpStripeThreads, 2) k_ip_stripe(Work wk, int 
         const IpStripe s = wk.ip_stripes[si];
         const IpBig big = wk.ip_big[s.big];
         const Bucket b = wk.buckets[p][big.bucket];
-        const DigitGeo g = digit_geo(b);
+        const DigitGeo g = digit_geo(b, wk.radix_bits);
         K *base = keys + s.start;
         for (int d = t; d < kBins; d += T) {
             fill[d] = 0;
@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(kIpPermuteThreads) k_ip_permute(Work wk, int l
         const IpStripe s = wk.ip_stripes[si];
         const IpBig big = wk.ip_big[s.big];
         const Bucket b = wk.buckets[p][big.bucket];
-        const C cy{wk, big, s.big, digit_geo(b), keys, ovf};
+        const C cy{wk, big, s.big, digit_geo(b, wk.radix_bits), keys, ovf};
         uint32_t *state = wk.ip_state + big.state0;
         bool fail = false;
         for (uint32_t j = grp; j < s.nfull && !fail; j += GROUPS) {
@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(kIpCleanupThreads) k_ip_cleanup(Work wk, int l
         const uint32_t bb = static_cast<uint32_t>(it / kBins), d = static_cast<uint32_t>(it % kBins);
         const IpBig big = wk.ip_big[bb];
         const Bucket b = wk.buckets[p][big.bucket];
-        const DigitGeo g = digit_geo(b);
+        const DigitGeo g = digit_geo(b, wk.radix_bits);
         if (d > g.mask) continue;
         const uint64_t D0 = dbase(wk, big.bucket, g, d, big.len), D1 = dbase(wk, big.bucket, g, d + 1, big.len);
         const uint64_t N = wk.ip_ncnt[it];

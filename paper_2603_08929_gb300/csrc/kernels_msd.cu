@@ -620,7 +620,7 @@ __global__ void __launch_bounds__(THREADS) k_hist(Work wk, int level) {
     for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) {
         const Chunk ch = wk.chunks[p][c];
         const Bucket b = wk.buckets[p][ch.bucket];
-        const int r_eff = min(kRadixBits, b.h);
+        const int r_eff = min(wk.radix_bits, b.h);
         const int shift = b.h - r_eff;
         const uint32_t mask = (1u << r_eff) - 1;
         for (int i = threadIdx.x; i < WARPS * kBins; i += THREADS) sh[i] = 0;
@@ -816,7 +816,7 @@ __global__ void __launch_bounds__(THREADS) k_classify(Work wk, int level) {
             }
             continue;
         }
-        const int r_eff = min(kRadixBits, b.h);
+        const int r_eff = min(wk.radix_bits, b.h);
         const int shift = b.h - r_eff;
         const uint32_t mask = (1u << r_eff) - 1;
         const int hb = 63 - __clzll(a ^ o);
@@ -1027,7 +1027,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_scatter(Work wk, int level) {
         const K *__restrict__ src = src_of<K>(wk, b.src);
         K *__restrict__ dst = dst_of<K>(wk, b.src);
         const bool vec_ok = b.src ? true : wk.keys_vec_ok;
-        const int r_eff = min(kRadixBits, b.h);
+        const int r_eff = min(wk.radix_bits, b.h);
         const int shift = b.h - r_eff;
         const uint32_t mask = (1u << r_eff) - 1;
         const bool next_same = c + 1 < nch && wk.chunks[p][c + 1].bucket == ch.bucket;
@@ -1525,23 +1525,33 @@ struct Cfg<uint64_t> {
 
 }  // namespace
 
-MsdShape msd_shape(int key_bytes) {
+MsdShape msd_shape(int key_bytes, const Tuning &t) {
     MsdShape s;
     uint32_t fin;
     if (key_bytes == 4) {
         s.tile = Cfg<uint32_t>::kThreads * Cfg<uint32_t>::kItems;
         fin = Cfg<uint32_t>::kFinThreads * Cfg<uint32_t>::kFinItems;
-        s.levels = 4;
     } else {
         s.tile = Cfg<uint64_t>::kThreads * Cfg<uint64_t>::kItems;
         fin = Cfg<uint64_t>::kFinThreads * Cfg<uint64_t>::kFinItems;
-        s.levels = 8;
     }
+    s.radix_bits = t.radix_bits ? t.radix_bits : kRadixBits;
+    s.levels = (key_bytes * 8 + s.radix_bits - 1) / s.radix_bits;
     s.chunk = 2 * s.tile;
-    s.unit_cap = fin - 16;  // a unit plus its misalignment fits one aligned finish window
+    // a unit plus its misalignment fits one aligned finish window
+    s.unit_cap = t.unit_keys ? static_cast<uint32_t>(t.unit_keys) : fin - 16;
     // tiny buckets (<= merge_cap / 4) group below 1.25 * merge_cap <= unit_cap
-    s.merge_cap = (s.unit_cap * 4 / 5) & ~63u;
+    s.merge_cap = t.merge_keys ? static_cast<uint32_t>(t.merge_keys) : (s.unit_cap * 4 / 5) & ~63u;
     return s;
+}
+
+bool tuning_valid(int key_bytes, const Tuning &t) {
+    const MsdShape d = msd_shape(key_bytes);
+    if (t.radix_bits && (t.radix_bits < kMinRadixBits || t.radix_bits > kRadixBits)) return false;
+    if (t.unit_keys && (t.unit_keys < 256 || static_cast<uint32_t>(t.unit_keys) > d.unit_cap)) return false;
+    const uint32_t unit = t.unit_keys ? static_cast<uint32_t>(t.unit_keys) : d.unit_cap;
+    if (t.merge_keys && (t.merge_keys < 64 || 5ull * static_cast<uint32_t>(t.merge_keys) > 4ull * unit)) return false;
+    return true;
 }
 
 template <typename K>
@@ -1567,9 +1577,8 @@ void msd_levels_and_finish(const Work &wk, cudaStream_t st, Recorder &rec, int n
     constexpr int T = Cfg<K>::kThreads, I = Cfg<K>::kItems;
     constexpr int FT = Cfg<K>::kFinThreads, FI = Cfg<K>::kFinItems;
     constexpr int CT = 2;  // tiles per chunk
-    const MsdShape shape = msd_shape(sizeof(K));
     if (levels) {
-        for (int level = 0; level < shape.levels; ++level) {
+        for (int level = 0; level < wk.levels; ++level) {
             rec.begin(BSORT_K_HIST, level);
             k_hist<K, 512><<<num_sms * 4, 512, 0, st>>>(wk, level);
             rec.end();
@@ -1602,8 +1611,7 @@ void msd_levels_and_finish(const Work &wk, cudaStream_t st, Recorder &rec, int n
 template <typename K>
 void launch_msd(const Work &wk, cudaStream_t st, Recorder &rec, int num_sms) {
     msd_prepare<K>();
-    const MsdShape shape = msd_shape(sizeof(K));
-    const bool direct = wk.n <= shape.unit_cap;
+    const bool direct = wk.n <= wk.unit_cap;
     const uint32_t nc0 = direct ? 0u : static_cast<uint32_t>((wk.n + wk.chunk_keys - 1) / wk.chunk_keys);
     rec.begin(BSORT_K_INIT, -1);
     k_init<<<direct ? 1 : max(1u, min(1024u, (nc0 + 255) / 256)), 256, 0, st>>>(wk, nc0, direct ? 1 : 0);
