@@ -354,9 +354,11 @@ def run_serve(args, rank, world):
     producer = torch.cuda.Stream()
     torch.cuda.synchronize()
 
+    smode = bs.MODE_INPLACE if args.inplace else bs.MODE_PINGPONG
+
     def serve(num_slots, max_batch, batch_keys, seconds):
         srv = bs.Server(num_slots=num_slots, hbm_budget_bytes=int(args.serve_budget_gb * (1 << 30)),
-                        max_request_keys=pool_n, max_batch=max_batch, batch_keys=batch_keys)
+                        max_request_keys=pool_n, max_batch=max_batch, batch_keys=batch_keys, mode=smode)
         last = int(np.searchsorted(tr["t"], seconds))
         lat, wait, done_keys = [], [], 0
         first_submit, last_done = None, 0
@@ -395,7 +397,8 @@ def run_serve(args, rank, world):
                 "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
                 "queue_p99_ms": float(np.percentile(np.array(wait), 99)),
                 "batches": st["batches"], "max_concurrent_slots": st["max_concurrent_slots"],
-                "peak_in_flight_gb": st["peak_in_flight_bytes"] / 1e9, "launches": st["launches"]}
+                "peak_in_flight_gb": st["peak_in_flight_bytes"] / 1e9, "launches": st["launches"],
+                "slot_workspace_gb": st["slot_workspace_bytes"] / 1e9}
 
     serve(args.serve_slots, 16, 1 << 20, min(2.0, args.serve_seconds))  # warm-up
     clocks = ClockSampler(torch.cuda.current_device())
@@ -409,8 +412,9 @@ def run_serve(args, rank, world):
         "vs_baseline": None, "dtype": "i16+i32+f32+f64", "data": "synthetic",
         "config": {"workload": "served sorting: Poisson %.0f requests/s for %.0f s, sizes log-uniform in "
                                "[2^10, 2^24], int16 25%% / int32 35%% / float32 30%% / float64 10%%, uniform "
-                               "or normal(0, 1) values, %.0f GB HBM budget, %d slots"
-                               % (args.serve_rate, args.serve_seconds, args.serve_budget_gb, args.serve_slots),
+                               "or normal(0, 1) values, %.0f GB HBM budget, %d slots, %s mode"
+                               % (args.serve_rate, args.serve_seconds, args.serve_budget_gb, args.serve_slots,
+                                  "in-place" if args.inplace else "ping-pong"),
                    "l2": "each request sorts a fresh copy of a window of a 2^24-key device pool"},
         "serve": main_arm,
         "fifo_one_slot": fifo,

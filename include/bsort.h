@@ -230,6 +230,8 @@ typedef struct {
     size_t hbm_budget_bytes;    /* admission budget */
     size_t max_request_keys;    /* largest request accepted (sizes the slot workspaces) */
     size_t batch_keys;          /* a slot batches requests while their total keys stay <= this */
+    int32_t mode;               /* bsort_mode of every sort (in-place: smaller workspaces) */
+    int32_t pad;
 } bsort_server_config;
 typedef struct {
     uint64_t tag;

@@ -49,7 +49,8 @@ class _Profile(ctypes.Structure):
 
 class _ServerConfig(ctypes.Structure):
     _fields_ = [("num_slots", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_size_t),
-                ("max_request_keys", ctypes.c_size_t), ("batch_keys", ctypes.c_size_t)]
+                ("max_request_keys", ctypes.c_size_t), ("batch_keys", ctypes.c_size_t), ("mode", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
 
 
 class _Completion(ctypes.Structure):
@@ -374,8 +375,8 @@ class Server:
     keeps a reference to each request's tensor until its completion is polled."""
 
     def __init__(self, num_slots: int = 8, hbm_budget_bytes: int = 64 << 30, max_request_keys: int = 1 << 24,
-                 max_batch: int = 8, batch_keys: int = 1 << 20):
-        cfg = _ServerConfig(num_slots, max_batch, hbm_budget_bytes, max_request_keys, batch_keys)
+                 max_batch: int = 8, batch_keys: int = 1 << 20, mode: int = MODE_PINGPONG):
+        cfg = _ServerConfig(num_slots, max_batch, hbm_budget_bytes, max_request_keys, batch_keys, int(mode), 0)
         srv = ctypes.c_void_p()
         _check(lib().bsort_server_create(ctypes.byref(cfg), ctypes.byref(srv)), "bsort_server_create")
         self._s = srv

@@ -140,8 +140,8 @@ bool bsort_server::step() {
             Request &r = s.batch[j];
             s.err[j] = 0;
             s.handle->last_ctl = nullptr;
-            r.launch = bsort_keys_ws(s.handle, r.keys, r.n, r.dt, r.desc, BSORT_MODE_PINGPONG, s.ws, s.ws_bytes,
-                                     s.stream);
+            r.launch = bsort_keys_ws(s.handle, r.keys, r.n, r.dt, r.desc, static_cast<bsort_mode>(cfg.mode), s.ws,
+                                     s.ws_bytes, s.stream);
             if (r.launch == BSORT_ERR_CUDA) fatal.store(r.launch);
             launches += static_cast<uint64_t>(s.handle->rec.launches);
             // the next request of the batch reuses the workspace (and its error word): copy this one's out
@@ -173,7 +173,8 @@ extern "C" {
 
 bsort_status bsort_server_create(const bsort_server_config *cfg, bsort_server **out) {
     if (!cfg || !out || cfg->num_slots < 1 || cfg->num_slots > 64 || cfg->max_request_keys < 2 ||
-        cfg->max_batch < 1 || cfg->max_batch > 4096)
+        cfg->max_batch < 1 || cfg->max_batch > 4096 ||
+        (cfg->mode != BSORT_MODE_PINGPONG && cfg->mode != BSORT_MODE_INPLACE))
         return BSORT_ERR_INVALID_ARG;
     bsort_server *s = new (std::nothrow) bsort_server();
     if (!s) return BSORT_ERR_NO_MEMORY;
@@ -183,7 +184,8 @@ bsort_status bsort_server_create(const bsort_server_config *cfg, bsort_server **
     size_t ws = 0;
     for (int dt = 0; dt <= 10; ++dt) {
         size_t b = 0;
-        if (bsort_workspace_bytes(cfg->max_request_keys, static_cast<bsort_dtype>(dt), BSORT_MODE_PINGPONG, &b) ==
+        if (bsort_workspace_bytes(cfg->max_request_keys, static_cast<bsort_dtype>(dt),
+                                  static_cast<bsort_mode>(cfg->mode), &b) ==
                 BSORT_OK &&
             b > ws)
             ws = b;
@@ -215,7 +217,7 @@ bsort_status bsort_server_submit(bsort_server *s, void *keys, size_t n, bsort_dt
     if (reinterpret_cast<uintptr_t>(keys) % b) return BSORT_ERR_MISALIGNED;
     if (s->fatal.load()) return static_cast<bsort_status>(s->fatal.load());
     size_t ws = 0;
-    bsort_workspace_bytes(n, dt, BSORT_MODE_PINGPONG, &ws);
+    bsort_workspace_bytes(n, dt, static_cast<bsort_mode>(s->cfg.mode), &ws);
     Request r{keys, n, dt, descending, tag, now_ns(), 0, n * static_cast<size_t>(b) + ws, BSORT_OK};
     {
         std::lock_guard<std::mutex> lk(s->mu);
