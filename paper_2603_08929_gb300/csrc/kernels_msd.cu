@@ -145,6 +145,17 @@ __device__ __forceinline__ void block_and_or(unsigned long long &a, unsigned lon
 // out at compile-time offsets, so addresses are one base plus a constant.
 extern __shared__ __align__(16) unsigned char g_dyn_smem[];
 
+// 16-byte asynchronous copy global -> shared (no register, no stall until
+// the wait), used to fetch the next work descriptor a unit ahead.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(smem))),
+                 "l"(gmem)
+                 : "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Shared-memory buffers of one tile ranking, at byte offset BASE of dynamic
 // shared memory.  Unstable ranking uses one CTA-wide counter row; stable
 // ranking uses per-digit, per-warp counters laid out digit-major with one pad
@@ -1142,7 +1153,8 @@ struct FinLayout {
     static constexpr size_t kTa = kShared;
     static constexpr size_t kTo = kTa + sizeof(K) * WARPS;
     static constexpr size_t kScan = kTo + sizeof(K) * WARPS;
-    static constexpr size_t kEnd = kScan + 4 * (WARPS + 1);
+    static constexpr size_t kNext = (kScan + 4 * (WARPS + 1) + 15) & ~size_t(15);  // Unit[2]
+    static constexpr size_t kEnd = kNext + 2 * sizeof(Unit);
     static_assert(sizeof(K) * (kTile + V) <= kTotals, "staging overlaps only the counter words");
     static_assert(kSplitCap == 16 * THREADS, "the scan gives each thread 16 sub-buckets");
 };
@@ -1187,8 +1199,14 @@ __global__ void __launch_bounds__(THREADS, 4) k_finish(Work wk) {
     if (wk.ctl->error) return;
     const uint32_t nu = min(wk.ctl->n_units, wk.max_units);
     K *__restrict__ out = static_cast<K *>(wk.keys);
-    for (uint32_t u = blockIdx.x; u < nu; u += gridDim.x) {
-        const Unit un = wk.units[u];
+    Unit *next = reinterpret_cast<Unit *>(g_dyn_smem + FL::kNext);  // descriptors, double-buffered
+    if (t == 0 && blockIdx.x < nu) cp_async16(&next[0], &wk.units[blockIdx.x]);
+    int it = 0;
+    for (uint32_t u = blockIdx.x; u < nu; u += gridDim.x, ++it) {
+        if (t == 0) cp_async_wait_all();
+        __syncthreads();
+        const Unit un = next[it & 1];
+        if (t == 0 && u + gridDim.x < nu) cp_async16(&next[(it + 1) & 1], &wk.units[u + gridDim.x]);
         const bool raw = un.raw;
         const K *__restrict__ src = src_of<K>(wk, un.src) + un.start;
         K *__restrict__ dstp = out + un.start;
