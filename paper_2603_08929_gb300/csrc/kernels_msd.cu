@@ -156,6 +156,21 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(smem))),
+                 "l"(gmem)
+                 : "memory");
+}
+
+// What the scatter needs of one chunk before it can stage keys: the chunk,
+// the next chunk (same bucket or not), the bucket, and per digit the chunk's
+// exclusive prefix, the next chunk's, and the bucket's digit base.
+struct ScatterPre {
+    Chunk ch, chn;
+    Bucket b;
+    uint32_t hc[kBins], hn[kBins], bb[kBins];
+};
+
 // Shared-memory buffers of one tile ranking, at byte offset BASE of dynamic
 // shared memory.  Unstable ranking uses one CTA-wide counter row; stable
 // ranking uses per-digit, per-warp counters laid out digit-major with one pad
@@ -1013,6 +1028,13 @@ __device__ __forceinline__ void stage_keys(const K (&k)[ITEMS], uint32_t vmask, 
 // write-out, so runs are long and coalesced.  Every run's destination is
 // checked against the bucket before anything is written.
 template <typename K, int THREADS, int ITEMS, int CHUNK_TILES>
+__host__ __device__ constexpr size_t scatter_pre_offset() {
+    return (sizeof(K) * THREADS * ITEMS * CHUNK_TILES + sizeof(unsigned long long) * kBins +
+            sizeof(uint32_t) * (3 * kBins + THREADS / 32 + 1) + 16 + 15) &
+           ~size_t(15);
+}
+
+template <typename K, int THREADS, int ITEMS, int CHUNK_TILES>
 __global__ void __launch_bounds__(THREADS, 2) k_scatter(Work wk, int level) {
     using L = TileLoad<K, THREADS, ITEMS>;
     constexpr int TILE = THREADS * ITEMS;
@@ -1026,14 +1048,59 @@ __global__ void __launch_bounds__(THREADS, 2) k_scatter(Work wk, int level) {
     uint32_t *scnt = sst + kBins;                                // [kBins] chunk counts
     uint32_t *tmp = scnt + kBins;                                // [WARPS + 1]
     int *bad = reinterpret_cast<int *>(tmp + WARPS + 1);
+    constexpr size_t kPreOff = scatter_pre_offset<K, THREADS, ITEMS, CHUNK_TILES>();
+    ScatterPre *pre = reinterpret_cast<ScatterPre *>(g_dyn_smem + kPreOff);
     const int p = level & 1;
+    const int t = threadIdx.x;
     if (wk.ctl->error) return;
-    if (threadIdx.x == 0) *bad = 0;  // stays 0 unless a check fails (then the CTA stops)
-    __syncthreads();
+    if (t == 0) *bad = 0;  // stays 0 unless a check fails (then the CTA stops)
     const uint32_t nch = wk.ctl->n_chunks[p];
-    for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) {
-        const Chunk ch = wk.chunks[p][c];
-        const Bucket b = wk.buckets[p][ch.bucket];
+    // Chunk metadata arrives by cp.async two chunks ahead in a ring of three
+    // slots: stage 1 (needs only the chunk index) fetches the chunk records
+    // and the chunk's prefix counts; stage 2 (needs the chunk's bucket) the
+    // bucket and its digit bases.
+    auto stage1 = [&](uint32_t c, int slot) {
+        ScatterPre &P = pre[slot];
+        if (t == 0) {
+            cp_async16(&P.ch, &wk.chunks[p][c]);
+            if (c + 1 < nch) cp_async16(&P.chn, &wk.chunks[p][c + 1]);
+            else P.chn.bucket = 0xffffffffu;
+        }
+        if (t < kBins) {
+            cp_async4(&P.hc[t], &wk.hist[static_cast<size_t>(t) * wk.max_chunks + c]);
+            if (c + 1 < nch) cp_async4(&P.hn[t], &wk.hist[static_cast<size_t>(t) * wk.max_chunks + c + 1]);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    auto stage2 = [&](int slot) {
+        ScatterPre &P = pre[slot];
+        const uint32_t bk = P.ch.bucket;
+        if (t == 0) {
+            cp_async16(&P.b, &wk.buckets[p][bk]);
+            cp_async16(reinterpret_cast<char *>(&P.b) + 16, reinterpret_cast<const char *>(&wk.buckets[p][bk]) + 16);
+        }
+        if (t < kBins) cp_async4(&P.bb[t], &wk.bucket_base[static_cast<size_t>(bk) * kBins + t]);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    if (blockIdx.x < nch) {
+        stage1(blockIdx.x, 0);
+        cp_async_wait_all();
+        __syncthreads();
+        stage2(0);
+        if (blockIdx.x + gridDim.x < nch) stage1(blockIdx.x + gridDim.x, 1);
+    }
+    int it = 0;
+    for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x, ++it) {
+        cp_async_wait_all();
+        __syncthreads();
+        {
+            const uint32_t c1 = c + gridDim.x, c2 = c1 + gridDim.x;
+            if (c1 < nch) stage2((it + 1) % 3);
+            if (c2 < nch) stage1(c2, (it + 2) % 3);
+        }
+        const ScatterPre &P = pre[it % 3];
+        const Chunk ch = P.ch;
+        const Bucket b = P.b;
         if (!b.scatter) continue;  // block-uniform
         const K *__restrict__ src = src_of<K>(wk, b.src);
         K *__restrict__ dst = dst_of<K>(wk, b.src);
@@ -1041,23 +1108,21 @@ __global__ void __launch_bounds__(THREADS, 2) k_scatter(Work wk, int level) {
         const int r_eff = min(wk.radix_bits, b.h);
         const int shift = b.h - r_eff;
         const uint32_t mask = (1u << r_eff) - 1;
-        const bool next_same = c + 1 < nch && wk.chunks[p][c + 1].bucket == ch.bucket;
+        const bool next_same = P.chn.bucket == ch.bucket;
         // chunk digit counts and destinations
         const int d = threadIdx.x;
         uint32_t n_d = 0;
         if (d < kBins && static_cast<uint32_t>(d) <= mask) {
-            const uint32_t *bb = wk.bucket_base + static_cast<size_t>(ch.bucket) * kBins;
-            const uint32_t ex = wk.hist[static_cast<size_t>(d) * wk.max_chunks + c];
+            const uint32_t ex = P.hc[d];
             uint32_t ex_next;
             if (next_same) {
-                ex_next = wk.hist[static_cast<size_t>(d) * wk.max_chunks + c + 1];
+                ex_next = P.hn[d];
             } else {  // last chunk of the bucket: the digit's bucket total
-                const uint32_t base_d = bb[d];
-                const uint32_t base_n = static_cast<uint32_t>(d) < mask ? bb[d + 1] : static_cast<uint32_t>(b.len);
-                ex_next = base_n - base_d;
+                const uint32_t base_n = static_cast<uint32_t>(d) < mask ? P.bb[d + 1] : static_cast<uint32_t>(b.len);
+                ex_next = base_n - P.bb[d];
             }
             n_d = ex_next - ex;
-            const unsigned long long o = b.start + bb[d] + ex;
+            const unsigned long long o = b.start + P.bb[d] + ex;
             off[d] = o;
             if (n_d && o + n_d > b.start + b.len) *bad = 1;  // never write outside the bucket
         }
@@ -1073,7 +1138,8 @@ __global__ void __launch_bounds__(THREADS, 2) k_scatter(Work wk, int level) {
         __syncthreads();
         if (*bad) {
             if (threadIdx.x == 0) set_error(wk.ctl, kErrBounds);
-            return;  // block-uniform
+            cp_async_wait_all();  // no copy may land after the CTA is gone
+            return;               // block-uniform
         }
         // stage: every key takes the next slot of its digit.  The loop body
         // is specialised per tile (block-uniform): keys still raw or already
@@ -1109,6 +1175,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_scatter(Work wk, int level) {
         }
         if (__syncthreads_or(overflow)) {
             if (threadIdx.x == 0) set_error(wk.ctl, kErrBounds);
+            cp_async_wait_all();
             return;
         }
         // write-out in staging order: the key at staging slot q belongs to
@@ -1125,8 +1192,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_scatter(Work wk, int level) {
 
 template <typename K, int THREADS, int ITEMS, int CHUNK_TILES>
 constexpr size_t scatter_smem() {
-    return sizeof(K) * THREADS * ITEMS * CHUNK_TILES + sizeof(unsigned long long) * kBins +
-           sizeof(uint32_t) * (3 * kBins + THREADS / 32 + 1) + 16;
+    return scatter_pre_offset<K, THREADS, ITEMS, CHUNK_TILES>() + 3 * sizeof(ScatterPre);
 }
 
 // Shared-memory layout of k_finish.  Two alternatives share the first region:
