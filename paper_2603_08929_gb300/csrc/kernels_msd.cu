@@ -1336,6 +1336,7 @@ __global__ void __launch_bounds__(THREADS, 4) k_finish(Work wk) {
             }
             if (!__syncthreads_or(ovf)) {
                 // sub-bucket starts: thread t owns sub-buckets [16t, 16t + 16)
+                bool small;
                 {
                     const uint4 *tv = reinterpret_cast<const uint4 *>(tot32) + 2 * t;
                     const uint4 q0 = tv[0], q1 = tv[1];
@@ -1356,12 +1357,39 @@ __global__ void __launch_bounds__(THREADS, 4) k_finish(Work wk) {
                     uint4 *sv = reinterpret_cast<uint4 *>(st32) + 2 * t;
                     sv[0] = make_uint4(o[0], o[1], o[2], o[3]);
                     sv[1] = make_uint4(o[4], o[5], o[6], o[7]);
+                    small = true;
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) small &= (c[e] & 0xffffu) < 16u && (c[e] >> 16) < 16u;
                 }
-                __syncthreads();
+                // every sub-bucket under 16 keys: turn its counters into exclusive
+                // prefix counters in place (multiplying by 0x1111... sums the
+                // nibbles below each nibble without carries), so a key's
+                // offset inside its sub-bucket is one nibble
+                const bool prefix = __syncthreads_and(small);
+                if (prefix) {
+#pragma unroll
+                    for (int e = 0; e < kSplitCap / THREADS; ++e) {
+                        const int sb = e * THREADS + t;
+                        words[sb] = (words[sb] * 0x1111111111111111ull) << 4;
+                    }
+                    __syncthreads();
+                }
                 // positions: sub-bucket start + keys of lower low values + arrival rank
                 uint32_t posr[(ITEMS + 1) / 2];
 #pragma unroll
                 for (int j = 0; j < (ITEMS + 1) / 2; ++j) posr[j] = 0;
+                if (prefix) {
+#pragma unroll
+                    for (int j = 0; j < ITEMS; ++j) {
+                        if ((vm >> j) & 1u) {
+                            const uint32_t f = static_cast<uint32_t>(k[j] >> lo) & fmask;
+                            const uint32_t low = f & lmask, sb = f >> lbits;
+                            const uint32_t below = (w32[2 * sb + (low >> 3)] >> (4 * (low & 7u))) & 15u;
+                            const uint32_t pos = st16[sb] + below + ((arr[j >> 3] >> (4 * (j & 7))) & 15u);
+                            posr[j >> 1] |= pos << ((j & 1) * 16);
+                        }
+                    }
+                } else {
 #pragma unroll
                 for (int j = 0; j < ITEMS; ++j) {
                     if ((vm >> j) & 1u) {
@@ -1378,6 +1406,7 @@ __global__ void __launch_bounds__(THREADS, 4) k_finish(Work wk) {
                         const uint32_t pos = st16[sb] + below + ((arr[j >> 3] >> (4 * (j & 7))) & 15u);
                         posr[j >> 1] |= pos << ((j & 1) * 16);
                     }
+                }
                 }
                 __syncthreads();
                 // keys to the staging buffer (slot lo_r + position), then out
