@@ -1133,6 +1133,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_scatter(Work wk, int level) {
             sst[d] = st;
             cur[d] = st;
             scnt[d] = n_d;
+            off[d] -= st;  // the key at staging slot q of digit d goes to off[d] + q (mod 2^64)
         }
         if (total != ch.len && threadIdx.x == 0) *bad = 1;
         __syncthreads();
@@ -1179,12 +1180,13 @@ __global__ void __launch_bounds__(THREADS, 2) k_scatter(Work wk, int level) {
             return;
         }
         // write-out in staging order: the key at staging slot q belongs to
-        // digit d's run, so it goes to off[d] + (q - sst[d]); consecutive
-        // slots are consecutive addresses inside a run
+        // digit d's run, so it goes to off[d] + q (off[d] holds the run's
+        // destination minus its staging start); consecutive slots are
+        // consecutive addresses inside a run
         for (uint32_t q = threadIdx.x; q < ch.len; q += THREADS) {
             const K key = sm_keys[q];
             const uint32_t dg = static_cast<uint32_t>(key >> shift) & mask;
-            dst[off[dg] + (q - sst[dg])] = key;
+            dst[off[dg] + q] = key;
         }
         __syncthreads();
     }
