@@ -15,16 +15,19 @@
 //                   under-full rest of each digit goes to a per-stripe buffer;
 //     k_ip_permute  digit d owns the block slots [A_d, A_d + N_d) of the bucket,
 //                   A_d = ceil(D_d / B) (D_d: digit base, N_d: its full blocks).
-//                   Warps carry blocks to slots: a block's digit names its next
-//                   free slot (an atomic cursor); the block already there, if
-//                   not yet moved, is taken along (a CAS on the slot's state
-//                   decides who takes it), so every block moves exactly once
-//                   and no warp ever waits for anything but a read in progress;
+//                   Each block's slot is fixed by the classification: its
+//                   stripe's share of digit d (claimed per stripe) plus its
+//                   rank there.  Groups of lanes carry blocks: the block at the
+//                   destination, if not yet moved, is taken along (an atomic OR
+//                   on the slot's state word decides who takes it and returns
+//                   its digit and rank), so every block moves exactly once and
+//                   nothing ever waits for anything but a read in progress;
 //     k_ip_cleanup  per digit, the partial blocks of all stripes and the part of
 //                   the digit's last block that crossed D_{d+1} (kept aside by
 //                   the carrier) fill the rest of the digit's range.
-// Auxiliary memory: counters, one partial-block buffer per stripe, one
-// overflow block per (bucket, digit) and one state word per block slot.
+// Auxiliary memory: counters, one partial-block buffer and one digit-share
+// row per stripe, one overflow block per (bucket, digit) and one state word
+// per block slot.
 #include "bsort_launch.h"
 
 namespace bsort {
@@ -33,10 +36,15 @@ namespace {
 
 constexpr unsigned kFullMask = 0xffffffffu;
 
-// slot states
-constexpr uint32_t kSlotFull = 0;   // holds a block that has not moved yet
-constexpr uint32_t kSlotTaken = 1;  // a warp is reading the block out
-constexpr uint32_t kSlotHole = 2;   // nothing left to read
+// Slot state word: bits 31-30 the state, bits 29-22 the digit of the block
+// the slot held after classification, bits 21-0 its rank among its stripe's
+// blocks of that digit.  OR-ing kSlotTaken takes a full slot and leaves the
+// other states as they are; the old word says what was taken.
+constexpr uint32_t kSlotFull = 0u << 30;   // holds a block that has not moved yet
+constexpr uint32_t kSlotTaken = 1u << 30;  // a group is reading the block out
+constexpr uint32_t kSlotHole = 3u << 30;   // nothing left to read
+constexpr uint32_t kSlotStateMask = 3u << 30;
+constexpr uint32_t kStripeBlocks = static_cast<uint32_t>(kIpStripeBytes / kIpBlockBytes);
 
 constexpr int kIpStripeThreads = 512;
 constexpr int kIpPermuteThreads = 256;
@@ -131,7 +139,6 @@ __global__ void k_ip_plan(Work wk, int level) {
             }
             for (uint32_t d = threadIdx.x; d < kBins; d += blockDim.x) {
                 wk.ip_ncnt[static_cast<size_t>(bb) * kBins + d] = 0;
-                wk.ip_cursor[static_cast<size_t>(bb) * kBins + d] = 0;
             }
         }
         __syncthreads();
@@ -282,6 +289,7 @@ __global__ void __launch_bounds__(kIpStripeThreads, 2) k_ip_stripe(Work wk, int 
                 const uint32_t cd = cnt[d], fd = fill[d], sd = tstart[d];
                 const uint32_t totd = fd + cd, nb = totd / B;
                 const uint32_t slot = blk[d];
+                const uint32_t rank0 = nfull[d];
                 for (uint32_t kb = 0; kb < nb; ++kb) {
                     if (lane < B) {
                         const uint32_t idx = kb * B + lane;
@@ -290,6 +298,9 @@ __global__ void __launch_bounds__(kIpStripeThreads, 2) k_ip_stripe(Work wk, int 
                         if (pos < t0 + static_cast<uint64_t>(tlen)) base[pos] = v;  // never past what was read
                         else ip_error(wk, kErrBounds);
                     }
+                    if (lane == 0)
+                        wk.ip_state[big.state0 + s.slot0 + slot + kb] =
+                            kSlotFull | (static_cast<uint32_t>(d) << 22) | (rank0 + kb);
                 }
                 __syncwarp();
                 const uint32_t from = nb * B > fd ? nb * B : fd;  // first stream index not yet in the buffer
@@ -304,8 +315,11 @@ __global__ void __launch_bounds__(kIpStripeThreads, 2) k_ip_stripe(Work wk, int 
             __syncthreads();
         }
         // stripe summary: full-block counts, partial blocks, slot states
+        // this stripe's blocks of digit d take the digit's slots [P, P + nfull)
+        // past its slot base, P claimed here in any order of the stripes
         for (int d = t; d < kBins; d += T) {
-            if (nfull[d]) atomicAdd(&wk.ip_ncnt[static_cast<size_t>(s.big) * kBins + d], nfull[d]);
+            wk.ip_prefix[static_cast<size_t>(si) * kBins + d] =
+                nfull[d] ? atomicAdd(&wk.ip_ncnt[static_cast<size_t>(s.big) * kBins + d], nfull[d]) : 0u;
             wk.ip_rem[static_cast<size_t>(si) * kBins + d] = static_cast<uint8_t>(fill[d]);
         }
         K *part = static_cast<K *>(wk.ip_part) + static_cast<size_t>(si) * kBins * B;
@@ -314,8 +328,7 @@ __global__ void __launch_bounds__(kIpStripeThreads, 2) k_ip_stripe(Work wk, int 
             if (static_cast<uint32_t>(e) < fill[d]) part[i] = buf[i];
         }
         const uint32_t nslots = (s.len + B - 1) / B;
-        for (uint32_t j = t; j < nslots; j += T)
-            wk.ip_state[big.state0 + s.slot0 + j] = j < wp ? kSlotFull : kSlotHole;
+        for (uint32_t j = wp + t; j < nslots; j += T) wk.ip_state[big.state0 + s.slot0 + j] = kSlotHole;
         if (t == 0) wk.ip_stripes[si].nfull = wp;
         __syncthreads();
     }
@@ -339,10 +352,15 @@ struct Carry {
     K *keys;
     K *ovf;
 
+    // Reads the block in slot `slot` (keys past the bucket's end, in its last
+    // partial slot, are not read).
     __device__ void load(uint32_t slot, int gl, K (&v)[E]) const {
-        const K *src = keys + big.start + static_cast<uint64_t>(slot) * B + gl;
+        const uint64_t p0 = static_cast<uint64_t>(slot) * B + gl;
 #pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = src[e * kGroup];
+        for (int e = 0; e < E; ++e) {
+            const uint64_t pos = p0 + e * kGroup;
+            v[e] = pos < big.len ? keys[big.start + pos] : K(0);
+        }
     }
 
     // Writes a block of digit d into slot `slot`; keys past D_{d+1} go to the
@@ -379,56 +397,64 @@ __global__ void __launch_bounds__(kIpPermuteThreads) k_ip_permute(Work wk, int l
         const Bucket b = wk.buckets[p][big.bucket];
         const C cy{wk, big, s.big, digit_geo(b, wk.radix_bits), keys, ovf};
         uint32_t *state = wk.ip_state + big.state0;
+        const uint32_t nslots = static_cast<uint32_t>((big.len + B - 1) / B);
+        // destination of the block whose state word is w and whose slot was `slot`:
+        // digit d's slot base + its stripe's share of d + its rank
+        auto dest = [&](uint32_t w, uint32_t slot, uint32_t &d) {
+            d = (w >> 22) & 0xFFu;
+            const uint32_t home = big.first_stripe + slot / kStripeBlocks;
+            const uint64_t a_d = (dbase(wk, big.bucket, cy.g, d, big.len) + B - 1) / B;
+            return static_cast<uint32_t>(a_d + wk.ip_prefix[static_cast<size_t>(home) * kBins + d] + (w & 0x3FFFFFu));
+        };
         bool fail = false;
         for (uint32_t j = grp; j < s.nfull && !fail; j += GROUPS) {
             const uint32_t seed = s.slot0 + j;
-            uint32_t got = 0;
-            if (gl == 0) got = atomicCAS(&state[seed], kSlotFull, kSlotTaken) == kSlotFull;
-            if (!__shfl_sync(gmask, got, leader)) continue;
+            uint32_t old = kSlotHole;
+            if (gl == 0) old = atomicOr(&state[seed], kSlotTaken);
+            old = __shfl_sync(gmask, old, leader);
+            if ((old & kSlotStateMask) != kSlotFull) continue;
             // take the seed block out, then free its slot
             K x[E];
             cy.load(seed, gl, x);
             __syncwarp(gmask);
             if (gl == 0) {
                 __threadfence();
-                atomicExch(&state[seed], kSlotHole);
+                atomicOr(&state[seed], kSlotHole);
             }
+            uint32_t xw = old, xslot = seed;  // the carried block's state word and original slot
             // carry until the block lands on a slot that holds nothing to take
             for (int hop = 0;; ++hop) {
-                const uint32_t d = digit_of(__shfl_sync(gmask, x[0], leader), cy.g);
-                uint32_t dst = 0, st = kSlotHole, ok = 1;
-                if (gl == 0) {
-                    const size_t di = static_cast<size_t>(s.big) * kBins + d;
-                    const uint32_t c = atomicAdd(&wk.ip_cursor[di], 1u);
-                    const uint64_t a_d = (dbase(wk, big.bucket, cy.g, d, big.len) + B - 1) / B;
-                    if (c >= wk.ip_ncnt[di]) ok = 0;
-                    dst = static_cast<uint32_t>(a_d) + c;
-                    if (ok) st = atomicCAS(&state[dst], kSlotFull, kSlotTaken);
-                }
-                ok = __shfl_sync(gmask, ok, leader);
-                if (!ok || hop > (1 << 26)) {
+                uint32_t d;
+                const uint32_t dst = dest(xw, xslot, d);
+                if (dst >= nslots || hop > (1 << 26)) {
                     if (gl == 0) ip_error(wk, kErrBounds);
                     fail = true;
                     break;
                 }
-                dst = __shfl_sync(gmask, dst, leader);
-                st = __shfl_sync(gmask, st, leader);
-                if (st == kSlotFull) {
-                    // we took the block at dst: read it, put ours, carry it on
-                    K y[E];
-                    cy.load(dst, gl, y);
+                // take whatever dst holds and read it in the same round trip
+                // (the read is used only if the slot was full: a full slot
+                // changes only when its one destination writer -- this group
+                // -- writes it)
+                K y[E];
+                cy.load(dst, gl, y);
+                uint32_t dw = 0;
+                if (gl == 0) dw = atomicOr(&state[dst], kSlotTaken);
+                dw = __shfl_sync(gmask, dw, leader);
+                if ((dw & kSlotStateMask) == kSlotFull) {
                     __syncwarp(gmask);
                     cy.put(d, dst, x, gl);
 #pragma unroll
                     for (int e = 0; e < E; ++e) x[e] = y[e];
+                    xw = dw;
+                    xslot = dst;
                     continue;
                 }
-                if (st == kSlotTaken) {
+                if ((dw & kSlotStateMask) == kSlotTaken) {
                     // a seeding group is reading the block at dst out
                     uint32_t ready = 0;
                     if (gl == 0) {
                         for (int i = 0; i < kSpinLimit; ++i) {
-                            if (atomicAdd(&state[dst], 0u) == kSlotHole) {
+                            if ((atomicAdd(&state[dst], 0u) & kSlotStateMask) == kSlotHole) {
                                 ready = 1;
                                 break;
                             }
@@ -517,8 +543,8 @@ __global__ void __launch_bounds__(kIpCleanupThreads) k_ip_cleanup(Work wk, int l
 template <typename K>
 __global__ void k_ip_account(Work wk) {
     const unsigned long long used =
-        static_cast<unsigned long long>(min(wk.ctl->n_stripes, wk.max_stripes)) * (kBins * kIpBlockBytes + kBins) +
-        static_cast<unsigned long long>(min(wk.ctl->n_big, wk.max_big)) * (kBins * kIpBlockBytes + 8 * kBins) +
+        static_cast<unsigned long long>(min(wk.ctl->n_stripes, wk.max_stripes)) * (kBins * kIpBlockBytes + 5 * kBins) +
+        static_cast<unsigned long long>(min(wk.ctl->n_big, wk.max_big)) * (kBins * kIpBlockBytes + 4 * kBins) +
         static_cast<unsigned long long>(min(wk.ctl->n_slots, wk.max_slots)) * 4;
     atomicMax(&wk.ctl->aux_used, used);
 }
