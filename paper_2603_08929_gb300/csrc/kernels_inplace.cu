@@ -194,7 +194,9 @@ struct StripeSmem {
     static constexpr size_t kBlk = kFill + 4 * kBins;             // block slot base of each digit in this tile
     static constexpr size_t kNFull = kBlk + 4 * kBins;            // full blocks of each digit in the stripe
     static constexpr size_t kScan = kNFull + 4 * kBins;
-    static constexpr size_t kEnd = kScan + 4 * (kIpStripeThreads / 32 + 1);
+    static constexpr size_t kBmap = kScan + 4 * (kIpStripeThreads / 32 + 1);  // digit of each block of a tile
+    static constexpr int kMaxTileBlocks = (TILE + kBins * (B - 1)) / B;
+    static constexpr size_t kEnd = kBmap + kMaxTileBlocks;
 };
 
 template <int THREADS>
@@ -228,7 +230,7 @@ __device__ __forceinline__ uint32_t ip_block_scan(uint32_t v, uint32_t *tmp, uin
 template <typename K>
 __global__ void __launch_bounds__(kIpStripeThreads, 2) k_ip_stripe(Work wk, int level) {
     using S = StripeSmem<K>;
-    constexpr int B = S::B, TILE = S::TILE, T = kIpStripeThreads, WARPS = T / 32;
+    constexpr int B = S::B, TILE = S::TILE, T = kIpStripeThreads;
     K *tile = reinterpret_cast<K *>(g_ip_smem + S::kTileK);
     K *sorted = reinterpret_cast<K *>(g_ip_smem + S::kSorted);
     K *buf = reinterpret_cast<K *>(g_ip_smem + S::kBuf);
@@ -237,8 +239,9 @@ __global__ void __launch_bounds__(kIpStripeThreads, 2) k_ip_stripe(Work wk, int 
     uint32_t *fill = reinterpret_cast<uint32_t *>(g_ip_smem + S::kFill);
     uint32_t *blk = reinterpret_cast<uint32_t *>(g_ip_smem + S::kBlk);
     uint32_t *nfull = reinterpret_cast<uint32_t *>(g_ip_smem + S::kNFull);
+    uint8_t *bmap = reinterpret_cast<uint8_t *>(g_ip_smem + S::kBmap);
     uint32_t *scan_tmp = reinterpret_cast<uint32_t *>(g_ip_smem + S::kScan);
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int t = threadIdx.x;
     const int p = level & 1;
     if (wk.ctl->error) return;
     const uint32_t ns = min(wk.ctl->n_stripes, wk.max_stripes);
@@ -284,32 +287,37 @@ __global__ void __launch_bounds__(kIpStripeThreads, 2) k_ip_stripe(Work wk, int 
             __syncthreads();
             if (t < kBins) tstart[t] = st;
             __syncthreads();
-            // each warp: full blocks of its digits to the stripe front, the rest to the digit buffer
-            for (int d = warp; d < kBins; d += WARPS) {
-                const uint32_t cd = cnt[d], fd = fill[d], sd = tstart[d];
-                const uint32_t totd = fd + cd, nb = totd / B;
-                const uint32_t slot = blk[d];
-                const uint32_t rank0 = nfull[d];
-                for (uint32_t kb = 0; kb < nb; ++kb) {
-                    if (lane < B) {
-                        const uint32_t idx = kb * B + lane;
-                        const K v = idx < fd ? buf[d * B + idx] : sorted[sd + idx - fd];
-                        const uint64_t pos = static_cast<uint64_t>(slot + kb) * B + lane;
-                        if (pos < t0 + static_cast<uint64_t>(tlen)) base[pos] = v;  // never past what was read
-                        else ip_error(wk, kErrBounds);
-                    }
-                    if (lane == 0)
-                        wk.ip_state[big.state0 + s.slot0 + slot + kb] =
-                            kSlotFull | (static_cast<uint32_t>(d) << 22) | (rank0 + kb);
-                }
-                __syncwarp();
-                const uint32_t from = nb * B > fd ? nb * B : fd;  // first stream index not yet in the buffer
-                for (uint32_t idx = from + lane; idx < totd; idx += 32) buf[d * B + (idx - nb * B)] = sorted[sd + idx - fd];
-                __syncwarp();
-                if (lane == 0) {
-                    fill[d] = totd - nb * B;
-                    nfull[d] += nb;
-                }
+            // full blocks of every digit go to the stripe front: block bi of
+            // this tile (slot wp + bi) belongs to digit bmap[bi]; one thread
+            // per key, so consecutive threads write consecutive addresses
+            if (t < kBins) {
+                for (uint32_t kb = 0; kb < nbk; ++kb) bmap[blk[t] - wp + kb] = static_cast<uint8_t>(t);
+            }
+            __syncthreads();
+            for (uint32_t i = t; i < tot_blocks * B; i += T) {
+                const uint32_t bi = i / B, e = i % B;
+                const uint32_t d = bmap[bi];
+                const uint32_t kb = bi - (blk[d] - wp);
+                const uint32_t idx = kb * B + e, fd = fill[d];
+                const K v = idx < fd ? buf[d * B + idx] : sorted[tstart[d] + idx - fd];
+                const uint64_t pos = static_cast<uint64_t>(wp + bi) * B + e;
+                if (pos < t0 + static_cast<uint64_t>(tlen)) base[pos] = v;  // never past what was read
+                else ip_error(wk, kErrBounds);
+                if (e == 0)
+                    wk.ip_state[big.state0 + s.slot0 + wp + bi] = kSlotFull | (d << 22) | (nfull[d] + kb);
+            }
+            __syncthreads();
+            // the rest of each digit's stream becomes its buffer
+            for (uint32_t i = t; i < static_cast<uint32_t>(kBins * B); i += T) {
+                const uint32_t d = i / B, r = i % B;
+                const uint32_t fd = fill[d], totd = fd + cnt[d], nb = totd / B;
+                const uint32_t idx = nb * B + r;  // stream index of the new buffer entry r
+                if (idx < totd && idx >= fd) buf[d * B + r] = sorted[tstart[d] + idx - fd];
+            }
+            __syncthreads();
+            if (t < kBins) {
+                fill[t] = f + c - nbk * B;
+                nfull[t] += nbk;
             }
             wp += tot_blocks;
             __syncthreads();
