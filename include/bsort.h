@@ -150,6 +150,16 @@ bsort_status bsort_workspace_bytes_tuned(size_t n, bsort_dtype dt, bsort_mode mo
                                          size_t *bytes);
 
 /*
+ * Failure-detection self-test: launches one device wait of the kind the
+ * library uses (a bounded poll, a fraction of a second) on a flag that nothing
+ * sets, on `stream`, and synchronises.  Returns BSORT_ERR_TIMEOUT when the
+ * wait gave up and reported it as designed (the context stays usable);
+ * BSORT_OK would mean the flag was seen set.  Allocates 8 bytes of device
+ * memory for the call.  The paper has no counterpart.
+ */
+bsort_status bsort_selftest_bounded_wait(void *stream);
+
+/*
  * Auxiliary device bytes the last call on `handle` used beyond the keys:
  * ping-pong mode, its whole workspace (the alternate buffer included);
  * in-place mode, the metadata plus the largest block buffers, slot states

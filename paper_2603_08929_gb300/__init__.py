@@ -133,6 +133,8 @@ def lib():
         L.bsort_handle_set_tuning.restype = i
         L.bsort_workspace_bytes_tuned.argtypes = [sz, i, i, ctypes.POINTER(_Tuning), ctypes.POINTER(sz)]
         L.bsort_workspace_bytes_tuned.restype = i
+        L.bsort_selftest_bounded_wait.argtypes = [vp]
+        L.bsort_selftest_bounded_wait.restype = i
         L.bsort_last_aux_bytes.argtypes = [vp, ctypes.POINTER(sz)]
         L.bsort_last_aux_bytes.restype = i
         L.bsort_server_create.argtypes = [ctypes.POINTER(_ServerConfig), ctypes.POINTER(vp)]
@@ -425,6 +427,11 @@ class Server:
             self.close()
         except Exception:  # noqa: BLE001 - interpreter shutdown
             pass
+
+
+def selftest_bounded_wait(stream=None) -> int:
+    """Status of ``bsort_selftest_bounded_wait`` (BSORT_ERR_TIMEOUT = 7 expected)."""
+    return int(lib().bsort_selftest_bounded_wait(_stream_ptr(stream)))
 
 
 def bsort_keys_host(keys, descending: bool = False, stream=None) -> None:

@@ -669,6 +669,25 @@ bsort_status bsort_last_aux_bytes(bsort_handle *handle, size_t *bytes) {
     return BSORT_OK;
 }
 
+bsort_status bsort_selftest_bounded_wait(void *stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint32_t *d = nullptr;
+    if (cudaMalloc(&d, 2 * sizeof(uint32_t)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return BSORT_ERR_NO_MEMORY;
+    }
+    uint32_t h[2] = {0, 0};
+    bsort_status rs = BSORT_ERR_CUDA;
+    if (cudaMemsetAsync(d, 0, 2 * sizeof(uint32_t), st) == cudaSuccess) {
+        launch_wait_selftest(d, st);
+        if (cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+            cudaStreamSynchronize(st) == cudaSuccess)
+            rs = (h[1] & kErrTimeout) ? BSORT_ERR_TIMEOUT : BSORT_OK;
+    }
+    cudaFree(d);
+    return rs;
+}
+
 bsort_status bsort_get_error(bsort_handle *handle, void *stream) {
     if (!handle) {
         int dev = 0;

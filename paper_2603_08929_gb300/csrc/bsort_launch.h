@@ -87,6 +87,9 @@ constexpr int kIpSmemCapBytes = 192 * 1024;        // buckets up to this size go
 constexpr uint64_t kIpStripeBytes = 1ull << 20;    // stripe classified by one CTA
 template <typename K>
 void ip_prepare();
+// One bounded device wait on flag_and_err[0] (which nothing sets); the timeout
+// lands in flag_and_err[1].
+void launch_wait_selftest(uint32_t *flag_and_err, cudaStream_t st);
 template <typename K>
 void launch_ip_level(const Work &wk, cudaStream_t st, Recorder &rec, int num_sms, int level);
 

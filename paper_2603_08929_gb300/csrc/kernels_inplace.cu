@@ -50,7 +50,7 @@ constexpr int kIpStripeThreads = 512;
 constexpr int kIpPermuteThreads = 256;
 constexpr int kIpCleanupThreads = 256;
 constexpr int kIpSmemThreads = 1024;
-constexpr int kSpinLimit = 1 << 22;
+constexpr int kSpinLimit = 1 << 20;  // polls of about a microsecond each: about a second
 
 template <typename K>
 struct IpCfg {
@@ -60,6 +60,26 @@ struct IpCfg {
 };
 
 extern __shared__ __align__(16) unsigned char g_ip_smem[];
+
+// Waits, at most kSpinLimit polls (a fraction of a second), until
+// (*word & mask) == want; returns whether it did.  The one kind of wait in
+// the library: a caller that gives up sets an error bit and returns.
+__device__ __forceinline__ uint32_t bounded_wait(uint32_t *word, uint32_t mask, uint32_t want) {
+    for (int i = 0; i < kSpinLimit; ++i) {
+        if ((atomicAdd(word, 0u) & mask) == want) {
+            __threadfence();
+            return 1;
+        }
+        __nanosleep(32);
+    }
+    return 0;
+}
+
+// Self-test of the bounded wait: waits on a flag nothing sets and records
+// the timeout in err (kErrTimeout), then returns.
+__global__ void k_wait_selftest(uint32_t *flag, uint32_t *err) {
+    if (threadIdx.x == 0 && !bounded_wait(flag, 0xffffffffu, 1u)) atomicOr(err, kErrTimeout);
+}
 
 __device__ __forceinline__ void ip_error(const Work &wk, uint32_t bits) { atomicOr(&wk.ctl->error, bits); }
 
@@ -460,16 +480,7 @@ __global__ void __launch_bounds__(kIpPermuteThreads) k_ip_permute(Work wk, int l
                 if ((dw & kSlotStateMask) == kSlotTaken) {
                     // a seeding group is reading the block at dst out
                     uint32_t ready = 0;
-                    if (gl == 0) {
-                        for (int i = 0; i < kSpinLimit; ++i) {
-                            if ((atomicAdd(&state[dst], 0u) & kSlotStateMask) == kSlotHole) {
-                                ready = 1;
-                                break;
-                            }
-                            __nanosleep(32);
-                        }
-                        __threadfence();
-                    }
+                    if (gl == 0) ready = bounded_wait(&state[dst], kSlotStateMask, kSlotHole);
                     if (!__shfl_sync(gmask, ready, leader)) {
                         if (gl == 0) ip_error(wk, kErrTimeout);
                         fail = true;
@@ -584,6 +595,10 @@ void launch_ip_level(const Work &wk, cudaStream_t st, Recorder &rec, int num_sms
     rec.end();
     rec.launches += 5;  // the group counted one of its six kernels
     rec.held_launches += 5;
+}
+
+void launch_wait_selftest(uint32_t *flag_and_err, cudaStream_t st) {
+    k_wait_selftest<<<1, 32, 0, st>>>(flag_and_err, flag_and_err + 1);
 }
 
 template void ip_prepare<uint32_t>();

@@ -97,3 +97,31 @@ def test_inplace_full_size_properties():
     x = W.make("uniform", "int32", n, seed=22)
     got, aux = sort_inplace(x)
     check_full_size(x, got, False)
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    """The library's one kind of device wait, on a flag nothing sets, gives up
+    and reports BSORT_ERR_TIMEOUT; the next sort on the same context works."""
+    import paper_2603_08929_gb300 as bs
+    assert bs.selftest_bounded_wait() == 7
+    x = W.make("uniform", "int32", 1 << 20, seed=8)
+    got, _ = sort_inplace(x)
+    assert_bit_exact(got, O.bsort(x.copy()), "after the timed-out wait")
+
+
+@pytest.mark.parametrize("dtype", ["int32", "float64"])
+def test_inplace_unaligned_view(dtype):
+    """A view one key past a 16-byte boundary: scalar paths everywhere."""
+    import torch
+    import paper_2603_08929_gb300 as bs
+    n = 700003
+    x = W.make("uniform", dtype, n + 1, seed=9)
+    base = to_device(x)
+    t = base[1:]
+    h = bs.Handle()
+    ws = torch.empty(bs.workspace_bytes(n, dtype, mode=bs.MODE_INPLACE), dtype=torch.uint8, device=t.device)
+    bs.bsort_keys_ws(h, t, ws, mode=bs.MODE_INPLACE)
+    assert h.get_error() == 0
+    out = base.cpu().numpy()
+    assert_bit_exact(out[1:], O.bsort(x[1:].copy()), "unaligned in-place")
+    assert out[:1].view(np.uint8).tobytes() == x[:1].view(np.uint8).tobytes()  # the key before the view is untouched
