@@ -150,6 +150,21 @@ bsort_status bsort_workspace_bytes_tuned(size_t n, bsort_dtype dt, bsort_mode mo
                                          size_t *bytes);
 
 /*
+ * Intermediate state, for checking the digit passes on their own: runs only
+ * the first `levels` MSD levels (r bits each, r = the handle's digit width)
+ * of bsort_keys_ws, finishes the shared-memory units and constant runs they
+ * produced, and leaves every bucket still open unsorted in place (decoded).
+ * The result is partitioned by the top levels * r bits of the key order --
+ * invariants (i)/(ii) of Alg. 1 at each of those bits (Sec. II) -- with the
+ * same bucket boundaries as any such partition; the order inside an open
+ * bucket is unspecified (the digit pass is not stable; keys are bit-identical
+ * when equal, so the final result is unique).  4- and 8-byte keys, ping-pong
+ * workspace.  levels >= the full count: the complete sort.
+ */
+bsort_status bsort_keys_partial_ws(bsort_handle *handle, void *keys, size_t n, bsort_dtype dt, int descending,
+                                   int levels, void *workspace, size_t ws_bytes, void *stream);
+
+/*
  * Failure-detection self-test: launches one device wait of the kind the
  * library uses (a bounded poll, a fraction of a second) on a flag that nothing
  * sets, on `stream`, and synchronises.  Returns BSORT_ERR_TIMEOUT when the

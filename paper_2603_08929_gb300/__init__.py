@@ -133,6 +133,8 @@ def lib():
         L.bsort_handle_set_tuning.restype = i
         L.bsort_workspace_bytes_tuned.argtypes = [sz, i, i, ctypes.POINTER(_Tuning), ctypes.POINTER(sz)]
         L.bsort_workspace_bytes_tuned.restype = i
+        L.bsort_keys_partial_ws.argtypes = [vp, vp, sz, i, i, i, vp, sz, vp]
+        L.bsort_keys_partial_ws.restype = i
         L.bsort_selftest_bounded_wait.argtypes = [vp]
         L.bsort_selftest_bounded_wait.restype = i
         L.bsort_last_aux_bytes.argtypes = [vp, ctypes.POINTER(sz)]
@@ -427,6 +429,18 @@ class Server:
             self.close()
         except Exception:  # noqa: BLE001 - interpreter shutdown
             pass
+
+
+def bsort_keys_partial_ws(handle: Handle, keys, workspace, levels: int, descending: bool = False,
+                          stream=None) -> None:
+    """Intermediate state after `levels` MSD levels (``bsort_keys_partial_ws``)."""
+    _device_tensor(keys)
+    _device_tensor(workspace)
+    _check(lib().bsort_keys_partial_ws(handle.ptr, ctypes.c_void_p(keys.data_ptr()), keys.numel(),
+                                       _dtype_code(keys.dtype), int(bool(descending)), int(levels),
+                                       ctypes.c_void_p(workspace.data_ptr()),
+                                       workspace.numel() * workspace.element_size(), _stream_ptr(stream)),
+           "bsort_keys_partial_ws")
 
 
 def selftest_bounded_wait(stream=None) -> int:

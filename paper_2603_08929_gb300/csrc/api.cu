@@ -227,6 +227,7 @@ Work make_work(const MsdLayout &L, char *ws, void *keys, size_t n, const DtypeIn
     wk.w = di.bytes * 8;
     wk.radix_bits = s.radix_bits;
     wk.levels = s.levels;
+    wk.stop_level = s.levels;
     wk.keys_vec_ok = (reinterpret_cast<uintptr_t>(keys) & 15) == 0;
     wk.inplace = L.inplace;
     wk.ip_big = L.inplace ? reinterpret_cast<IpBig *>(ws + L.ip_big) : nullptr;
@@ -301,7 +302,8 @@ bsort_status run_sort(bsort_handle *h, void *keys, size_t n, const DtypeInfo &di
         if (ws_bytes < L.total) return BSORT_ERR_WORKSPACE_TOO_SMALL;
         h->last_inplace = inplace;
         h->last_fixed_aux = inplace ? L.lists_end - L.ctl : L.total;
-        const Work wk = make_work(L, ws, keys, n, di, codec, tune);
+        Work wk = make_work(L, ws, keys, n, di, codec, tune);
+        if (h->stop_levels > 0 && h->stop_levels < wk.levels) wk.stop_level = h->stop_levels;
         if (di.bytes == 4) launch_msd<uint32_t>(wk, st, h->rec, sms);
         else launch_msd<uint64_t>(wk, st, h->rec, sms);
         h->last_path = 2;
@@ -667,6 +669,24 @@ bsort_status bsort_last_aux_bytes(bsort_handle *handle, size_t *bytes) {
     }
     *bytes = used;
     return BSORT_OK;
+}
+
+bsort_status bsort_keys_partial_ws(bsort_handle *handle, void *keys, size_t n, bsort_dtype dt, int descending,
+                                   int levels, void *workspace, size_t ws_bytes, void *stream) {
+    if (!handle || levels < 1) return BSORT_ERR_INVALID_ARG;
+    DtypeInfo di;
+    const bsort_status st = check_args(keys, n, dt, &di);
+    if (st != BSORT_OK) return st;
+    if (di.bytes <= 2) return BSORT_ERR_UNSUPPORTED;
+    if (n <= 1) return BSORT_OK;
+    if (!workspace) return BSORT_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(workspace) % kAlign) return BSORT_ERR_MISALIGNED;
+    std::lock_guard<std::mutex> lk(handle->mu);
+    handle->stop_levels = levels;
+    const bsort_status rs = run_sort(handle, keys, n, di, descending, workspace, ws_bytes,
+                                     static_cast<cudaStream_t>(stream));
+    handle->stop_levels = 0;
+    return rs;
 }
 
 bsort_status bsort_selftest_bounded_wait(void *stream) {

@@ -132,6 +132,7 @@ struct Work {
     int32_t w;            // key bits
     int32_t radix_bits;   // digit width of the MSD levels (kMinRadixBits..kRadixBits)
     int32_t levels;       // host-launched MSD levels: ceil(w / radix_bits)
+    int32_t stop_level;   // levels actually run (levels, or fewer for an intermediate state)
     bool keys_vec_ok;     // caller's buffer is 16-byte aligned (vector loads)
     // in-place mode (digit permutation inside the caller's buffer)
     bool inplace;

@@ -25,6 +25,7 @@ struct bsort_handle {
     int last_key_bytes = 0;
     uint64_t last_n = 0;
     bsort::Tuning tune[2];  // MSD tuning for 4-byte [0] and 8-byte [1] keys (bsort_keys_ws)
+    int stop_levels = 0;    // > 0: run only this many MSD levels (bsort_keys_partial_ws)
     bool profiling = false;
     bool events = false;
     Ctl *prof_ctl = nullptr;  // device slots: work counters of each recorded call

@@ -1621,6 +1621,24 @@ __global__ void k_fill(Work wk) {
     }
 }
 
+// Intermediate state only: the buckets still open before `level` (partitioned
+// by the bits above their h, unsorted below) are written, decoded, to their
+// place in the caller's buffer as they are.
+template <typename K>
+__global__ void k_drain(Work wk, int level) {
+    if (wk.ctl->error) return;
+    const int p = level & 1;
+    const uint32_t nb = wk.ctl->n_buckets[p];
+    K *out = static_cast<K *>(wk.keys);
+    for (uint32_t i = blockIdx.x; i < nb; i += gridDim.x) {
+        const Bucket b = wk.buckets[p][i];
+        if (b.src == 0 && b.raw) continue;  // never moved, never encoded
+        const K *src = src_of<K>(wk, b.src);
+        for (uint64_t j = threadIdx.x; j < b.len; j += blockDim.x)
+            out[b.start + j] = decode_key(src[b.start + j], wk.codec);
+    }
+}
+
 template <typename K>
 struct Cfg;
 template <>
@@ -1693,7 +1711,7 @@ void msd_levels_and_finish(const Work &wk, cudaStream_t st, Recorder &rec, int n
     constexpr int FT = Cfg<K>::kFinThreads, FI = Cfg<K>::kFinItems;
     constexpr int CT = 2;  // tiles per chunk
     if (levels) {
-        for (int level = 0; level < wk.levels; ++level) {
+        for (int level = 0; level < wk.stop_level; ++level) {
             rec.begin(BSORT_K_HIST, level);
             k_hist<K, 512><<<num_sms * 4, 512, 0, st>>>(wk, level);
             rec.end();
@@ -1711,6 +1729,11 @@ void msd_levels_and_finish(const Work &wk, cudaStream_t st, Recorder &rec, int n
                 rec.end();
             }
         }
+    }
+    if (levels && wk.stop_level < wk.levels) {
+        rec.begin(BSORT_K_FILL, wk.stop_level);
+        k_drain<K><<<num_sms * 2, 256, 0, st>>>(wk, wk.stop_level);
+        rec.end();
     }
     rec.begin(BSORT_K_FINISH, -1);
     k_finish<K, FT, FI><<<num_sms * 8, FT, finish_smem<K, FT, FI>(), st>>>(wk);
