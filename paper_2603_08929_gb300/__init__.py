@@ -17,7 +17,8 @@ from . import build as _build
 
 __all__ = [
     "DTYPES", "BsortError", "lib", "bsort_keys", "bsort_keys_ws", "bsort_keys_host", "bsort_keys_noalloc",
-    "bsort_keys_segmented", "segmented_workspace_bytes", "Graph", "Server",
+    "bsort_keys_segmented", "segmented_workspace_bytes", "Graph", "Server", "sort_", "sort_segmented_",
+    "bsort_keys_partial_ws", "selftest_bounded_wait",
     "workspace_bytes", "Handle", "sort_", "status_string",
 ]
 
@@ -197,7 +198,27 @@ def bsort_keys(keys, descending: bool = False, stream=None) -> None:
                             int(bool(descending)), _stream_ptr(stream)), "bsort_keys")
 
 
-sort_ = bsort_keys
+_inplace_handle = None
+
+
+def sort_(keys, descending: bool = False, mode: str = "pingpong", stream=None):
+    """Sorts a contiguous CUDA tensor in place and returns it.  mode
+    "pingpong" (default: ``bsort_keys``, cached workspace) or "inplace" (a
+    workspace of ``workspace_bytes(..., MODE_INPLACE)`` allocated by torch for
+    the call, no alternate copy of the keys)."""
+    global _inplace_handle
+    if mode == "pingpong":
+        bsort_keys(keys, descending=descending, stream=stream)
+    elif mode == "inplace":
+        import torch
+        if _inplace_handle is None:
+            _inplace_handle = Handle()
+        ws = torch.empty(max(1, workspace_bytes(keys.numel(), keys.dtype, mode=MODE_INPLACE)), dtype=torch.uint8,
+                         device=keys.device)
+        bsort_keys_ws(_inplace_handle, keys, ws, descending=descending, stream=stream, mode=MODE_INPLACE)
+    else:
+        raise ValueError("mode must be 'pingpong' or 'inplace'")
+    return keys
 
 
 def _tuning(t):
@@ -332,6 +353,13 @@ def bsort_keys_segmented(keys, offsets, descending: bool = False, stream=None, h
                                              ctypes.c_void_p(workspace.data_ptr()),
                                              workspace.numel() * workspace.element_size(), _stream_ptr(stream)),
                "bsort_keys_segmented_ws")
+
+
+def sort_segmented_(keys, offsets, descending: bool = False, stream=None):
+    """Sorts each segment [offsets[i], offsets[i+1]) of a CUDA tensor in place
+    (``bsort_keys_segmented``) and returns the tensor."""
+    bsort_keys_segmented(keys, offsets, descending=descending, stream=stream)
+    return keys
 
 
 class Graph:

@@ -125,3 +125,27 @@ def test_inplace_unaligned_view(dtype):
     out = base.cpu().numpy()
     assert_bit_exact(out[1:], O.bsort(x[1:].copy()), "unaligned in-place")
     assert out[:1].view(np.uint8).tobytes() == x[:1].view(np.uint8).tobytes()  # the key before the view is untouched
+
+
+@pytest.mark.parametrize("mode", ["pingpong", "inplace"])
+def test_python_sort_modes(mode):
+    import paper_2603_08929_gb300 as bs
+    x = W.make("normal", "float32", 200003, seed=10)
+    t = to_device(x)
+    assert bs.sort_(t, descending=True, mode=mode) is t
+    assert_bit_exact(t.cpu().numpy(), O.bsort(x.copy(), descending=True), mode)
+    with pytest.raises(ValueError):
+        bs.sort_(t, mode="sideways")
+
+
+def test_python_sort_segmented():
+    import torch
+    import paper_2603_08929_gb300 as bs
+    sizes = np.array([3, 0, 5000, 1, 70000], dtype=np.int64)
+    x = W.make("uniform", "int64", int(sizes.sum()), seed=11)
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    t = to_device(x)
+    bs.sort_segmented_(t, torch.from_numpy(off).cuda())
+    got = t.cpu().numpy()
+    for a, b in zip(off[:-1], off[1:]):
+        assert_bit_exact(got[a:b], O.bsort(x[a:b].copy()), "segment [%d, %d)" % (a, b))
