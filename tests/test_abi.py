@@ -76,3 +76,42 @@ def test_workspace_sizes(lib):
     assert pkg.workspace_bytes(n, "uint16", mode=pkg.MODE_INPLACE) == pkg.workspace_bytes(n, "uint16")
     with pytest.raises(pkg.BsortError):
         pkg.workspace_bytes(100, "int32", mode=7)
+
+
+def test_more_argument_checks_without_a_gpu(lib):
+    """Entry points added for tuning, intermediate states, serving and
+    in-place accounting validate their arguments before any CUDA call."""
+    import paper_2603_08929_gb300 as pkg
+    h = ctypes.c_void_p()
+    assert lib.bsort_handle_create(ctypes.byref(h)) == 0
+    try:
+        T = pkg._Tuning
+        bad = T(9, 0, 0, 0)
+        assert lib.bsort_handle_set_tuning(h, 4, ctypes.byref(bad)) == 1   # digit width out of range
+        assert lib.bsort_handle_set_tuning(h, 3, None) == 1                 # key width
+        assert lib.bsort_handle_set_tuning(h, 8, ctypes.byref(T(6, 1024, 128, 0))) == 0
+        assert lib.bsort_handle_set_tuning(h, 8, None) == 0                 # back to defaults
+        ws = ctypes.c_void_p(0x100000)
+        # intermediate state: levels >= 1, 4/8-byte keys, keys and workspace checked
+        assert lib.bsort_keys_partial_ws(h, ctypes.c_void_p(0x1000), 10, 6, 0, 0, ws, 1 << 20, None) == 1
+        assert lib.bsort_keys_partial_ws(h, ctypes.c_void_p(0x1000), 10, 3, 0, 1, ws, 1 << 20, None) == 2
+        assert lib.bsort_keys_partial_ws(h, None, 10, 6, 0, 1, ws, 1 << 20, None) == 1
+        assert lib.bsort_keys_partial_ws(h, ctypes.c_void_p(0x1000), 10, 6, 0, 1, ctypes.c_void_p(0x100010),
+                                         1 << 20, None) == 3                # workspace not 256-byte aligned
+        # bsort_keys_ws: unknown mode, missing workspace
+        assert lib.bsort_keys_ws(h, ctypes.c_void_p(0x1000), 10, 6, 0, 7, ws, 1 << 20, None) == 1
+        assert lib.bsort_keys_ws(h, ctypes.c_void_p(0x1000), 10, 6, 0, 1, None, 0, None) == 1
+        # segmented 1/2-byte keys are not part of this build
+        assert lib.bsort_keys_segmented(ctypes.c_void_p(0x1000), 10, ctypes.c_void_p(0x2000), 2, 3, 0, None) == 2
+        # no call yet: no auxiliary bytes
+        n = ctypes.c_size_t(123)
+        assert lib.bsort_last_aux_bytes(h, ctypes.byref(n)) == 0 and n.value == 0
+    finally:
+        lib.bsort_handle_destroy(h)
+    # server configuration checks
+    srv = ctypes.c_void_p()
+    C = pkg._ServerConfig
+    assert lib.bsort_server_create(ctypes.byref(C(0, 1, 1 << 30, 1 << 20, 1 << 16, 0, 0)), ctypes.byref(srv)) == 1
+    assert lib.bsort_server_create(ctypes.byref(C(2, 0, 1 << 30, 1 << 20, 1 << 16, 0, 0)), ctypes.byref(srv)) == 1
+    assert lib.bsort_server_create(ctypes.byref(C(2, 1, 1 << 30, 1 << 20, 1 << 16, 5, 0)), ctypes.byref(srv)) == 1
+    assert lib.bsort_server_submit(None, None, 0, 6, 0, 0) == 1
