@@ -218,7 +218,6 @@ template <typename K, int THREADS, int ITEMS, typename RS>
 struct Ranker {
     static constexpr int WARPS = THREADS / 32;
     static constexpr int STRIDE = WARPS + 1;
-    static constexpr int TILE = THREADS * ITEMS;
     static_assert(THREADS >= kBins, "one thread per digit in the scans");
 
     template <bool STABLE>
@@ -1226,13 +1225,6 @@ struct FinLayout {
     static_assert(sizeof(K) * (kTile + V) <= kTotals, "staging overlaps only the counter words");
     static_assert(kSplitCap == 16 * THREADS, "the scan gives each thread 16 sub-buckets");
 };
-
-// Sum of the sixteen 4-bit counters of (x, y): bytes hold at most 4 * 15.
-__device__ __forceinline__ uint32_t nib_sum(uint32_t x, uint32_t y) {
-    constexpr uint32_t m = 0x0F0F0F0Fu;
-    const uint32_t b = (x & m) + ((x >> 4) & m) + (y & m) + ((y >> 4) & m);
-    return (b * 0x01010101u) >> 24;
-}
 
 // Sorts every unit in shared memory and writes it, decoded, to its final
 // place.  With at most 16 varying bits (and enough keys to fill the
