@@ -16,8 +16,8 @@
  * subnormals, signalling NaNs keep their bits.
  *
  * Every call sorts in place: the result is written back into the caller's
- * array, as the paper's functions return "the same array a but sorted"
- * (Algs. 3/4 outputs).
+ * array, as the paper's functions hand back their input array sorted
+ * (outputs of Algs. 3/4).
  *
  * Conventions shared by all entry points
  *   - `keys` / offsets are DEVICE pointers unless the name says host; the
