@@ -59,7 +59,7 @@ typedef enum {
 typedef enum {
     BSORT_OK = 0,
     BSORT_ERR_INVALID_ARG = 1,          /* NULL pointer, bad dtype/mode, bad handle */
-    BSORT_ERR_UNSUPPORTED = 2,          /* valid request this build cannot serve */
+    BSORT_ERR_UNSUPPORTED = 2,          /* valid request the library does not support */
     BSORT_ERR_MISALIGNED = 3,           /* pointer not aligned to the key size */
     BSORT_ERR_NO_MEMORY = 4,            /* device allocation failed */
     BSORT_ERR_WORKSPACE_TOO_SMALL = 5,  /* ws_bytes < bsort_workspace_bytes() */

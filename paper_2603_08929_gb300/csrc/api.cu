@@ -317,7 +317,7 @@ bsort_status run_sort(bsort_handle *h, void *keys, size_t n, const DtypeInfo &di
 bsort_status check_segmented(const void *keys, size_t n, const uint64_t *d_offsets, size_t nseg, bsort_dtype dt,
                              DtypeInfo *di) {
     if (!dtype_info(dt, di)) return BSORT_ERR_INVALID_ARG;
-    if (di->bytes < 4) return BSORT_ERR_UNSUPPORTED;  // segmented 1/2-byte keys: not in this build
+    if (di->bytes < 4) return BSORT_ERR_UNSUPPORTED;  // the segmented form takes 4- and 8-byte keys only
     if (nseg == 0 || n == 0) return BSORT_OK;
     if (!keys || !d_offsets) return BSORT_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(keys) % di->bytes || reinterpret_cast<uintptr_t>(d_offsets) % 8)
@@ -394,7 +394,7 @@ const char *bsort_status_string(bsort_status status) {
     switch (status) {
     case BSORT_OK: return "BSORT_OK";
     case BSORT_ERR_INVALID_ARG: return "BSORT_ERR_INVALID_ARG: invalid argument";
-    case BSORT_ERR_UNSUPPORTED: return "BSORT_ERR_UNSUPPORTED: request not supported by this build";
+    case BSORT_ERR_UNSUPPORTED: return "BSORT_ERR_UNSUPPORTED: request the library does not support";
     case BSORT_ERR_MISALIGNED: return "BSORT_ERR_MISALIGNED: pointer not aligned to the key size";
     case BSORT_ERR_NO_MEMORY: return "BSORT_ERR_NO_MEMORY: device allocation failed";
     case BSORT_ERR_WORKSPACE_TOO_SMALL: return "BSORT_ERR_WORKSPACE_TOO_SMALL: workspace smaller than required";

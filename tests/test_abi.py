@@ -101,7 +101,7 @@ def test_more_argument_checks_without_a_gpu(lib):
         # bsort_keys_ws: unknown mode, missing workspace
         assert lib.bsort_keys_ws(h, ctypes.c_void_p(0x1000), 10, 6, 0, 7, ws, 1 << 20, None) == 1
         assert lib.bsort_keys_ws(h, ctypes.c_void_p(0x1000), 10, 6, 0, 1, None, 0, None) == 1
-        # segmented 1/2-byte keys are not part of this build
+        # the segmented form takes 4- and 8-byte keys only
         assert lib.bsort_keys_segmented(ctypes.c_void_p(0x1000), 10, ctypes.c_void_p(0x2000), 2, 3, 0, None) == 2
         # no call yet: no auxiliary bytes
         n = ctypes.c_size_t(123)
