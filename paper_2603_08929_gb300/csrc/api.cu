@@ -65,7 +65,7 @@ struct MsdLayout {
     uint32_t max_buckets, max_chunks, max_units, max_fills;
     // in-place mode (alt is empty then)
     bool inplace;
-    size_t ip_big, ip_stripes, ip_ncnt, ip_prefix, ip_rem, ip_part, ip_ovf, ip_state, lists_end;
+    size_t ip_big, ip_stripes, ip_ncnt, ip_rem, ip_part, ip_ovf, ip_state, lists_end;
     uint32_t max_big, max_stripes, max_slots;
 };
 
@@ -104,7 +104,7 @@ MsdLayout msd_layout(size_t n, int key_bytes, size_t nseg = 0, bool inplace = fa
     L.fills = take(sizeof(Fill) * L.max_fills);
     L.lists_end = off;
     L.max_big = L.max_stripes = L.max_slots = 0;
-    L.ip_big = L.ip_stripes = L.ip_ncnt = L.ip_prefix = L.ip_rem = L.ip_part = L.ip_ovf = L.ip_state = 0;
+    L.ip_big = L.ip_stripes = L.ip_ncnt = L.ip_rem = L.ip_part = L.ip_ovf = L.ip_state = 0;
     if (inplace) {
         // a level's big buckets are disjoint and longer than the shared-memory capacity
         const uint64_t blk = kIpBlockBytes / key_bytes;
@@ -116,7 +116,6 @@ MsdLayout msd_layout(size_t n, int key_bytes, size_t nseg = 0, bool inplace = fa
         L.ip_big = take(sizeof(IpBig) * L.max_big);
         L.ip_stripes = take(sizeof(IpStripe) * L.max_stripes);
         L.ip_ncnt = take(sizeof(uint32_t) * kBins * static_cast<size_t>(L.max_big));
-        L.ip_prefix = take(sizeof(uint32_t) * kBins * static_cast<size_t>(L.max_stripes));
         L.ip_rem = take(static_cast<size_t>(kBins) * L.max_stripes);
         L.ip_part = take(static_cast<size_t>(kIpBlockBytes) * kBins * L.max_stripes);
         L.ip_ovf = take(static_cast<size_t>(kIpBlockBytes) * kBins * L.max_big);
@@ -233,7 +232,6 @@ Work make_work(const MsdLayout &L, char *ws, void *keys, size_t n, const DtypeIn
     wk.ip_big = L.inplace ? reinterpret_cast<IpBig *>(ws + L.ip_big) : nullptr;
     wk.ip_stripes = L.inplace ? reinterpret_cast<IpStripe *>(ws + L.ip_stripes) : nullptr;
     wk.ip_ncnt = L.inplace ? reinterpret_cast<uint32_t *>(ws + L.ip_ncnt) : nullptr;
-    wk.ip_prefix = L.inplace ? reinterpret_cast<uint32_t *>(ws + L.ip_prefix) : nullptr;
     wk.ip_rem = L.inplace ? reinterpret_cast<uint8_t *>(ws + L.ip_rem) : nullptr;
     wk.ip_part = L.inplace ? static_cast<void *>(ws + L.ip_part) : nullptr;
     wk.ip_ovf = L.inplace ? static_cast<void *>(ws + L.ip_ovf) : nullptr;

@@ -139,7 +139,6 @@ struct Work {
     IpBig *ip_big;          // [max_big]
     IpStripe *ip_stripes;   // [max_stripes]
     uint32_t *ip_ncnt;      // [max_big][kBins] full blocks per digit
-    uint32_t *ip_prefix;    // [max_stripes][kBins] a stripe's first slot among its digit's slots
     uint8_t *ip_rem;        // [max_stripes][kBins] keys left in a partial block
     void *ip_part;          // [max_stripes][kBins][block keys] partial blocks
     void *ip_ovf;           // [max_big][kBins][block keys] overflow of a digit's last block

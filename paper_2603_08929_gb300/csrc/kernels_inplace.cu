@@ -15,19 +15,21 @@
 //                   under-full rest of each digit goes to a per-stripe buffer;
 //     k_ip_permute  digit d owns the block slots [A_d, A_d + N_d) of the bucket,
 //                   A_d = ceil(D_d / B) (D_d: digit base, N_d: its full blocks).
-//                   Each block's slot is fixed by the classification: its
-//                   stripe's share of digit d (claimed per stripe) plus its
-//                   rank there.  Groups of lanes carry blocks: the block at the
-//                   destination, if not yet moved, is taken along (an atomic OR
-//                   on the slot's state word decides who takes it and returns
-//                   its digit and rank), so every block moves exactly once and
-//                   nothing ever waits for anything but a read in progress;
+//                   Each block's slot is fixed by the classification (its
+//                   stripe's share of digit d, claimed per stripe, plus its
+//                   rank there) and written into the state word of the slot
+//                   it sits in.  Groups of lanes carry blocks: the block at
+//                   the destination, if not yet moved, is taken along (an
+//                   atomic OR on the slot's state word decides who takes it
+//                   and returns where it goes) while its read is in flight,
+//                   so every block moves exactly once in one round trip per
+//                   hop and nothing ever waits for anything but a read in
+//                   progress;
 //     k_ip_cleanup  per digit, the partial blocks of all stripes and the part of
 //                   the digit's last block that crossed D_{d+1} (kept aside by
 //                   the carrier) fill the rest of the digit's range.
-// Auxiliary memory: counters, one partial-block buffer and one digit-share
-// row per stripe, one overflow block per (bucket, digit) and one state word
-// per block slot.
+// Auxiliary memory: counters, one partial-block buffer per stripe, one
+// overflow block per (bucket, digit) and one state word per block slot.
 #include "bsort_launch.h"
 
 namespace bsort {
@@ -36,15 +38,15 @@ namespace {
 
 constexpr unsigned kFullMask = 0xffffffffu;
 
-// Slot state word: bits 31-30 the state, bits 29-22 the digit of the block
-// the slot held after classification, bits 21-0 its rank among its stripe's
-// blocks of that digit.  OR-ing kSlotTaken takes a full slot and leaves the
-// other states as they are; the old word says what was taken.
+// Slot state word: bits 31-30 the state, bits 29-0 the destination slot of
+// the block the slot held after classification (while the stripe is being
+// classified: bits 29-22 its digit, bits 21-0 its rank among the stripe's
+// blocks of that digit).  OR-ing kSlotTaken takes a full slot and leaves the
+// other states as they are; the old word says where the taken block goes.
 constexpr uint32_t kSlotFull = 0u << 30;   // holds a block that has not moved yet
 constexpr uint32_t kSlotTaken = 1u << 30;  // a group is reading the block out
 constexpr uint32_t kSlotHole = 3u << 30;   // nothing left to read
 constexpr uint32_t kSlotStateMask = 3u << 30;
-constexpr uint32_t kStripeBlocks = static_cast<uint32_t>(kIpStripeBytes / kIpBlockBytes);
 
 constexpr int kIpStripeThreads = 512;
 constexpr int kIpPermuteThreads = 256;
@@ -342,13 +344,22 @@ __global__ void __launch_bounds__(kIpStripeThreads, 2) k_ip_stripe(Work wk, int 
             wp += tot_blocks;
             __syncthreads();
         }
-        // stripe summary: full-block counts, partial blocks, slot states
-        // this stripe's blocks of digit d take the digit's slots [P, P + nfull)
-        // past its slot base, P claimed here in any order of the stripes
+        // stripe summary: full-block counts, partial blocks, slot states.
+        // This stripe's blocks of digit d take the digit's slots [P, P + nfull)
+        // past its slot base A_d = ceil(D_d / B), P claimed here in any order of
+        // the stripes; each full slot's word then names its block's destination.
+        uint32_t *pref = cnt;     // reuse: per-digit claimed share
+        uint32_t *abase = tstart; // reuse: per-digit slot base
         for (int d = t; d < kBins; d += T) {
-            wk.ip_prefix[static_cast<size_t>(si) * kBins + d] =
-                nfull[d] ? atomicAdd(&wk.ip_ncnt[static_cast<size_t>(s.big) * kBins + d], nfull[d]) : 0u;
+            pref[d] = nfull[d] ? atomicAdd(&wk.ip_ncnt[static_cast<size_t>(s.big) * kBins + d], nfull[d]) : 0u;
+            abase[d] = static_cast<uint32_t>((dbase(wk, big.bucket, g, d, big.len) + B - 1) / B);
             wk.ip_rem[static_cast<size_t>(si) * kBins + d] = static_cast<uint8_t>(fill[d]);
+        }
+        __syncthreads();
+        for (uint32_t j = t; j < wp; j += T) {
+            uint32_t *w = &wk.ip_state[big.state0 + s.slot0 + j];
+            const uint32_t v = *w, d = (v >> 22) & 0xFFu;
+            *w = kSlotFull | (abase[d] + pref[d] + (v & 0x3FFFFFu));
         }
         K *part = static_cast<K *>(wk.ip_part) + static_cast<size_t>(si) * kBins * B;
         for (int i = t; i < kBins * B; i += T) {
@@ -379,6 +390,7 @@ struct Carry {
     DigitGeo g;
     K *keys;
     K *ovf;
+    const uint64_t *dend;  // [kBins] D_{d+1}, relative to the bucket start (shared memory)
 
     // Reads the block in slot `slot` (keys past the bucket's end, in its last
     // partial slot, are not read).
@@ -394,13 +406,13 @@ struct Carry {
     // Writes a block of digit d into slot `slot`; keys past D_{d+1} go to the
     // digit's overflow buffer.
     __device__ void put(uint32_t d, uint32_t slot, const K (&v)[E], int gl) const {
-        const uint64_t dend = dbase(wk, big.bucket, g, d + 1, big.len);
+        const uint64_t end = dend[d];
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const uint64_t pos = static_cast<uint64_t>(slot) * B + gl + e * kGroup;
-            if (pos < dend) keys[big.start + pos] = v[e];
-            else if (pos - dend < static_cast<uint64_t>(B))
-                ovf[(static_cast<size_t>(bb) * kBins + d) * B + (pos - dend)] = v[e];
+            if (pos < end) keys[big.start + pos] = v[e];
+            else if (pos - end < static_cast<uint64_t>(B))
+                ovf[(static_cast<size_t>(bb) * kBins + d) * B + (pos - end)] = v[e];
             else ip_error(wk, kErrBounds);
         }
     }
@@ -415,6 +427,7 @@ __global__ void __launch_bounds__(kIpPermuteThreads) k_ip_permute(Work wk, int l
     const int leader = lane & ~(kGroup - 1);
     const unsigned gmask = 0xFFu << leader;
     const int p = level & 1;
+    __shared__ uint64_t dend[kBins];
     if (wk.ctl->error) return;
     const uint32_t ns = min(wk.ctl->n_stripes, wk.max_stripes);
     K *keys = static_cast<K *>(wk.keys);
@@ -423,17 +436,13 @@ __global__ void __launch_bounds__(kIpPermuteThreads) k_ip_permute(Work wk, int l
         const IpStripe s = wk.ip_stripes[si];
         const IpBig big = wk.ip_big[s.big];
         const Bucket b = wk.buckets[p][big.bucket];
-        const C cy{wk, big, s.big, digit_geo(b, wk.radix_bits), keys, ovf};
+        __syncthreads();  // the previous stripe's groups are done with dend
+        for (int d = threadIdx.x; d < kBins; d += kIpPermuteThreads)
+            dend[d] = dbase(wk, big.bucket, digit_geo(b, wk.radix_bits), d + 1, big.len);
+        __syncthreads();
+        const C cy{wk, big, s.big, digit_geo(b, wk.radix_bits), keys, ovf, dend};
         uint32_t *state = wk.ip_state + big.state0;
         const uint32_t nslots = static_cast<uint32_t>((big.len + B - 1) / B);
-        // destination of the block whose state word is w and whose slot was `slot`:
-        // digit d's slot base + its stripe's share of d + its rank
-        auto dest = [&](uint32_t w, uint32_t slot, uint32_t &d) {
-            d = (w >> 22) & 0xFFu;
-            const uint32_t home = big.first_stripe + slot / kStripeBlocks;
-            const uint64_t a_d = (dbase(wk, big.bucket, cy.g, d, big.len) + B - 1) / B;
-            return static_cast<uint32_t>(a_d + wk.ip_prefix[static_cast<size_t>(home) * kBins + d] + (w & 0x3FFFFFu));
-        };
         bool fail = false;
         for (uint32_t j = grp; j < s.nfull && !fail; j += GROUPS) {
             const uint32_t seed = s.slot0 + j;
@@ -449,11 +458,11 @@ __global__ void __launch_bounds__(kIpPermuteThreads) k_ip_permute(Work wk, int l
                 __threadfence();
                 atomicOr(&state[seed], kSlotHole);
             }
-            uint32_t xw = old, xslot = seed;  // the carried block's state word and original slot
+            uint32_t xw = old;  // the carried block's state word: its destination
             // carry until the block lands on a slot that holds nothing to take
             for (int hop = 0;; ++hop) {
-                uint32_t d;
-                const uint32_t dst = dest(xw, xslot, d);
+                const uint32_t d = digit_of(__shfl_sync(gmask, x[0], leader), cy.g);
+                const uint32_t dst = xw & ~kSlotStateMask;
                 if (dst >= nslots || hop > (1 << 26)) {
                     if (gl == 0) ip_error(wk, kErrBounds);
                     fail = true;
@@ -474,7 +483,6 @@ __global__ void __launch_bounds__(kIpPermuteThreads) k_ip_permute(Work wk, int l
 #pragma unroll
                     for (int e = 0; e < E; ++e) x[e] = y[e];
                     xw = dw;
-                    xslot = dst;
                     continue;
                 }
                 if ((dw & kSlotStateMask) == kSlotTaken) {
@@ -562,7 +570,7 @@ __global__ void __launch_bounds__(kIpCleanupThreads) k_ip_cleanup(Work wk, int l
 template <typename K>
 __global__ void k_ip_account(Work wk) {
     const unsigned long long used =
-        static_cast<unsigned long long>(min(wk.ctl->n_stripes, wk.max_stripes)) * (kBins * kIpBlockBytes + 5 * kBins) +
+        static_cast<unsigned long long>(min(wk.ctl->n_stripes, wk.max_stripes)) * (kBins * kIpBlockBytes + kBins) +
         static_cast<unsigned long long>(min(wk.ctl->n_big, wk.max_big)) * (kBins * kIpBlockBytes + 4 * kBins) +
         static_cast<unsigned long long>(min(wk.ctl->n_slots, wk.max_slots)) * 4;
     atomicMax(&wk.ctl->aux_used, used);

@@ -48,24 +48,24 @@ def classify(keys, digit_of, stripe_keys, B, ndig):
 
 def carrier(gid, seeds, shared, log):
     """One carrier group as a coroutine; every yield is a scheduling point."""
-    buf, state, dest, B, dend = shared["buf"], shared["state"], shared["dest"], shared["B"], shared["dend"]
+    buf, state, B, dend = shared["buf"], shared["state"], shared["B"], shared["dend"]
     for seed in seeds:
-        st, d, r = state[seed]  # atomic OR of TAKEN: read and set in one step
+        st, d, dst0 = state[seed]  # atomic OR of TAKEN: read and set in one step
         if shared.get("split_seed_or"):  # planted mistake: read, then set later
             yield
         if st == FULL:
-            state[seed] = (TAKEN, d, r)
+            state[seed] = (TAKEN, d, dst0)
         yield
         if st != FULL:  # it was taken or a hole
             continue
         x = buf[seed * B:(seed + 1) * B]
         log["read"].add(seed)
         yield
-        state[seed] = (HOLE, d, r)
-        xw, xslot = (d, r), seed
+        state[seed] = (HOLE, d, dst0)
+        xw = (d, dst0)  # the carried block's digit (from its keys) and destination (from its word)
         while True:
             yield
-            dst = dest(xw[0], xw[1], xslot)
+            dst = xw[1]
             y = buf[dst * B:(dst + 1) * B]  # speculative read, same round trip as the OR
             dst_state = state[dst]
             if dst_state[0] == FULL:
@@ -74,7 +74,7 @@ def carrier(gid, seeds, shared, log):
             if dst_state[0] == FULL:
                 log["read"].add(dst)
                 put(buf, dst, x, B, xw[0], dend, shared, log)
-                x, xw, xslot = y, dst_state[1:], dst
+                x, xw = y, dst_state[1:]
                 continue
             spins = 0
             while state[dst][0] != HOLE:  # a seeder is reading dst out
@@ -116,11 +116,13 @@ def run_model(n, B, stripe_blocks, ndig, groups, seed, split_seed_or=False):
             prefix[s][d] = N[d]
             N[d] += nfull[s][d]
     A = [(D[d] + B - 1) // B for d in range(ndig)]
+    # each full slot's word then names its block's destination: digit slot
+    # base + the stripe's share + the block's rank
+    for slot, (st, d, r) in enumerate(state):
+        if st == FULL:
+            state[slot] = (FULL, d, A[d] + prefix[slot // stripe_blocks][d] + r)
 
-    def dest(d, r, slot):
-        return A[d] + prefix[slot // stripe_blocks][d] + r
-
-    shared = {"buf": buf, "state": state, "state0": list(state), "dest": dest, "B": B, "dend": D,
+    shared = {"buf": buf, "state": state, "state0": list(state), "B": B, "dend": D,
               "ovf": [[] for _ in range(ndig)], "split_seed_or": split_seed_or}
     log = {"read": set(), "written": set()}
     # groups seed the full slots of the stripes, interleaved
