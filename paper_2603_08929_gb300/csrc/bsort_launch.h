@@ -36,6 +36,11 @@ struct Recorder {
         rec[count].call = calls;
         cudaEventRecord(rec[count].a, stream);
     }
+    // Counts kernels of the current group beyond the one begin() counted.
+    void more(int kernels) {
+        launches += kernels;
+        held_launches += kernels;
+    }
     void end() {
         if (!active || count >= BSORT_PROFILE_MAX) return;
         cudaEventRecord(rec[count].b, stream);

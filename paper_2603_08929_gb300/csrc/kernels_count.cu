@@ -281,6 +281,7 @@ void launch_count16(const CountWork &cw, cudaStream_t st, Recorder &rec, int num
     k_count_hist16<<<cw.grid16, kHist16Threads, 32768 * 4, st>>>(static_cast<const uint16_t *>(cw.keys), cw.n,
                                                                  cw.codec, cw.partial, corr);
     k_count_reduce16<<<256, 256, 0, st>>>(cw.partial, static_cast<int>(cw.grid16), corr, cw.hist);
+    rec.more(1);
     rec.end();
     rec.begin(BSORT_K_COUNT_SCAN, -1);
     k_count_scan<<<1, 1024, 0, st>>>(cw.hist, 65536, cw.starts);

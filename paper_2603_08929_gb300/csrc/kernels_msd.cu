@@ -1730,6 +1730,7 @@ void msd_levels_and_finish(const Work &wk, cudaStream_t st, Recorder &rec, int n
     rec.begin(BSORT_K_FINISH, -1);
     k_finish<K, FT, FI><<<num_sms * 8, FT, finish_smem<K, FT, FI>(), st>>>(wk);
     k_finish_lsd<K, FT, FI><<<num_sms * 4, FT, finish_lsd_smem<K, FT, FI>(), st>>>(wk);
+    rec.more(1);
     rec.end();
     if (levels) {
         rec.begin(BSORT_K_FILL, -1);
@@ -1757,6 +1758,7 @@ void launch_msd_segmented(const Work &wk, const uint64_t *d_offsets, uint32_t ns
     k_zero_ctl<<<1, 256, 0, st>>>(wk);
     k_seg_init<<<max(1u, min(static_cast<uint32_t>(num_sms) * 4, (nseg + 255) / 256)), 256, 0, st>>>(wk, d_offsets,
                                                                                                       nseg);
+    rec.more(1);
     rec.end();
     msd_levels_and_finish<K>(wk, st, rec, num_sms, true);
 }

@@ -174,3 +174,23 @@ def test_counting_finish_full_size():
     got, fu = _sorted_with_profile(x)
     assert fu["counting"] > 0.99 * (fu["counting"] + fu["compare"] + fu["lsd"]), fu
     check_full_size(x, got, False)
+
+
+@pytest.mark.gpu
+def test_launch_count_is_every_kernel():
+    """The count the benchmark reports as gpu_launches: every kernel of a call."""
+    import torch
+    import paper_2603_08929_gb300 as bs
+    h = bs.Handle()
+    for n, want in ((1 << 20, 1 + 4 * 4 + 2 + 1), (3000, 1 + 2), (1 << 19, None)):
+        x = W.make("uniform", "int32", n, seed=1)
+        t = to_device(x)
+        ws = torch.empty(bs.workspace_bytes(n, "int32"), dtype=torch.uint8, device=t.device)
+        bs.bsort_keys_ws(h, t, ws)
+        if want is not None:
+            assert h.launch_count() == want, (n, h.launch_count())
+    x = W.make("uniform", "uint16", 1 << 20, seed=1)
+    t = to_device(x)
+    ws = torch.empty(bs.workspace_bytes(t.numel(), "uint16"), dtype=torch.uint8, device=t.device)
+    bs.bsort_keys_ws(h, t, ws)
+    assert h.launch_count() == 4  # histogram, reduce, scan, fill
