@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--mode", default="plain", choices=["plain", "segmented", "serve"],
                     help="plain: one 2^log2n array; segmented: the batched workload (see run_segmented)")
     ap.add_argument("--segments", type=int, default=10000, help="segments per dtype (segmented mode)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="segmented mode: library default tuning instead of the autotuner's choice")
     ap.add_argument("--seg-max-log2", type=int, default=20, help="segment sizes floor(2^(k*u)), u uniform")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrivals per second (serve mode)")
     ap.add_argument("--serve-seconds", type=float, default=60.0, help="length of the arrival trace (serve mode)")
@@ -66,6 +68,9 @@ def parse():
     ap.add_argument("--desc", action="store_true")
     ap.add_argument("--inplace", action="store_true", help="in-place mode (no alternate buffer); reports aux bytes")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--radix-bits", type=int, default=0, help="plain mode: MSD digit width 4..11 (0: default 8)")
+    ap.add_argument("--unit-keys", type=int, default=0, help="plain mode: shared-memory finish threshold (0: default)")
+    ap.add_argument("--chunk-tiles", type=int, default=0, help="plain mode: chunk of 1 or 2 scatter tiles (0: 2)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample-log2", type=int, default=23)
@@ -244,12 +249,14 @@ def run_segmented(args, rank, world):
     import torch
     import paper_2603_08929_gb300 as bs
     from paper_2603_08929_gb300 import build as B
+    from paper_2603_08929_gb300 import tune
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     B.build()
     dev = torch.device("cuda", torch.cuda.current_device())
     h = bs.Handle()
     stream = torch.cuda.current_stream()
     arms = []
+    tuned = {}
     for k, dt in enumerate(("int32", "float32")):
         sizes = W.segment_sizes(args.seed + 17 * k + rank, args.segments, args.seg_max_log2)
         n = int(sizes.sum())
@@ -257,9 +264,22 @@ def run_segmented(args, rank, world):
         off = torch.from_numpy(np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)).to(dev)
         pristine = torch.from_numpy(x).to(dev)
         keys = pristine.clone()
-        ws = torch.empty(bs.segmented_workspace_bytes(n, len(sizes), dt), dtype=torch.uint8, device=dev)
-        g = bs.Graph(h, keys, ws, offsets=off)
-        arms.append((dt, sizes, n, pristine, keys, ws, g, off))
+        # autotuned digit width, finish threshold and chunk for this workload (untimed)
+        tuning = None
+        if not args.no_autotune:
+            log = []
+            best = tune.autotune_segmented(pristine, off, steps=2, log=log)
+            tuning = {f: best[f] for f in tune.FIELDS}
+            tuned[dt] = {"chosen": tuning, "ms": best["ms"],
+                         "candidates_ms": {"r%d T=%s chunk=%d" % (c["radix_bits"] or 8, c["unit_keys"] or "def",
+                                                                   c["chunk_tiles"] or 2): round(ms, 3)
+                                           for c, ms in log}}
+        hk = bs.Handle()
+        hk.set_tuning(4, tuning)
+        ws = torch.empty(bs.segmented_workspace_bytes(n, len(sizes), dt, tuning=tuning), dtype=torch.uint8,
+                         device=dev)
+        g = bs.Graph(hk, keys, ws, offsets=off)
+        arms.append((dt, sizes, n, pristine, keys, ws, g, off, hk))
     total = sum(a[2] for a in arms)
 
     def timed(fn, steps, warmup):
@@ -290,7 +310,7 @@ def run_segmented(args, rank, world):
         if a[6].error(stream) != 0:
             raise RuntimeError("device error word set in the segmented sort")
     # correctness of the last run: every segment non-decreasing (int32 arm)
-    dt, sizes, n, pristine, keys, ws, g, off = arms[0]
+    dt, sizes, n, pristine, keys, ws, g, off, _ = arms[0]
     seg_id = torch.repeat_interleave(torch.arange(len(sizes), device=dev), torch.from_numpy(sizes).to(dev))
     same = seg_id[1:] == seg_id[:-1]
     ok = bool(torch.all((keys[1:] >= keys[:-1]) | ~same).item())
@@ -318,6 +338,7 @@ def run_segmented(args, rank, world):
                                "[1, 2^%d], uniform bits, ascending; one captured graph per dtype"
                                % (args.segments, args.segments, args.seg_max_log2),
                    "keys": total, "segments": 2 * args.segments,
+                   "tuning": tuned if tuned else "library defaults (--no-autotune)",
                    "l2": "inputs %.1f GB > L2; restored from a pristine copy before each step (untimed)"
                          % (sum(a[2] * 4 for a in arms) / 1e9)},
         "plain_per_segment": {"value": total / (ms_plain * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms_plain,
@@ -464,8 +485,12 @@ def main():
     bufs = [base.clone() for _ in range(total_steps)]
     del base
     mode = bs.MODE_INPLACE if args.inplace else bs.MODE_PINGPONG
-    ws = torch.empty(bs.workspace_bytes(n, args.dtype, mode=mode), dtype=torch.uint8, device=dev)
+    tuning = {"radix_bits": args.radix_bits, "unit_keys": args.unit_keys, "chunk_tiles": args.chunk_tiles}
+    tuning = tuning if any(tuning.values()) and esize >= 4 else None
+    ws = torch.empty(bs.workspace_bytes(n, args.dtype, mode=mode, tuning=tuning), dtype=torch.uint8, device=dev)
     h = bs.Handle()
+    if tuning:
+        h.set_tuning(esize, tuning)
     h.set_profiling(True)
     stream = torch.cuda.current_stream()
 
@@ -533,14 +558,15 @@ def main():
             ", in-place mode" if args.inplace else ""),
             "n": n, "per_gpu_keys": n, "l2": "input 2^%d x %d B > L2; each step sorts its own copy"
                                             % (args.log2n, esize),
-            "parallelism": "replicas%d" % world},
+            "parallelism": "replicas%d" % world,
+            "tuning": tuning or "library defaults"},
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "kernel": dom_kind, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
                      "traffic": measured_traffic(
                          dom_kind, args.dtype,
                          dk["bytes"] / (2 * esize) / max(dk["launches"], 1)) if dom_kind in (
-                             "finish", "scatter") else None},
+                             "finish", "scatter") and not tuning else None},
         "sort_roofline": {"counted_bytes_per_step": total_bytes, "achieved": sort_gbs,
                           "frac": sort_gbs / peak, "peak": peak,
                           "fixed_2nb_frac": 2 * n * esize / (ms_per_step * 1e-3) / 1e9 / peak},
@@ -574,7 +600,7 @@ def main():
         e2e_s = statistics.median(ts)
         line["e2e"] = {"value": n / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": n * esize,
                        "d2h_bytes_per_step": n * esize, "ms_per_step": e2e_s * 1e3,
-                       "api": "bsort_keys_host (pinned host array in and out)"}
+                       "api": "bsort_keys_host (pinned host array in and out; library default tuning)"}
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(x, args.desc, args.cpu_sample_log2)
     if rank == 0:

@@ -128,22 +128,30 @@ bsort_status bsort_keys_ws(bsort_handle *handle, void *keys, size_t n, bsort_dty
  * Runtime tuning of the MSD path of a handle (used by bsort_keys_ws on that
  * handle), per key width (key_bytes 4 or 8); 1- and 2-byte keys take the
  * counting path and have nothing to tune.  Zero fields keep the defaults:
- *   radix_bits  digit width of the MSD levels, 4..8 (default 8): r binary
- *               partitions of Alg. 1 fused per pass; ceil(w / r) levels;
+ *   radix_bits  digit width of the MSD levels, 4..11 (default 8): r binary
+ *               partitions of Alg. 1 fused per pass; ceil(w / r) levels.
+ *               Widths above 8 use 2048-entry digit tables; the in-place
+ *               mode runs widths above 8 as 8;
  *   unit_keys   largest bucket the shared-memory finish takes, 256..default
  *               (5104 for 4-byte keys, 2544 for 8-byte keys);
  *   merge_keys  adjacent small buckets merge up to this many keys, 64..4/5 of
- *               unit_keys (default 4/5 of unit_keys, rounded down to 64).
- * The result never depends on the tuning, only the speed.  A workspace for a
- * tuned handle must be sized with bsort_workspace_bytes_tuned (a smaller
- * finish threshold needs longer work lists).  NULL restores the defaults.
- * Invalid fields: BSORT_ERR_INVALID_ARG, nothing changed.
+ *               unit_keys (default 4/5 of unit_keys, rounded down to 64);
+ *   chunk_tiles keys one CTA histograms and scatters at a time, in scatter
+ *               tiles: 1 or 2 (default 2; a tile is 8192 4-byte or 4096
+ *               8-byte keys).
+ * The result never depends on the tuning, only the speed.  The tuning applies
+ * to bsort_keys_ws and to the segmented calls on that handle.  A workspace
+ * for a tuned handle must be sized with bsort_workspace_bytes_tuned or
+ * bsort_segmented_workspace_bytes_tuned (a smaller finish threshold, a
+ * narrower digit or a smaller chunk needs longer work lists, a wider digit
+ * larger tables).  NULL restores the defaults.  Invalid fields:
+ * BSORT_ERR_INVALID_ARG, nothing changed.
  */
 typedef struct {
     int32_t radix_bits;
     int32_t unit_keys;
     int32_t merge_keys;
-    int32_t pad;
+    int32_t chunk_tiles;
 } bsort_tuning;
 bsort_status bsort_handle_set_tuning(bsort_handle *handle, int key_bytes, const bsort_tuning *tuning);
 bsort_status bsort_workspace_bytes_tuned(size_t n, bsort_dtype dt, bsort_mode mode, const bsort_tuning *tuning,
@@ -208,6 +216,9 @@ bsort_status bsort_keys_host(void *host_keys, size_t n, bsort_dtype dt, int desc
  * shared-memory finish size, finish units) of the MSD levels.
  */
 bsort_status bsort_segmented_workspace_bytes(size_t n, size_t num_segments, bsort_dtype dt, size_t *bytes);
+/* Workspace of a segmented sort on a handle tuned with `tuning` (NULL: defaults). */
+bsort_status bsort_segmented_workspace_bytes_tuned(size_t n, size_t num_segments, bsort_dtype dt,
+                                                   const bsort_tuning *tuning, size_t *bytes);
 bsort_status bsort_keys_segmented_ws(bsort_handle *handle, void *keys, size_t n, const uint64_t *d_offsets,
                                      size_t num_segments, bsort_dtype dt, int descending, void *workspace,
                                      size_t ws_bytes, void *stream);

@@ -68,7 +68,7 @@ class _ServerInfo(ctypes.Structure):
 
 class _Tuning(ctypes.Structure):
     _fields_ = [("radix_bits", ctypes.c_int32), ("unit_keys", ctypes.c_int32), ("merge_keys", ctypes.c_int32),
-                ("pad", ctypes.c_int32)]
+                ("chunk_tiles", ctypes.c_int32)]
 
 
 class BsortError(RuntimeError):
@@ -116,6 +116,8 @@ def lib():
         L.bsort_keys_noalloc.restype = i
         L.bsort_segmented_workspace_bytes.argtypes = [sz, sz, i, ctypes.POINTER(sz)]
         L.bsort_segmented_workspace_bytes.restype = i
+        L.bsort_segmented_workspace_bytes_tuned.argtypes = [sz, sz, i, ctypes.POINTER(_Tuning), ctypes.POINTER(sz)]
+        L.bsort_segmented_workspace_bytes_tuned.restype = i
         L.bsort_keys_segmented_ws.argtypes = [vp, vp, sz, vp, sz, i, i, vp, sz, vp]
         L.bsort_keys_segmented_ws.restype = i
         L.bsort_keys_segmented.argtypes = [vp, sz, vp, sz, i, i, vp]
@@ -225,12 +227,12 @@ def _tuning(t):
     if t is None:
         return None
     return ctypes.byref(_Tuning(int(t.get("radix_bits", 0)), int(t.get("unit_keys", 0)),
-                                int(t.get("merge_keys", 0)), 0))
+                                int(t.get("merge_keys", 0)), int(t.get("chunk_tiles", 0))))
 
 
 def workspace_bytes(n: int, dtype, mode: int = MODE_PINGPONG, tuning: dict = None) -> int:
     """Workspace bytes for bsort_keys_ws; ``tuning`` (a dict with radix_bits,
-    unit_keys, merge_keys) sizes it for a handle tuned that way."""
+    unit_keys, merge_keys, chunk_tiles) sizes it for a handle tuned that way."""
     out = ctypes.c_size_t(0)
     if tuning is None:
         _check(lib().bsort_workspace_bytes(int(n), _dtype_code(dtype), int(mode), ctypes.byref(out)),
@@ -322,10 +324,17 @@ def bsort_keys_noalloc(keys, descending: bool = False, stream=None) -> None:
            "bsort_keys_noalloc")
 
 
-def segmented_workspace_bytes(n: int, num_segments: int, dtype) -> int:
+def segmented_workspace_bytes(n: int, num_segments: int, dtype, tuning: dict = None) -> int:
+    """Workspace bytes of a segmented sort; ``tuning`` sizes it for a handle
+    tuned that way."""
     out = ctypes.c_size_t(0)
-    _check(lib().bsort_segmented_workspace_bytes(int(n), int(num_segments), _dtype_code(dtype), ctypes.byref(out)),
-           "bsort_segmented_workspace_bytes")
+    if tuning is None:
+        _check(lib().bsort_segmented_workspace_bytes(int(n), int(num_segments), _dtype_code(dtype),
+                                                     ctypes.byref(out)), "bsort_segmented_workspace_bytes")
+    else:
+        _check(lib().bsort_segmented_workspace_bytes_tuned(int(n), int(num_segments), _dtype_code(dtype),
+                                                           _tuning(tuning), ctypes.byref(out)),
+               "bsort_segmented_workspace_bytes_tuned")
     return int(out.value)
 
 

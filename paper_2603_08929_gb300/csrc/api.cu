@@ -70,7 +70,7 @@ struct MsdLayout {
 };
 
 MsdLayout msd_layout(size_t n, int key_bytes, size_t nseg = 0, bool inplace = false, const Tuning &tune = Tuning()) {
-    const MsdShape s = msd_shape(key_bytes, tune);
+    const MsdShape s = msd_shape(key_bytes, tune, inplace);
     MsdLayout L;
     // finish units hold at least merge_cap / 4 keys unless merged, and merged
     // groups reach merge_cap unless a run ends: the unit count per level is
@@ -80,7 +80,10 @@ MsdLayout msd_layout(size_t n, int key_bytes, size_t nseg = 0, bool inplace = fa
     L.max_buckets = static_cast<uint32_t>(n / (s.unit_cap + 1) + 2);
     // a bucket of len keys spans ceil((len + misalignment) / chunk) <= 1 + (len + 16) / chunk chunks
     L.max_chunks = static_cast<uint32_t>(L.max_buckets + (n + 16ull * L.max_buckets) / s.chunk + 2);
-    L.max_units = static_cast<uint32_t>((4 + 2 * static_cast<uint64_t>(s.levels)) * per_t + 16 + nseg);
+    // wide digits are classified in pages of 256: a run of merged small
+    // buckets also ends at a page boundary (one more unit per page and parent)
+    const uint64_t page_units = static_cast<uint64_t>(s.bins / kBins - 1) * s.levels * L.max_buckets;
+    L.max_units = static_cast<uint32_t>((4 + 2 * static_cast<uint64_t>(s.levels)) * per_t + 16 + nseg + page_units);
     L.max_fills = static_cast<uint32_t>(n / kFillPiece + per_t + 16);
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -95,10 +98,10 @@ MsdLayout msd_layout(size_t n, int key_bytes, size_t nseg = 0, bool inplace = fa
     L.buckets1 = take(sizeof(Bucket) * L.max_buckets);
     L.chunks0 = take(sizeof(Chunk) * L.max_chunks);
     L.chunks1 = take(sizeof(Chunk) * L.max_chunks);
-    L.hist = take(sizeof(uint32_t) * kBins * static_cast<size_t>(L.max_chunks));
+    L.hist = take(sizeof(uint32_t) * s.bins * static_cast<size_t>(L.max_chunks));
     L.cand = take(sizeof(uint64_t) * L.max_chunks);
     L.cor = take(sizeof(uint64_t) * L.max_chunks);
-    L.bbase = take(sizeof(uint32_t) * kBins * static_cast<size_t>(L.max_buckets));
+    L.bbase = take(sizeof(uint32_t) * s.bins * static_cast<size_t>(L.max_buckets));
     L.units = take(sizeof(Unit) * L.max_units);
     L.fb_units = take(sizeof(Unit) * L.max_units);
     L.fills = take(sizeof(Fill) * L.max_fills);
@@ -198,7 +201,7 @@ bsort_status check_args(const void *keys, size_t n, bsort_dtype dt, DtypeInfo *d
 
 Work make_work(const MsdLayout &L, char *ws, void *keys, size_t n, const DtypeInfo &di, const Codec &codec,
                const Tuning &tune = Tuning()) {
-    const MsdShape s = msd_shape(di.bytes, tune);
+    const MsdShape s = msd_shape(di.bytes, tune, L.inplace);
     Work wk;
     wk.ctl = reinterpret_cast<Ctl *>(ws + L.ctl);
     wk.buckets[0] = reinterpret_cast<Bucket *>(ws + L.buckets0);
@@ -225,6 +228,7 @@ Work make_work(const MsdLayout &L, char *ws, void *keys, size_t n, const DtypeIn
     wk.merge_cap = s.merge_cap;
     wk.w = di.bytes * 8;
     wk.radix_bits = s.radix_bits;
+    wk.bins = s.bins;
     wk.levels = s.levels;
     wk.stop_level = s.levels;
     wk.keys_vec_ok = (reinterpret_cast<uintptr_t>(keys) & 15) == 0;
@@ -338,9 +342,10 @@ bsort_status run_segmented(bsort_handle *h, void *keys, size_t n, const uint64_t
     }
     begin_call(h, st);
     if (!record) h->rec.active = false;
-    const MsdLayout L = msd_layout(n, di.bytes, nseg);
+    const Tuning &tune = h->tune[di.bytes == 8];
+    const MsdLayout L = msd_layout(n, di.bytes, nseg, false, tune);
     if (ws_bytes < L.total) return BSORT_ERR_WORKSPACE_TOO_SMALL;
-    const Work wk = make_work(L, static_cast<char *>(workspace), keys, n, di, codec_for(di, descending));
+    const Work wk = make_work(L, static_cast<char *>(workspace), keys, n, di, codec_for(di, descending), tune);
     if (di.bytes == 4) launch_msd_segmented<uint32_t>(wk, d_offsets, static_cast<uint32_t>(nseg), st, h->rec, sms);
     else launch_msd_segmented<uint64_t>(wk, d_offsets, static_cast<uint32_t>(nseg), st, h->rec, sms);
     h->last_path = 2;
@@ -378,6 +383,7 @@ bool to_tuning(const bsort_tuning *in, int key_bytes, Tuning *out) {
         t.radix_bits = in->radix_bits;
         t.unit_keys = in->unit_keys;
         t.merge_keys = in->merge_keys;
+        t.chunk_tiles = in->chunk_tiles;
     }
     if (!tuning_valid(key_bytes, t)) return false;
     *out = t;
@@ -506,6 +512,17 @@ bsort_status bsort_segmented_workspace_bytes(size_t n, size_t num_segments, bsor
     return BSORT_OK;
 }
 
+bsort_status bsort_segmented_workspace_bytes_tuned(size_t n, size_t num_segments, bsort_dtype dt,
+                                                   const bsort_tuning *tuning, size_t *bytes) {
+    DtypeInfo di;
+    if (!bytes || !dtype_info(dt, &di)) return BSORT_ERR_INVALID_ARG;
+    if (di.bytes < 4) return BSORT_ERR_UNSUPPORTED;
+    Tuning t;
+    if (!to_tuning(tuning, di.bytes, &t)) return BSORT_ERR_INVALID_ARG;
+    *bytes = msd_layout(n, di.bytes, num_segments, false, t).total;
+    return BSORT_OK;
+}
+
 bsort_status bsort_keys_segmented_ws(bsort_handle *handle, void *keys, size_t n, const uint64_t *d_offsets,
                                      size_t num_segments, bsort_dtype dt, int descending, void *workspace,
                                      size_t ws_bytes, void *stream) {
@@ -530,7 +547,8 @@ bsort_status bsort_keys_segmented(void *keys, size_t n, const uint64_t *d_offset
     bsort_handle *h = default_handle(dev);
     if (!h) return BSORT_ERR_NO_MEMORY;
     std::lock_guard<std::mutex> lk(h->mu);
-    const bsort_status gs = grow(&h->ws, &h->ws_bytes, msd_layout(n, di.bytes, num_segments).total);
+    const bsort_status gs =
+        grow(&h->ws, &h->ws_bytes, msd_layout(n, di.bytes, num_segments, false, h->tune[di.bytes == 8]).total);
     if (gs != BSORT_OK) return gs;
     return run_segmented(h, keys, n, d_offsets, num_segments, di, descending, h->ws, h->ws_bytes,
                          static_cast<cudaStream_t>(stream), true);

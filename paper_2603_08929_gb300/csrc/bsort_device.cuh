@@ -17,9 +17,11 @@
 
 namespace bsort {
 
-constexpr int kRadixBits = 8;              // default digit width (and the widest one)
-constexpr int kBins = 1 << kRadixBits;
+constexpr int kRadixBits = 8;              // default digit width of the MSD levels
+constexpr int kBins = 1 << kRadixBits;     // digits of an 8-bit pass (narrow tables, LSD finish passes)
 constexpr int kMinRadixBits = 4;           // narrowest tunable digit width
+constexpr int kMaxRadixBits = 11;          // widest tunable digit width (ping-pong levels)
+constexpr int kWideBins = 1 << kMaxRadixBits;  // table stride of the digit widths above kRadixBits
 constexpr int kMaxLevels = 16;             // ceil(64 / kMinRadixBits)
 
 // device error word bits
@@ -114,10 +116,10 @@ struct Work {
     Ctl *ctl;
     Bucket *buckets[2];
     Chunk *chunks[2];
-    uint32_t *hist;         // [kBins][max_chunks], digit-major; excl. prefix after the scan
+    uint32_t *hist;         // [bins][max_chunks], digit-major; excl. prefix after the scan
     uint64_t *chunk_and;    // [max_chunks]
     uint64_t *chunk_or;     // [max_chunks]
-    uint32_t *bucket_base;  // [max_buckets][kBins]: digit totals, then digit bases relative to the bucket start
+    uint32_t *bucket_base;  // [max_buckets][bins]: digit totals, then digit bases relative to the bucket start
     Unit *units;
     Unit *fb_units;  // [max_units] skewed units for the LSD finish
     Fill *fills;
@@ -130,7 +132,8 @@ struct Work {
     uint32_t unit_cap;    // largest run the shared-memory finish sorts
     uint32_t merge_cap;   // adjacent small buckets merge while their sum stays <= this
     int32_t w;            // key bits
-    int32_t radix_bits;   // digit width of the MSD levels (kMinRadixBits..kRadixBits)
+    int32_t radix_bits;   // digit width of the MSD levels (kMinRadixBits..kMaxRadixBits)
+    uint32_t bins;        // row stride of hist / bucket_base: kBins up to 8-bit digits, kWideBins above
     int32_t levels;       // host-launched MSD levels: ceil(w / radix_bits)
     int32_t stop_level;   // levels actually run (levels, or fewer for an intermediate state)
     bool keys_vec_ok;     // caller's buffer is 16-byte aligned (vector loads)

@@ -51,25 +51,31 @@ struct Recorder {
 // Per-key-width tuning of the MSD path.
 struct MsdShape {
     uint32_t tile;       // keys per scatter tile (threads x items)
-    uint32_t chunk;      // keys per chunk (multiple of tile)
+    uint32_t chunk;      // keys per chunk (1 or 2 tiles)
     uint32_t unit_cap;   // largest bucket finished in shared memory
     uint32_t merge_cap;  // adjacent small buckets merge up to this many keys
     int levels;          // host-side level launches (ceil(w / radix bits))
     int radix_bits;      // digit width
+    uint32_t bins;       // row stride of the per-digit tables (kBins or kWideBins)
 };
 
-// Runtime tuning of the MSD path (0 fields: defaults).  Digit width 4..8
-// bits; finish threshold between 256 keys and the compile-time tile; merge
-// threshold between 64 keys and the finish threshold.
+// Most tiles per chunk (the scatter stages a whole chunk in shared memory).
+constexpr int kMaxChunkTiles = 2;
+
+// Runtime tuning of the MSD path (0 fields: defaults).  Digit width 4..11
+// bits (the in-place mode caps it at 8); finish threshold between 256 keys
+// and the compile-time tile; merge threshold between 64 keys and the finish
+// threshold; chunk of 1 or 2 scatter tiles.
 struct Tuning {
     int radix_bits = 0;
     int unit_keys = 0;
     int merge_keys = 0;
+    int chunk_tiles = 0;
 };
 
 // false: a field is out of range.
 bool tuning_valid(int key_bytes, const Tuning &t);
-MsdShape msd_shape(int key_bytes, const Tuning &t = Tuning());
+MsdShape msd_shape(int key_bytes, const Tuning &t = Tuning(), bool inplace = false);
 
 // Launches the whole MSD pipeline for 4- or 8-byte keys.
 template <typename K>

@@ -107,7 +107,7 @@ __device__ __forceinline__ uint32_t digit_of(K key, const DigitGeo &g) {
 // D_d relative to the bucket start: the digit base, len past the last digit.
 __device__ __forceinline__ uint64_t dbase(const Work &wk, uint32_t bucket, const DigitGeo &g, uint32_t d,
                                           uint64_t len) {
-    return d <= g.mask ? wk.bucket_base[static_cast<size_t>(bucket) * kBins + d] : len;
+    return d <= g.mask ? wk.bucket_base[static_cast<size_t>(bucket) * wk.bins + d] : len;
 }
 
 // ---------------------------------------------------------------------------
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(kIpSmemThreads) k_ip_smem(Work wk, int level) 
         K *base = keys + b.start;
         for (int j = threadIdx.x; j < len; j += T) keys_s[j] = b.raw ? encode_key(base[j], wk.codec) : base[j];
         for (uint32_t d = threadIdx.x; d < kBins; d += T)
-            cur[d] = d <= g.mask ? wk.bucket_base[static_cast<size_t>(i) * kBins + d] : 0u;
+            cur[d] = d <= g.mask ? wk.bucket_base[static_cast<size_t>(i) * wk.bins + d] : 0u;
         __syncthreads();
         bool bad = false;
         for (int j = threadIdx.x; j < len; j += T) {

@@ -165,10 +165,11 @@ __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
 // What the scatter needs of one chunk before it can stage keys: the chunk,
 // the next chunk (same bucket or not), the bucket, and per digit the chunk's
 // exclusive prefix, the next chunk's, and the bucket's digit base.
+template <int NB>
 struct ScatterPre {
     Chunk ch, chn;
     Bucket b;
-    uint32_t hc[kBins], hn[kBins], bb[kBins];
+    uint32_t hc[NB], hn[NB], bb[NB];
 };
 
 // Shared-memory buffers of one tile ranking, at byte offset BASE of dynamic
@@ -628,11 +629,16 @@ __device__ __forceinline__ void hist_range(const K *__restrict__ src, uint64_t l
     }
 }
 
-// Per-chunk digit histogram (one shared-memory row per warp) and AND/OR.
-template <typename K, int THREADS>
+// Per-chunk digit histogram and AND/OR.  NB digit slots: with NB = kBins
+// every warp counts into its own shared-memory row; with kWideBins (digits of
+// 9..11 bits, where same-digit collisions inside a warp are rare) four rows
+// are shared by the warps.  Rows 0 .. 2^radix_bits - 1 of the chunk's
+// histogram column are written.
+template <typename K, int THREADS, int NB>
 __global__ void __launch_bounds__(THREADS) k_hist(Work wk, int level) {
     constexpr int WARPS = THREADS / 32;
-    __shared__ uint32_t sh[WARPS * kBins];
+    constexpr int ROWS = NB <= kBins ? WARPS : 4;
+    __shared__ uint32_t sh[ROWS * NB];
     __shared__ unsigned long long ta[WARPS], to[WARPS];
     const int p = level & 1;
     if (wk.ctl->error) return;  // an earlier launch found a problem: stop touching memory
@@ -640,7 +646,8 @@ __global__ void __launch_bounds__(THREADS) k_hist(Work wk, int level) {
         wk.ctl->n_buckets[p ^ 1] = 0;
         wk.ctl->n_chunks[p ^ 1] = 0;
     }
-    const int warp = threadIdx.x >> 5;
+    const int row = (threadIdx.x >> 5) % ROWS;
+    const int nd = 1 << wk.radix_bits;  // <= NB
     const uint32_t nch = wk.ctl->n_chunks[p];
     for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) {
         const Chunk ch = wk.chunks[p][c];
@@ -648,22 +655,22 @@ __global__ void __launch_bounds__(THREADS) k_hist(Work wk, int level) {
         const int r_eff = min(wk.radix_bits, b.h);
         const int shift = b.h - r_eff;
         const uint32_t mask = (1u << r_eff) - 1;
-        for (int i = threadIdx.x; i < WARPS * kBins; i += THREADS) sh[i] = 0;
+        for (int i = threadIdx.x; i < ROWS * NB; i += THREADS) sh[i] = 0;
         __syncthreads();
         K a = static_cast<K>(~K(0)), o = 0;
         const K *src = src_of<K>(wk, b.src);
         const bool vec_ok = b.src ? true : wk.keys_vec_ok;
         if (b.raw)
             hist_range<K, THREADS, true>(src, ch.start, ch.start + ch.len, vec_ok, shift, mask, wk.codec,
-                                         sh + warp * kBins, a, o);
+                                         sh + row * NB, a, o);
         else
             hist_range<K, THREADS, false>(src, ch.start, ch.start + ch.len, vec_ok, shift, mask, wk.codec,
-                                          sh + warp * kBins, a, o);
+                                          sh + row * NB, a, o);
         __syncthreads();
-        for (int d = threadIdx.x; d < kBins; d += THREADS) {
+        for (int d = threadIdx.x; d < nd; d += THREADS) {
             uint32_t sum = 0;
 #pragma unroll
-            for (int w = 0; w < WARPS; ++w) sum += sh[w * kBins + d];
+            for (int w = 0; w < ROWS; ++w) sum += sh[w * NB + d];
             wk.hist[static_cast<size_t>(d) * wk.max_chunks + c] = sum;
         }
         unsigned long long aa = a, oo = o;
@@ -710,7 +717,7 @@ __global__ void __launch_bounds__(THREADS) k_colscan(Work wk, int level) {
         if (in) {
             const uint32_t out = static_cast<uint32_t>(ex_global - seg0);
             col[c] = out;
-            if (last) wk.bucket_base[static_cast<size_t>(b) * kBins + d] = out + v;
+            if (last) wk.bucket_base[static_cast<size_t>(b) * wk.bins + d] = out + v;
         }
         if (threadIdx.x == THREADS - 1) sh_last = seg0;
         __syncthreads();
@@ -811,20 +818,22 @@ __device__ void emit_fill(const Work &wk, uint64_t start, uint64_t len, uint64_t
 }
 
 // Per bucket of this level: common-prefix test, digit bases, child classes.
+// Thread t takes digit page * THREADS + t; digits wider than 8 bits take
+// several pages, with the running digit base carried between them (a run of
+// merged small children ends at a page boundary).
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS) k_classify(Work wk, int level) {
-    static_assert(THREADS == kBins, "one thread per digit");
+    static_assert(THREADS == kBins, "one thread per digit of a page");
     __shared__ unsigned long long ta[THREADS / 32], to[THREADS / 32];
     __shared__ unsigned long long tmp64[THREADS / 32 + 1];
     __shared__ uint32_t tmp[THREADS / 32 + 1];
     __shared__ uint32_t sh_choff[THREADS], sh_slot[THREADS], sh_bases[2];
-    __shared__ unsigned long long sh_len[THREADS], sh_base[THREADS];
     __shared__ int itmp[THREADS / 32 + 1], sh_i2[THREADS];
     __shared__ uint32_t sh_u[THREADS], sh_u2[THREADS];
     const int p = level & 1, q = p ^ 1;
     if (wk.ctl->error) return;
     const uint32_t nb = wk.ctl->n_buckets[p];
-    const int d = threadIdx.x;
+    const int t = threadIdx.x;
     for (uint32_t i = blockIdx.x; i < nb; i += gridDim.x) {
         const Bucket b = wk.buckets[p][i];
         unsigned long long a = ~0ull, o = 0;
@@ -852,61 +861,65 @@ __global__ void __launch_bounds__(THREADS) k_classify(Work wk, int level) {
                                   sh_slot, sh_bases);
             continue;
         }
-        const unsigned long long tot =
-            static_cast<uint32_t>(d) <= mask ? wk.bucket_base[static_cast<size_t>(i) * kBins + d] : 0ull;
-        unsigned long long total;
-        const unsigned long long ex = block_exclusive_scan64<THREADS>(tot, tmp64, total);
-        const unsigned long long base = b.start + ex;
-        if (static_cast<uint32_t>(d) <= mask) wk.bucket_base[static_cast<size_t>(i) * kBins + d] = static_cast<uint32_t>(ex);
         if (threadIdx.x == 0) {
             wk.buckets[p][i].scatter = 1;
             atomicAdd(&wk.ctl->scatter_keys[level], static_cast<unsigned long long>(b.len));
         }
-        sh_len[d] = tot;
-        sh_base[d] = base;
         const int hc = shift;  // bits left in the children
         const int dst = wk.inplace ? 0 : b.src ^ 1;
-        const bool big = tot > wk.unit_cap;
-        // children with no bits left are constant: value = common prefix | digit
-        if (big && hc == 0) {
-            const unsigned long long hi_mask = b.h >= 64 ? 0ull : (~0ull << b.h);
-            emit_fill(wk, base, tot, (a & hi_mask) | static_cast<unsigned long long>(d));
-        }
-        emit_buckets<THREADS>(wk, q, big && hc > 0, base, tot, hc, dst, 0, tmp, sh_choff, sh_slot, sh_bases);
-        // Small children become finish units.  Children of at most
-        // merge_cap / 4 keys ("tiny") merge with their tiny neighbours: inside a
-        // run of adjacent tiny children (empty children do not break a run),
-        // child e joins group floor(P_e / merge_cap) of the run, P_e being the
-        // keys of the run before it, so a group holds < 1.25 * merge_cap keys.
-        {
+        const int pages = static_cast<int>((mask + THREADS) / THREADS);
+        unsigned long long carry = 0;  // keys of the digits of earlier pages
+        for (int pg = 0; pg < pages; ++pg) {
+            const uint32_t d = static_cast<uint32_t>(pg * THREADS + t);
+            const bool in = d <= mask;
+            uint32_t *bbase = wk.bucket_base + static_cast<size_t>(i) * wk.bins + d;
+            const unsigned long long tot = in ? *bbase : 0ull;
+            unsigned long long total;
+            const unsigned long long ex = carry + block_exclusive_scan64<THREADS>(tot, tmp64, total);
+            const unsigned long long base = b.start + ex;
+            if (in) *bbase = static_cast<uint32_t>(ex);
+            carry += total;
+            const bool big = tot > wk.unit_cap;
+            // children with no bits left are constant: value = common prefix | digit
+            if (big && hc == 0) {
+                const unsigned long long hi_mask = b.h >= 64 ? 0ull : (~0ull << b.h);
+                emit_fill(wk, base, tot, (a & hi_mask) | static_cast<unsigned long long>(d));
+            }
+            emit_buckets<THREADS>(wk, q, big && hc > 0, base, tot, hc, dst, 0, tmp, sh_choff, sh_slot, sh_bases);
+            // Small children become finish units.  Children of at most
+            // merge_cap / 4 keys ("tiny") merge with their tiny neighbours:
+            // inside a run of adjacent tiny children (empty children do not
+            // break a run), child e joins group floor(P_e / merge_cap) of the
+            // run, P_e being the keys of the run before it, so a group holds
+            // < 1.25 * merge_cap keys.
             const uint32_t len = static_cast<uint32_t>(tot);
             const bool small = tot > 0 && tot <= wk.unit_cap;
             const bool tiny = small && len <= wk.merge_cap / 4;
             const bool solid = tot > 0 && !tiny;  // breaks runs
             // latest solid child before e, latest tiny child before e
-            const int last_solid = block_inclusive_max<THREADS>(solid ? d : -1, itmp);
-            const int last_tiny_incl = block_inclusive_max<THREADS>(tiny ? d : -1, itmp);
-            sh_i2[d] = last_tiny_incl;
+            const int last_solid = block_inclusive_max<THREADS>(solid ? t : -1, itmp);
+            const int last_tiny_incl = block_inclusive_max<THREADS>(tiny ? t : -1, itmp);
+            sh_i2[t] = last_tiny_incl;
             __syncthreads();
-            const int prev_tiny = d > 0 ? sh_i2[d - 1] : -1;
+            const int prev_tiny = t > 0 ? sh_i2[t - 1] : -1;
             const bool run_start = tiny && (prev_tiny < 0 || prev_tiny < last_solid);
             uint32_t dummy;
             const uint32_t g_ex = block_exclusive_scan<THREADS>(tiny ? len : 0u, tmp, dummy);
-            sh_u[d] = g_ex;
-            const int rs_idx = block_inclusive_max<THREADS>(run_start ? d : -1, itmp);
+            sh_u[t] = g_ex;
+            const int rs_idx = block_inclusive_max<THREADS>(run_start ? t : -1, itmp);
             // (barriers inside the scans publish sh_u)
             const uint32_t pre = tiny ? g_ex - sh_u[rs_idx] : 0u;
             const uint32_t gid = pre / wk.merge_cap;
-            sh_u2[d] = gid;
+            sh_u2[t] = gid;
             __syncthreads();
             const bool head = tiny && (run_start || sh_u2[prev_tiny] != gid);
-            const int head_idx = block_inclusive_max<THREADS>(head ? d : -1, itmp);
-            sh_u[d] = 0;
+            const int head_idx = block_inclusive_max<THREADS>(head ? t : -1, itmp);
+            sh_u[t] = 0;
             __syncthreads();
             if (tiny) atomicAdd(&sh_u[head_idx], len);
             __syncthreads();
             const bool emit = (small && !tiny) || head;
-            const uint32_t ulen = head ? sh_u[d] : len;
+            const uint32_t ulen = head ? sh_u[t] : len;
             uint32_t n_emit;
             const uint32_t slot = block_exclusive_scan<THREADS>(emit ? 1u : 0u, tmp, n_emit);
             uint32_t keys_total;
@@ -927,8 +940,8 @@ __global__ void __launch_bounds__(THREADS) k_classify(Work wk, int level) {
                 un.pad[0] = un.pad[1] = 0;
                 wk.units[sh_bases[0] + slot] = un;
             }
+            __syncthreads();
         }
-        __syncthreads();
     }
 }
 
@@ -1026,29 +1039,34 @@ __device__ __forceinline__ void stage_keys(const K (&k)[ITEMS], uint32_t vmask, 
 // warp per run.  The whole chunk (CHUNK_TILES tiles) is staged before the
 // write-out, so runs are long and coalesced.  Every run's destination is
 // checked against the bucket before anything is written.
-template <typename K, int THREADS, int ITEMS, int CHUNK_TILES>
+//
+// NB digit slots (kBins, or kWideBins for digits of 9..11 bits): with NB >
+// THREADS each thread owns NB / THREADS consecutive digits in the per-chunk
+// bookkeeping.
+template <typename K, int THREADS, int ITEMS, int CHUNK_TILES, int NB>
 __host__ __device__ constexpr size_t scatter_pre_offset() {
-    return (sizeof(K) * THREADS * ITEMS * CHUNK_TILES + sizeof(unsigned long long) * kBins +
-            sizeof(uint32_t) * (3 * kBins + THREADS / 32 + 1) + 16 + 15) &
+    return (sizeof(K) * THREADS * ITEMS * CHUNK_TILES + sizeof(unsigned long long) * NB +
+            sizeof(uint32_t) * (NB + THREADS / 32 + 1) + 16 + 15) &
            ~size_t(15);
 }
 
-template <typename K, int THREADS, int ITEMS, int CHUNK_TILES>
+template <typename K, int THREADS, int ITEMS, int CHUNK_TILES, int NB>
 __global__ void __launch_bounds__(THREADS, 2) k_scatter(Work wk, int level) {
     using L = TileLoad<K, THREADS, ITEMS>;
+    using Pre = ScatterPre<NB>;
     constexpr int TILE = THREADS * ITEMS;
     constexpr int CAP = TILE * CHUNK_TILES;
     constexpr int V = L::V;
     constexpr int WARPS = THREADS / 32;
+    constexpr int DPT = NB > THREADS ? NB / THREADS : 1;  // digits per thread
+    static_assert(NB <= THREADS || NB % THREADS == 0, "whole digits per thread");
     K *sm_keys = reinterpret_cast<K *>(g_dyn_smem);
     unsigned long long *off = reinterpret_cast<unsigned long long *>(g_dyn_smem + sizeof(K) * CAP);
-    uint32_t *cur = reinterpret_cast<uint32_t *>(off + kBins);  // [kBins] staging cursors
-    uint32_t *sst = cur + kBins;                                 // [kBins] staging starts
-    uint32_t *scnt = sst + kBins;                                // [kBins] chunk counts
-    uint32_t *tmp = scnt + kBins;                                // [WARPS + 1]
+    uint32_t *cur = reinterpret_cast<uint32_t *>(off + NB);  // [NB] staging cursors
+    uint32_t *tmp = cur + NB;                                // [WARPS + 1]
     int *bad = reinterpret_cast<int *>(tmp + WARPS + 1);
-    constexpr size_t kPreOff = scatter_pre_offset<K, THREADS, ITEMS, CHUNK_TILES>();
-    ScatterPre *pre = reinterpret_cast<ScatterPre *>(g_dyn_smem + kPreOff);
+    constexpr size_t kPreOff = scatter_pre_offset<K, THREADS, ITEMS, CHUNK_TILES, NB>();
+    Pre *pre = reinterpret_cast<Pre *>(g_dyn_smem + kPreOff);
     const int p = level & 1;
     const int t = threadIdx.x;
     if (wk.ctl->error) return;
@@ -1058,27 +1076,30 @@ __global__ void __launch_bounds__(THREADS, 2) k_scatter(Work wk, int level) {
     // slots: stage 1 (needs only the chunk index) fetches the chunk records
     // and the chunk's prefix counts; stage 2 (needs the chunk's bucket) the
     // bucket and its digit bases.
+    // (digits >= 2^radix_bits are never read: their rows are not fetched)
+    const int nd = 1 << wk.radix_bits;
     auto stage1 = [&](uint32_t c, int slot) {
-        ScatterPre &P = pre[slot];
+        Pre &P = pre[slot];
         if (t == 0) {
             cp_async16(&P.ch, &wk.chunks[p][c]);
             if (c + 1 < nch) cp_async16(&P.chn, &wk.chunks[p][c + 1]);
             else P.chn.bucket = 0xffffffffu;
         }
-        if (t < kBins) {
-            cp_async4(&P.hc[t], &wk.hist[static_cast<size_t>(t) * wk.max_chunks + c]);
-            if (c + 1 < nch) cp_async4(&P.hn[t], &wk.hist[static_cast<size_t>(t) * wk.max_chunks + c + 1]);
+        for (int d = t; d < nd; d += THREADS) {
+            cp_async4(&P.hc[d], &wk.hist[static_cast<size_t>(d) * wk.max_chunks + c]);
+            if (c + 1 < nch) cp_async4(&P.hn[d], &wk.hist[static_cast<size_t>(d) * wk.max_chunks + c + 1]);
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
     auto stage2 = [&](int slot) {
-        ScatterPre &P = pre[slot];
+        Pre &P = pre[slot];
         const uint32_t bk = P.ch.bucket;
         if (t == 0) {
             cp_async16(&P.b, &wk.buckets[p][bk]);
             cp_async16(reinterpret_cast<char *>(&P.b) + 16, reinterpret_cast<const char *>(&wk.buckets[p][bk]) + 16);
         }
-        if (t < kBins) cp_async4(&P.bb[t], &wk.bucket_base[static_cast<size_t>(bk) * kBins + t]);
+        for (int d = t; d < nd; d += THREADS)
+            cp_async4(&P.bb[d], &wk.bucket_base[static_cast<size_t>(bk) * wk.bins + d]);
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
     if (blockIdx.x < nch) {
@@ -1097,7 +1118,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_scatter(Work wk, int level) {
             if (c1 < nch) stage2((it + 1) % 3);
             if (c2 < nch) stage1(c2, (it + 2) % 3);
         }
-        const ScatterPre &P = pre[it % 3];
+        const Pre &P = pre[it % 3];
         const Chunk ch = P.ch;
         const Bucket b = P.b;
         if (!b.scatter) continue;  // block-uniform
@@ -1108,31 +1129,42 @@ __global__ void __launch_bounds__(THREADS, 2) k_scatter(Work wk, int level) {
         const int shift = b.h - r_eff;
         const uint32_t mask = (1u << r_eff) - 1;
         const bool next_same = P.chn.bucket == ch.bucket;
-        // chunk digit counts and destinations
-        const int d = threadIdx.x;
-        uint32_t n_d = 0;
-        if (d < kBins && static_cast<uint32_t>(d) <= mask) {
-            const uint32_t ex = P.hc[d];
-            uint32_t ex_next;
-            if (next_same) {
-                ex_next = P.hn[d];
-            } else {  // last chunk of the bucket: the digit's bucket total
-                const uint32_t base_n = static_cast<uint32_t>(d) < mask ? P.bb[d + 1] : static_cast<uint32_t>(b.len);
-                ex_next = base_n - P.bb[d];
+        // chunk digit counts and destinations (thread t: digits t * DPT ..)
+        uint32_t n_d[DPT];
+        uint32_t n_sum = 0, n_max = 0;
+#pragma unroll
+        for (int e = 0; e < DPT; ++e) {
+            const int d = threadIdx.x * DPT + e;
+            n_d[e] = 0;
+            if (d < NB && static_cast<uint32_t>(d) <= mask) {
+                const uint32_t ex = P.hc[d];
+                uint32_t ex_next;
+                if (next_same) {
+                    ex_next = P.hn[d];
+                } else {  // last chunk of the bucket: the digit's bucket total
+                    const uint32_t base_n =
+                        static_cast<uint32_t>(d) < mask ? P.bb[d + 1] : static_cast<uint32_t>(b.len);
+                    ex_next = base_n - P.bb[d];
+                }
+                n_d[e] = ex_next - ex;
+                const unsigned long long o = b.start + P.bb[d] + ex;
+                off[d] = o;
+                if (n_d[e] && o + n_d[e] > b.start + b.len) *bad = 1;  // never write outside the bucket
             }
-            n_d = ex_next - ex;
-            const unsigned long long o = b.start + P.bb[d] + ex;
-            off[d] = o;
-            if (n_d && o + n_d > b.start + b.len) *bad = 1;  // never write outside the bucket
+            n_sum += n_d[e];
+            n_max = max(n_max, n_d[e]);
         }
         __syncthreads();
         uint32_t total;
-        const uint32_t st = block_exclusive_scan<THREADS>(n_d, tmp, total);
-        if (d < kBins) {
-            sst[d] = st;
-            cur[d] = st;
-            scnt[d] = n_d;
-            off[d] -= st;  // the key at staging slot q of digit d goes to off[d] + q (mod 2^64)
+        uint32_t st = block_exclusive_scan<THREADS>(n_sum, tmp, total);
+#pragma unroll
+        for (int e = 0; e < DPT; ++e) {
+            const int d = threadIdx.x * DPT + e;
+            if (d < NB) {
+                cur[d] = st;
+                off[d] -= st;  // the key at staging slot q of digit d goes to off[d] + q (mod 2^64)
+                st += n_d[e];
+            }
         }
         if (total != ch.len && threadIdx.x == 0) *bad = 1;
         __syncthreads();
@@ -1146,7 +1178,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_scatter(Work wk, int level) {
         // encoded, a whole aligned tile or a partial one, and -- from the
         // chunk's known counts -- whether warps often share one digit.
         const uint64_t cend = ch.start + ch.len;
-        const bool skew = block_reduce_max<THREADS>(n_d, tmp) * 8u > ch.len;
+        const bool skew = block_reduce_max<THREADS>(n_max, tmp) * 8u > ch.len;
         bool overflow = false;
         for (uint64_t pos = ch.start; pos < cend;) {
             const uint64_t wstart = pos - pos % V;
@@ -1191,9 +1223,9 @@ __global__ void __launch_bounds__(THREADS, 2) k_scatter(Work wk, int level) {
     }
 }
 
-template <typename K, int THREADS, int ITEMS, int CHUNK_TILES>
+template <typename K, int THREADS, int ITEMS, int CHUNK_TILES, int NB>
 constexpr size_t scatter_smem() {
-    return scatter_pre_offset<K, THREADS, ITEMS, CHUNK_TILES>() + 3 * sizeof(ScatterPre);
+    return scatter_pre_offset<K, THREADS, ITEMS, CHUNK_TILES, NB>() + 3 * sizeof(ScatterPre<NB>);
 }
 
 // Shared-memory layout of k_finish.  Two alternatives share the first region:
@@ -1650,7 +1682,7 @@ struct Cfg<uint64_t> {
 
 }  // namespace
 
-MsdShape msd_shape(int key_bytes, const Tuning &t) {
+MsdShape msd_shape(int key_bytes, const Tuning &t, bool inplace) {
     MsdShape s;
     uint32_t fin;
     if (key_bytes == 4) {
@@ -1661,8 +1693,10 @@ MsdShape msd_shape(int key_bytes, const Tuning &t) {
         fin = Cfg<uint64_t>::kFinThreads * Cfg<uint64_t>::kFinItems;
     }
     s.radix_bits = t.radix_bits ? t.radix_bits : kRadixBits;
+    if (inplace && s.radix_bits > kRadixBits) s.radix_bits = kRadixBits;  // the permutation's tables are 8-bit
+    s.bins = s.radix_bits > kRadixBits ? kWideBins : kBins;
     s.levels = (key_bytes * 8 + s.radix_bits - 1) / s.radix_bits;
-    s.chunk = 2 * s.tile;
+    s.chunk = (t.chunk_tiles ? t.chunk_tiles : kMaxChunkTiles) * s.tile;
     // a unit plus its misalignment fits one aligned finish window
     s.unit_cap = t.unit_keys ? static_cast<uint32_t>(t.unit_keys) : fin - 16;
     // tiny buckets (<= merge_cap / 4) group below 1.25 * merge_cap <= unit_cap
@@ -1672,7 +1706,8 @@ MsdShape msd_shape(int key_bytes, const Tuning &t) {
 
 bool tuning_valid(int key_bytes, const Tuning &t) {
     const MsdShape d = msd_shape(key_bytes);
-    if (t.radix_bits && (t.radix_bits < kMinRadixBits || t.radix_bits > kRadixBits)) return false;
+    if (t.radix_bits && (t.radix_bits < kMinRadixBits || t.radix_bits > kMaxRadixBits)) return false;
+    if (t.chunk_tiles < 0 || t.chunk_tiles > kMaxChunkTiles) return false;
     if (t.unit_keys && (t.unit_keys < 256 || static_cast<uint32_t>(t.unit_keys) > d.unit_cap)) return false;
     const uint32_t unit = t.unit_keys ? static_cast<uint32_t>(t.unit_keys) : d.unit_cap;
     if (t.merge_keys && (t.merge_keys < 64 || 5ull * static_cast<uint32_t>(t.merge_keys) > 4ull * unit)) return false;
@@ -1681,12 +1716,14 @@ bool tuning_valid(int key_bytes, const Tuning &t) {
 
 template <typename K>
 void msd_prepare() {
-    constexpr int T = Cfg<K>::kThreads, I = Cfg<K>::kItems;
+    constexpr int T = Cfg<K>::kThreads, I = Cfg<K>::kItems, CT = kMaxChunkTiles;
     constexpr int FT = Cfg<K>::kFinThreads, FI = Cfg<K>::kFinItems;
     ip_prepare<K>();
     static const bool attrs = [] {  // once per process; thread-safe static initialisation
-        cudaFuncSetAttribute(k_scatter<K, T, I, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(scatter_smem<K, T, I, 2>()));
+        cudaFuncSetAttribute(k_scatter<K, T, I, CT, kBins>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(scatter_smem<K, T, I, CT, kBins>()));
+        cudaFuncSetAttribute(k_scatter<K, T, I, CT, kWideBins>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(scatter_smem<K, T, I, CT, kWideBins>()));
         cudaFuncSetAttribute(k_finish<K, FT, FI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(finish_smem<K, FT, FI>()));
         cudaFuncSetAttribute(k_finish_lsd<K, FT, FI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1701,14 +1738,16 @@ template <typename K>
 void msd_levels_and_finish(const Work &wk, cudaStream_t st, Recorder &rec, int num_sms, bool levels) {
     constexpr int T = Cfg<K>::kThreads, I = Cfg<K>::kItems;
     constexpr int FT = Cfg<K>::kFinThreads, FI = Cfg<K>::kFinItems;
-    constexpr int CT = 2;  // tiles per chunk
+    constexpr int CT = kMaxChunkTiles;  // staging capacity in tiles (a chunk holds 1 or 2)
+    const bool wide = wk.bins > static_cast<uint32_t>(kBins);
     if (levels) {
         for (int level = 0; level < wk.stop_level; ++level) {
             rec.begin(BSORT_K_HIST, level);
-            k_hist<K, 512><<<num_sms * 4, 512, 0, st>>>(wk, level);
+            if (wide) k_hist<K, 512, kWideBins><<<num_sms * 4, 512, 0, st>>>(wk, level);
+            else k_hist<K, 512, kBins><<<num_sms * 4, 512, 0, st>>>(wk, level);
             rec.end();
             rec.begin(BSORT_K_SCAN, level);
-            k_colscan<1024><<<kBins, 1024, 0, st>>>(wk, level);
+            k_colscan<1024><<<1 << wk.radix_bits, 1024, 0, st>>>(wk, level);
             rec.end();
             rec.begin(BSORT_K_CLASSIFY, level);
             k_classify<kBins><<<num_sms * 4, kBins, 0, st>>>(wk, level);
@@ -1717,7 +1756,11 @@ void msd_levels_and_finish(const Work &wk, cudaStream_t st, Recorder &rec, int n
                 launch_ip_level<K>(wk, st, rec, num_sms, level);
             } else {
                 rec.begin(BSORT_K_SCATTER, level);
-                k_scatter<K, T, I, CT><<<num_sms * 2, T, scatter_smem<K, T, I, CT>(), st>>>(wk, level);
+                if (wide)
+                    k_scatter<K, T, I, CT, kWideBins>
+                        <<<num_sms * 2, T, scatter_smem<K, T, I, CT, kWideBins>(), st>>>(wk, level);
+                else
+                    k_scatter<K, T, I, CT, kBins><<<num_sms * 2, T, scatter_smem<K, T, I, CT, kBins>(), st>>>(wk, level);
                 rec.end();
             }
         }

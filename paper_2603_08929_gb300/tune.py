@@ -1,10 +1,13 @@
 """Autotuner of the MSD path: times candidate tunings (digit width, finish
-threshold, merge threshold) for a dtype and size on the current GPU and keeps
-the fastest per (dtype, size class) in a JSON table.  The tuning never changes
-a result, only the speed; `lookup` picks the entry of the nearest size class.
+threshold, merge threshold, chunk size in scatter tiles) for a dtype and size
+on the current GPU and keeps the fastest per (dtype, size class) in a JSON
+table; `autotune_segmented` does the same on a caller's segmented workload.
+The tuning never changes a result, only the speed; `lookup` picks the entry of
+the nearest size class.
 
 Table format: {"<dtype>": {"<log2 n>": {"radix_bits": r, "unit_keys": u,
-"merge_keys": m, "ms": t}}} -- zero fields mean the library default.
+"merge_keys": m, "chunk_tiles": c, "ms": t}}} -- zero fields mean the library
+default.
 """
 from __future__ import annotations
 
@@ -12,8 +15,12 @@ import json
 import math
 import os
 
-# digit width x finish threshold (0: default); merge threshold follows the finish threshold
-CANDIDATES = [{"radix_bits": r, "unit_keys": u, "merge_keys": 0} for r in (8, 7, 6, 5) for u in (0, 2048)]
+FIELDS = ("radix_bits", "unit_keys", "merge_keys", "chunk_tiles")
+
+# digit width x finish threshold (0: default) x chunk of 2 or 1 scatter tiles;
+# the merge threshold follows the finish threshold
+CANDIDATES = [{"radix_bits": r, "unit_keys": u, "merge_keys": 0, "chunk_tiles": c}
+              for r in (8, 11, 6, 4) for u in (0, 2048) for c in (0, 1)]
 
 
 def _random_keys(dtype: str, n: int, device):
@@ -57,6 +64,47 @@ def time_tuning(dtype: str, n: int, tuning: dict, steps: int = 3, device=None) -
     return times[len(times) // 2]
 
 
+def time_tuning_segmented(keys, offsets, tuning: dict, steps: int = 3) -> float:
+    """Median milliseconds of one segmented sort of `keys` (a CUDA tensor,
+    left unchanged) over `offsets` (int64 CUDA tensor, S + 1 entries) with
+    `tuning`."""
+    import torch
+    from . import Handle, bsort_keys_segmented, segmented_workspace_bytes
+    h = Handle()
+    h.set_tuning(keys.element_size(), tuning)
+    nseg = offsets.numel() - 1
+    ws = torch.empty(segmented_workspace_bytes(keys.numel(), nseg, keys.dtype, tuning=tuning),
+                     dtype=torch.uint8, device=keys.device)
+    stream = torch.cuda.current_stream()
+    times = []
+    for i in range(steps + 1):
+        y = keys.clone()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bsort_keys_segmented(y, offsets, stream=stream, handle=h, workspace=ws)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i:
+            times.append(e0.elapsed_time(e1))
+    if h.get_error(stream) != 0:
+        raise RuntimeError("device error word set while tuning")
+    times.sort()
+    return times[len(times) // 2]
+
+
+def autotune_segmented(keys, offsets, candidates=None, steps: int = 3, log: list = None) -> dict:
+    """The fastest candidate for this segmented workload, with its time in
+    "ms"; `log` (a list) receives every (candidate, ms)."""
+    best = None
+    for c in candidates or CANDIDATES:
+        ms = time_tuning_segmented(keys, offsets, c, steps)
+        if log is not None:
+            log.append((c, ms))
+        if best is None or ms < best["ms"]:
+            best = dict(c, ms=ms)
+    return best
+
+
 def autotune(dtype: str, n: int, candidates=None, steps: int = 3) -> dict:
     """The fastest candidate for (dtype, n), with its time in "ms"."""
     best = None
@@ -97,8 +145,8 @@ def lookup(table: dict, dtype: str, n: int) -> dict:
     """The tuning of the nearest size class of `dtype` (defaults if none)."""
     entries = table.get(dtype, {})
     if not entries:
-        return {"radix_bits": 0, "unit_keys": 0, "merge_keys": 0}
+        return {f: 0 for f in FIELDS}
     k = size_class(n)
     best = min(entries, key=lambda s: (abs(int(s) - k), int(s)))
     e = entries[best]
-    return {f: int(e.get(f, 0)) for f in ("radix_bits", "unit_keys", "merge_keys")}
+    return {f: int(e.get(f, 0)) for f in FIELDS}

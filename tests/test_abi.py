@@ -86,8 +86,10 @@ def test_more_argument_checks_without_a_gpu(lib):
     assert lib.bsort_handle_create(ctypes.byref(h)) == 0
     try:
         T = pkg._Tuning
-        bad = T(9, 0, 0, 0)
+        bad = T(12, 0, 0, 0)
         assert lib.bsort_handle_set_tuning(h, 4, ctypes.byref(bad)) == 1   # digit width out of range
+        assert lib.bsort_handle_set_tuning(h, 4, ctypes.byref(T(11, 0, 0, 3))) == 1  # chunk of 3 tiles
+        assert lib.bsort_handle_set_tuning(h, 4, ctypes.byref(T(11, 0, 0, 1))) == 0
         assert lib.bsort_handle_set_tuning(h, 3, None) == 1                 # key width
         assert lib.bsort_handle_set_tuning(h, 8, ctypes.byref(T(6, 1024, 128, 0))) == 0
         assert lib.bsort_handle_set_tuning(h, 8, None) == 0                 # back to defaults
