@@ -103,6 +103,8 @@ def _load():
         lib.orc_rank.restype = None
         lib.orc_multiset_digest.argtypes = [u64p, sz, u64p]
         lib.orc_multiset_digest.restype = None
+        lib.orc_stable_argsort.argtypes = [u64p, sz, i, i, i, i, i, u64p]
+        lib.orc_stable_argsort.restype = i
         _lib = lib
     return _lib
 
@@ -193,3 +195,22 @@ def multiset_digest(x: np.ndarray) -> tuple:
     out = np.zeros(4, dtype=np.uint64)
     _load().orc_multiset_digest(_ptr(words), words.size, _ptr(out))
     return tuple(int(v) for v in out)
+
+
+def stable_argsort_words(words: np.ndarray, fmt: KeyFormat, descending: bool = False) -> np.ndarray:
+    """Input positions in the order of a stable sort of raw words by the
+    definition order (equal keys keep input order)."""
+    words = np.ascontiguousarray(words, dtype=np.uint64)
+    perm = np.zeros(words.size, dtype=np.uint64)
+    st = _load().orc_stable_argsort(_ptr(words), words.size, fmt.w, fmt.kind, fmt.e, fmt.f,
+                                    0 if descending else 1, _ptr(perm))
+    if st != 0:
+        raise ValueError("oracle rejected the input (status %d)" % st)
+    return perm.astype(np.int64)
+
+
+def stable_argsort(x: np.ndarray, descending: bool = False) -> np.ndarray:
+    """Key-value sorting by definition: the permutation (int64 positions) a
+    stable sort of ``x`` under the paper's order applies; ``x[p]`` is the
+    sorted keys and ``v[p]`` the values carried along."""
+    return stable_argsort_words(to_words(x), FORMATS[np.dtype(x.dtype)], descending)

@@ -28,6 +28,11 @@
  * reach -- numeric order, -0 < +0, NaNs at the two ends ordered by their
  * mantissa field -- without using the bit partition, so the two can pin
  * each other.
+ *
+ * Key-value sorting (not in the paper) is defined here by its plain meaning:
+ * `orc_stable_argsort` orders the input positions by the definition order of
+ * their keys, equal keys (bit-identical) in input order -- a stable sort, so
+ * the permutation is unique and values carried along it are fixed.
  */
 #include <stdint.h>
 #include <stddef.h>
@@ -427,4 +432,44 @@ void orc_multiset_digest(const uint64_t *a, size_t n, uint64_t *out4)
         x3 ^= mix_a(a[i] + 0x9e3779b97f4a7c15ULL);
     }
     out4[0] = s1; out4[1] = s2; out4[2] = x3; out4[3] = (uint64_t)n;
+}
+
+/* Stable argsort by the definition order: perm[k] = input position of the
+ * k-th element of the ordered sequence, elements that compare equal in
+ * input order.  A bottom-up merge sort of the positions (stable because a
+ * merge takes from the left run on ties). */
+int orc_stable_argsort(const uint64_t *a, size_t n, int w, int kind, int e_bits, int f_bits, int asc,
+                       uint64_t *perm)
+{
+    int st = check_format(w, kind, e_bits, f_bits);
+    if (st != ORC_OK) return st;
+    st = check_bits(a, n, w);
+    if (st != ORC_OK) return st;
+    uint64_t *tmp = (uint64_t *)malloc((n ? n : 1) * sizeof(uint64_t));
+    if (!tmp) return ORC_ERR_MEM;
+    for (size_t i = 0; i < n; i++) perm[i] = i;
+    uint64_t *src = perm, *dst = tmp;
+    for (size_t width = 1; width < n; width *= 2) {
+        for (size_t lo = 0; lo < n; lo += 2 * width) {
+            size_t mid = lo + width < n ? lo + width : n;
+            size_t hi = lo + 2 * width < n ? lo + 2 * width : n;
+            size_t i = lo, j = mid, k = lo;
+            while (i < mid && j < hi) {
+                int r = orc_cmp_total(a[src[i]], a[src[j]], w, kind, e_bits, f_bits);
+                if (!asc) r = -r;
+#if ORC_PLANT == 8
+                int take_left = r < 0; /* planted: ties go right first */
+#else
+                int take_left = r <= 0;
+#endif
+                dst[k++] = take_left ? src[i++] : src[j++];
+            }
+            while (i < mid) dst[k++] = src[i++];
+            while (j < hi) dst[k++] = src[j++];
+        }
+        uint64_t *t = src; src = dst; dst = t;
+    }
+    if (src != perm) memcpy(perm, src, n * sizeof(uint64_t));
+    free(tmp);
+    return ORC_OK;
 }

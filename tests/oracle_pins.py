@@ -7,6 +7,7 @@ requires each bug to trip at least one pin.
 """
 from __future__ import annotations
 
+import functools
 import itertools
 import os
 import random
@@ -297,6 +298,55 @@ def pin_idempotent_and_modes_agree():
         a = O.bsort(x)
         assert np.array_equal(O.bsort(a).view(ut), a.view(ut))
         assert np.array_equal(O.bsort(x, mode=O.STABLE).view(ut), a.view(ut))
+
+
+# --- key-value sorting: the stable permutation -------------------------------
+
+def _py_stable_perm(xs, fmt, asc):
+    """Stable order of positions by py_order_key (the exact-rational
+    restatement), equal keys by position."""
+    keys = [py_order_key(v, fmt) for v in xs]
+
+    def cmp(i, j):
+        if keys[i] != keys[j]:
+            return (-1 if keys[i] < keys[j] else 1) * (1 if asc else -1)
+        return (i > j) - (i < j)
+    return sorted(range(len(xs)), key=functools.cmp_to_key(cmp))
+
+
+def pin_stable_argsort_tiny():
+    """Tiny inputs full of ties in every kind of format: the oracle's stable
+    permutation equals the independent restatement's."""
+    rnd = random.Random(4321)
+    fmts = [O.KeyFormat(3, O.UNSIGNED), O.KeyFormat(4, O.SIGNED), O.KeyFormat(6, O.SIGNED),
+            O.KeyFormat(6, O.FLOAT, 3, 2), O.KeyFormat(5, O.FLOAT, 2, 2), O.KeyFormat(8, O.FLOAT, 4, 3)]
+    for fmt in fmts:
+        for trial in range(60):
+            n = rnd.randint(0, 12)
+            pool = [rnd.randrange(1 << fmt.w) for _ in range(rnd.randint(1, 4))]
+            xs = [rnd.choice(pool) if rnd.random() < 0.7 else rnd.randrange(1 << fmt.w) for _ in range(n)]
+            for asc in (True, False):
+                got = O.stable_argsort_words(np.array(xs, dtype=np.uint64), fmt, not asc).tolist()
+                assert got == _py_stable_perm(xs, fmt, asc), (fmt, xs, asc, got)
+
+
+def pin_stable_argsort_machine_types():
+    """Every machine type, many ties: the permutation is one, the keys it
+    gathers are the (pinned) sorted keys, and identical keys keep their input
+    order."""
+    rng = np.random.default_rng(9)
+    for dt in O.FORMATS:
+        ut = {8: np.uint8, 16: np.uint16, 32: np.uint32, 64: np.uint64}[dt.itemsize * 8]
+        pool = rng.integers(0, np.iinfo(ut).max, size=24, dtype=ut, endpoint=True)
+        x = np.where(rng.random(5000) < 0.8, rng.choice(pool, 5000),
+                     rng.integers(0, np.iinfo(ut).max, size=5000, dtype=ut, endpoint=True)).astype(ut).view(dt)
+        for desc in (False, True):
+            p = O.stable_argsort(x, desc)
+            assert np.array_equal(np.sort(p), np.arange(x.size))
+            assert np.array_equal(x[p].view(ut), O.bsort(x, desc).view(ut)), dt
+            w = O.to_words(x)[p]
+            same = w[1:] == w[:-1]
+            assert np.all(p[1:][same] > p[:-1][same]), "ties out of input order (%s)" % dt
 
 
 ALL_PINS = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]

@@ -22,6 +22,7 @@ PLANTS = {
     5: "negative NaNs ordered by ascending payload",
     6: "subnormal exponent off by one",
     7: "stable split reverses the back side",
+    8: "stable argsort takes ties from the right run",
 }
 
 
