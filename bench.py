@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="bsort", choices=["bsort", "reference"])
-    ap.add_argument("--mode", default="plain", choices=["plain", "segmented", "serve"],
+    ap.add_argument("--mode", default="plain", choices=["plain", "segmented", "serve", "pairs"],
                     help="plain: one 2^log2n array; segmented: the batched workload (see run_segmented)")
     ap.add_argument("--segments", type=int, default=10000, help="segments per dtype (segmented mode)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -68,9 +68,12 @@ def parse():
     ap.add_argument("--desc", action="store_true")
     ap.add_argument("--inplace", action="store_true", help="in-place mode (no alternate buffer); reports aux bytes")
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--radix-bits", type=int, default=0, help="plain mode: MSD digit width 4..11 (0: default 8)")
-    ap.add_argument("--unit-keys", type=int, default=0, help="plain mode: shared-memory finish threshold (0: default)")
-    ap.add_argument("--chunk-tiles", type=int, default=0, help="plain mode: chunk of 1 or 2 scatter tiles (0: 2)")
+    ap.add_argument("--value-dtype", default="int32", help="pairs mode: dtype of the values ('none': argsort only)")
+    ap.add_argument("--radix-bits", type=int, default=0,
+                    help="plain / pairs mode: MSD digit width 4..11 (0: default 8; pairs: of the packed-word sort)")
+    ap.add_argument("--unit-keys", type=int, default=0,
+                    help="plain / pairs mode: shared-memory finish threshold (0: default)")
+    ap.add_argument("--chunk-tiles", type=int, default=0, help="plain / pairs mode: chunk of 1 or 2 scatter tiles (0: 2)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample-log2", type=int, default=23)
@@ -448,6 +451,74 @@ def run_serve(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_pairs_mode(args, rank, world):
+    """Stable key-value sort of 2^log2n keys of --dtype (--dist) with
+    --value-dtype values (or, with 'none', the int64 positions: an argsort).
+    Each step restores keys and values from pristine copies (untimed) and
+    times one bsort_pairs_ws call with CUDA events."""
+    import torch
+    import paper_2603_08929_gb300 as bs
+    from paper_2603_08929_gb300 import build as B
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    B.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n = 1 << args.log2n
+    x = torch.from_numpy(W.make(args.dist, args.dtype, n, seed=args.seed + rank)).to(dev)
+    argsort = args.value_dtype == "none"
+    v0 = None if argsort else torch.from_numpy(W.make("uniform", args.value_dtype, n, seed=args.seed + 1)).to(dev)
+    keys = torch.empty_like(x)
+    vals = None if argsort else torch.empty_like(v0)
+    idx = torch.empty(n, dtype=torch.int64, device=dev) if argsort else None
+    tuning8 = {"radix_bits": args.radix_bits, "unit_keys": args.unit_keys, "chunk_tiles": args.chunk_tiles}
+    tuning8 = tuning8 if any(tuning8.values()) else None
+    ws = torch.empty(bs.pairs_workspace_bytes(n, args.dtype, tuning8=tuning8), dtype=torch.uint8, device=dev)
+    h = bs.Handle()
+    if tuning8:
+        h.set_tuning(8, tuning8)
+    stream = torch.cuda.current_stream()
+    times = []
+    for i in range(args.warmup + args.steps):
+        keys.copy_(x)
+        if vals is not None:
+            vals.copy_(v0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bs.bsort_pairs_ws(h, keys, ws, values=vals, indices=idx, descending=args.desc, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            times.append(e0.elapsed_time(e1))
+    if h.get_error(stream) != 0:
+        raise RuntimeError("device error word set in the key-value sort")
+    ms = sum(times) / len(times)
+    signed_ok = args.dtype in ("int8", "int16", "int32", "int64", "uint8")  # torch compares these on the device
+    ok = (bool(torch.all(keys[1:] <= keys[:-1]).item()) if args.desc else
+          bool(torch.all(keys[1:] >= keys[:-1]).item())) if signed_ok else None
+    esize = x.element_size()
+    vsize = 8 if argsort else v0.element_size()
+    peak, peak_src = load_peaks()
+    floor_bytes = n * (2 * esize + (vsize if argsort else 2 * vsize))  # read keys (+values), write keys + values/positions
+    line = {
+        "metric": METRIC, "value": n / (ms * 1e-3) / 1e9, "unit": "Gpairs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": DTYPE_TAG.get(args.dtype, args.dtype), "data": "synthetic",
+        "config": {"workload": "stable key-value sort, %s %s keys, 2^%d, %s, %s" % (
+            args.dtype, args.dist, args.log2n, "argsort (int64 positions)" if argsort else
+            "%s values" % args.value_dtype, "descending" if args.desc else "ascending"),
+            "n": n, "l2": "inputs > L2 at this size; restored from pristine copies before each step (untimed)",
+            "tuning_of_the_word_sort": tuning8 or "library defaults"},
+        "gpu_launches": h.launch_count(),
+        "min_bytes_frac": floor_bytes / (ms * 1e-3) / 1e9 / peak,
+        "min_bytes_note": "bytes any key-value sort must move (read keys%s, write keys and %s) / time / %s HBM "
+                          "copy bandwidth" % ("" if argsort else " and values", "positions" if argsort else "values",
+                                              peak_src),
+        "sorted_check": ok,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -459,6 +530,9 @@ def main():
         return
     if args.mode == "serve":
         run_serve(args, rank, world)
+        return
+    if args.mode == "pairs":
+        run_pairs_mode(args, rank, world)
         return
     import torch
     import paper_2603_08929_gb300 as bs

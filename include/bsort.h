@@ -200,6 +200,35 @@ bsort_status bsort_last_aux_bytes(bsort_handle *handle, size_t *bytes);
  */
 bsort_status bsort_keys_host(void *host_keys, size_t n, bsort_dtype dt, int descending, void *stream);
 
+/* ---- key-value sorting ----------------------------------------------------
+ *
+ * Stable key-value sort (the paper sorts keys only; here equal keys -- they
+ * are bit-identical -- keep their input order, ascending and descending
+ * alike, so the permutation is unique).  keys: n keys of dtype dt (device),
+ * sorted in place exactly as bsort_keys sorts them; values: NULL, or n
+ * device elements of value_bytes (1, 2, 4 or 8) bytes, any content, permuted
+ * in place along with their keys; indices: NULL, or n device int64 outputs,
+ * the input position of each output element (an argsort).  keys, values and
+ * indices must not overlap each other or the workspace.  n < 2^32 (else
+ * BSORT_ERR_UNSUPPORTED); pointers aligned to their element size
+ * (BSORT_ERR_MISALIGNED); workspace: bsort_pairs_workspace_bytes, 256-byte
+ * aligned, owned by the caller.  Asynchronous on `stream`; device-side
+ * failures land in the handle's error word (bsort_get_error).
+ * Method: each key's order-preserving code (high 32 bits) and its input
+ * position (low 32 bits) form one 64-bit word; the words are distinct, so the
+ * 8-byte MSD sort of the words is the stable order.  8-byte keys take two
+ * such sorts, on the low and then the high half of their code (LSD over the
+ * halves).  Values (and 8-byte keys) follow by one gather.  The handle's
+ * tuning for 8-byte keys applies to these sorts; a tuned handle needs the
+ * workspace of bsort_pairs_workspace_bytes_tuned with that tuning (NULL:
+ * defaults).
+ */
+bsort_status bsort_pairs_workspace_bytes(size_t n, bsort_dtype dt, size_t *bytes);
+bsort_status bsort_pairs_workspace_bytes_tuned(size_t n, bsort_dtype dt, const bsort_tuning *tuning8, size_t *bytes);
+bsort_status bsort_pairs_ws(bsort_handle *handle, void *keys, void *values, size_t value_bytes, int64_t *indices,
+                            size_t n, bsort_dtype dt, int descending, void *workspace, size_t ws_bytes,
+                            void *stream);
+
 /* ---- segmented and graph forms -------------------------------------------
  *
  * Segmented sort: the segments [d_offsets[s], d_offsets[s+1]), s <

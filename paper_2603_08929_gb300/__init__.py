@@ -118,6 +118,12 @@ def lib():
         L.bsort_segmented_workspace_bytes.restype = i
         L.bsort_segmented_workspace_bytes_tuned.argtypes = [sz, sz, i, ctypes.POINTER(_Tuning), ctypes.POINTER(sz)]
         L.bsort_segmented_workspace_bytes_tuned.restype = i
+        L.bsort_pairs_workspace_bytes.argtypes = [sz, i, ctypes.POINTER(sz)]
+        L.bsort_pairs_workspace_bytes.restype = i
+        L.bsort_pairs_workspace_bytes_tuned.argtypes = [sz, i, ctypes.POINTER(_Tuning), ctypes.POINTER(sz)]
+        L.bsort_pairs_workspace_bytes_tuned.restype = i
+        L.bsort_pairs_ws.argtypes = [vp, vp, vp, sz, vp, sz, i, i, vp, sz, vp]
+        L.bsort_pairs_ws.restype = i
         L.bsort_keys_segmented_ws.argtypes = [vp, vp, sz, vp, sz, i, i, vp, sz, vp]
         L.bsort_keys_segmented_ws.restype = i
         L.bsort_keys_segmented.argtypes = [vp, sz, vp, sz, i, i, vp]
@@ -312,6 +318,70 @@ def bsort_keys_ws(handle: Handle, keys, workspace, descending: bool = False, str
                                ctypes.c_void_p(workspace.data_ptr()),
                                workspace.numel() * workspace.element_size(), _stream_ptr(stream)),
            "bsort_keys_ws")
+
+
+def pairs_workspace_bytes(n: int, dtype, tuning8: dict = None) -> int:
+    """Workspace bytes of a key-value sort of n keys (``tuning8``: the
+    handle's tuning for 8-byte keys, which the sort of the packed words uses)."""
+    out = ctypes.c_size_t(0)
+    if tuning8 is None:
+        _check(lib().bsort_pairs_workspace_bytes(int(n), _dtype_code(dtype), ctypes.byref(out)),
+               "bsort_pairs_workspace_bytes")
+    else:
+        _check(lib().bsort_pairs_workspace_bytes_tuned(int(n), _dtype_code(dtype), _tuning(tuning8),
+                                                       ctypes.byref(out)), "bsort_pairs_workspace_bytes_tuned")
+    return int(out.value)
+
+
+def bsort_pairs_ws(handle: Handle, keys, workspace, values=None, indices=None, descending: bool = False,
+                   stream=None) -> None:
+    """Stable key-value sort (C ABI ``bsort_pairs_ws``): ``keys`` sorted in
+    place, ``values`` (None or a CUDA tensor of as many 1-, 2-, 4- or 8-byte
+    elements) permuted in place with them, ``indices`` (None or an int64 CUDA
+    tensor of as many elements) set to the input position of each output
+    element.  Equal keys keep their input order."""
+    _device_tensor(keys)
+    _device_tensor(workspace)
+    n = keys.numel()
+    vptr, vbytes = None, 0
+    if values is not None:
+        _device_tensor(values)
+        if values.numel() != n:
+            raise ValueError("values must have as many elements as keys")
+        vptr, vbytes = ctypes.c_void_p(values.data_ptr()), values.element_size()
+    iptr = None
+    if indices is not None:
+        _device_tensor(indices)
+        if indices.numel() != n or str(indices.dtype) != "torch.int64":
+            raise ValueError("indices must be an int64 tensor with as many elements as keys")
+        iptr = ctypes.c_void_p(indices.data_ptr())
+    _check(lib().bsort_pairs_ws(handle.ptr, ctypes.c_void_p(keys.data_ptr()), vptr, vbytes, iptr, n,
+                                _dtype_code(keys.dtype), int(bool(descending)), ctypes.c_void_p(workspace.data_ptr()),
+                                workspace.numel() * workspace.element_size(), _stream_ptr(stream)),
+           "bsort_pairs_ws")
+
+
+_pairs_handle = None
+
+
+def sort_pairs_(keys, values=None, descending: bool = False, return_indices: bool = False, stream=None):
+    """Stable key-value sort in place with a workspace allocated by torch for
+    the call.  Returns (keys, values, indices), indices an int64 tensor of
+    input positions when ``return_indices`` (else None)."""
+    import torch
+    global _pairs_handle
+    if _pairs_handle is None:
+        _pairs_handle = Handle()
+    ws = torch.empty(max(1, pairs_workspace_bytes(keys.numel(), keys.dtype)), dtype=torch.uint8, device=keys.device)
+    idx = torch.empty(keys.numel(), dtype=torch.int64, device=keys.device) if return_indices else None
+    bsort_pairs_ws(_pairs_handle, keys, ws, values=values, indices=idx, descending=descending, stream=stream)
+    return keys, values, idx
+
+
+def argsort(keys, descending: bool = False, stream=None):
+    """Stable argsort of a CUDA tensor: the int64 input positions in sorted
+    order.  ``keys`` is left unchanged (a copy of it is sorted)."""
+    return sort_pairs_(keys.clone(), descending=descending, return_indices=True, stream=stream)[2]
 
 
 def bsort_keys_noalloc(keys, descending: bool = False, stream=None) -> None:

@@ -18,7 +18,8 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libbsort.so")
 
-SOURCES = ["api.cu", "kernels_msd.cu", "kernels_inplace.cu", "kernels_count.cu", "noalloc.cu", "serve.cu"]
+SOURCES = ["api.cu", "kernels_msd.cu", "kernels_inplace.cu", "kernels_count.cu", "kernels_pairs.cu", "noalloc.cu",
+           "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

@@ -377,6 +377,32 @@ size_t workspace_for(size_t n, const DtypeInfo &di, bool inplace = false, const 
     return di.bytes <= 2 ? count_layout(n, di.bytes).total : msd_layout(n, di.bytes, 0, inplace, tune).total;
 }
 
+// Key-value sorting workspace: the 64-bit words, the first sort's
+// permutation (8-byte keys), the final input positions, then an 8-byte MSD
+// workspace whose alternate buffer (its first n * 8 bytes) doubles as the
+// gather target afterwards, and one error word.
+struct PairsLayout {
+    size_t words, perm, idx, err, inner, inner_bytes, total;
+};
+
+PairsLayout pairs_layout(size_t n, int key_bytes, const Tuning &tune8) {
+    PairsLayout L;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = off;
+        off = align_up(off + bytes);
+        return at;
+    };
+    L.words = take(8 * n);
+    L.perm = take(key_bytes == 8 ? 4 * n : 0);
+    L.idx = take(4 * n);
+    L.err = take(4);
+    L.inner = off;
+    L.inner_bytes = msd_layout(n, 8, 0, false, tune8).total;
+    L.total = L.inner + L.inner_bytes;
+    return L;
+}
+
 bool to_tuning(const bsort_tuning *in, int key_bytes, Tuning *out) {
     Tuning t;
     if (in) {
@@ -456,6 +482,96 @@ bsort_status bsort_keys_ws(bsort_handle *handle, void *keys, size_t n, bsort_dty
     std::lock_guard<std::mutex> lk(handle->mu);
     return run_sort(handle, keys, n, di, descending, workspace, ws_bytes, static_cast<cudaStream_t>(stream),
                     mode == BSORT_MODE_INPLACE);
+}
+
+bsort_status bsort_pairs_workspace_bytes(size_t n, bsort_dtype dt, size_t *bytes) {
+    DtypeInfo di;
+    if (!bytes || !dtype_info(dt, &di)) return BSORT_ERR_INVALID_ARG;
+    *bytes = pairs_layout(n, di.bytes, Tuning()).total;
+    return BSORT_OK;
+}
+
+bsort_status bsort_pairs_workspace_bytes_tuned(size_t n, bsort_dtype dt, const bsort_tuning *tuning8, size_t *bytes) {
+    DtypeInfo di;
+    if (!bytes || !dtype_info(dt, &di)) return BSORT_ERR_INVALID_ARG;
+    Tuning t;
+    if (!to_tuning(tuning8, 8, &t)) return BSORT_ERR_INVALID_ARG;
+    *bytes = pairs_layout(n, di.bytes, t).total;
+    return BSORT_OK;
+}
+
+bsort_status bsort_pairs_ws(bsort_handle *handle, void *keys, void *values, size_t value_bytes, int64_t *indices,
+                            size_t n, bsort_dtype dt, int descending, void *workspace, size_t ws_bytes,
+                            void *stream) {
+    if (!handle) return BSORT_ERR_INVALID_ARG;
+    DtypeInfo di;
+    if (!dtype_info(dt, &di)) return BSORT_ERR_INVALID_ARG;
+    if (values && value_bytes != 1 && value_bytes != 2 && value_bytes != 4 && value_bytes != 8)
+        return BSORT_ERR_INVALID_ARG;
+    if (n >= (1ull << 32)) return BSORT_ERR_UNSUPPORTED;  // positions travel in 32 bits
+    if (n == 0) return BSORT_OK;
+    if (!keys) return BSORT_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(keys) % di.bytes || (values && reinterpret_cast<uintptr_t>(values) % value_bytes) ||
+        reinterpret_cast<uintptr_t>(indices) % 8)
+        return BSORT_ERR_MISALIGNED;
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::lock_guard<std::mutex> lk(handle->mu);
+    if (n == 1) {  // one element: position 0, nothing moves
+        handle->rec.launches = 0;
+        if (indices && cudaMemsetAsync(indices, 0, 8, st) != cudaSuccess) return BSORT_ERR_CUDA;
+        return BSORT_OK;
+    }
+    if (!workspace) return BSORT_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(workspace) % kAlign) return BSORT_ERR_MISALIGNED;
+    const PairsLayout L = pairs_layout(n, di.bytes, handle->tune[1]);
+    if (ws_bytes < L.total) return BSORT_ERR_WORKSPACE_TOO_SMALL;
+    (void)cudaGetLastError();
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return BSORT_ERR_CUDA;
+    const int sms = num_sms_of(dev);
+    char *ws = static_cast<char *>(workspace);
+    uint64_t *words = reinterpret_cast<uint64_t *>(ws + L.words);
+    uint32_t *perm = di.bytes == 8 ? reinterpret_cast<uint32_t *>(ws + L.perm) : nullptr;
+    uint32_t *idx = reinterpret_cast<uint32_t *>(ws + L.idx);
+    uint32_t *err = reinterpret_cast<uint32_t *>(ws + L.err);
+    char *inner = ws + L.inner;
+    void *tmp = inner;  // the inner sort's alternate buffer, free once the sorts are done
+    const Codec codec = codec_for(di, descending);
+    DtypeInfo word_info;
+    dtype_info(BSORT_U64, &word_info);
+    int launches = 0;
+    if (cudaMemsetAsync(err, 0, 4, st) != cudaSuccess) return BSORT_ERR_CUDA;
+    launch_pairs_pack(keys, di.bytes, n, codec, 0, nullptr, words, err, st, sms);
+    ++launches;
+    bsort_status s = run_sort(handle, words, n, word_info, 0, inner, L.inner_bytes, st);
+    launches += handle->rec.launches;
+    if (s != BSORT_OK) return s;
+    if (di.bytes == 8) {
+        launch_pairs_perm(words, n, perm, handle->last_ctl, err, st, sms);
+        launch_pairs_pack(keys, 8, n, codec, 1, perm, words, err, st, sms);
+        launches += 2;
+        s = run_sort(handle, words, n, word_info, 0, inner, L.inner_bytes, st);
+        launches += handle->rec.launches;
+        if (s != BSORT_OK) return s;
+    }
+    Ctl *ctl = handle->last_ctl;
+    const bool gathers = values || di.bytes == 8;  // positions kept only for the gathers
+    launch_pairs_index(words, perm, n, di.bytes <= 4 ? keys : nullptr, di.bytes, codec, gathers ? idx : nullptr,
+                       indices, ctl, err, st, sms);
+    ++launches;
+    if (di.bytes == 8) {  // keys by their positions, then back into the caller's buffer
+        launch_gather(keys, 8, idx, n, tmp, ctl, st, sms);
+        ++launches;
+        if (cudaMemcpyAsync(keys, tmp, 8 * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return BSORT_ERR_CUDA;
+    }
+    if (values) {
+        launch_gather(values, static_cast<int>(value_bytes), idx, n, tmp, ctl, st, sms);
+        ++launches;
+        if (cudaMemcpyAsync(values, tmp, value_bytes * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return BSORT_ERR_CUDA;
+    }
+    handle->rec.launches = launches;
+    return cudaGetLastError() == cudaSuccess ? BSORT_OK : BSORT_ERR_CUDA;
 }
 
 bsort_status bsort_keys(void *keys, size_t n, bsort_dtype dt, int descending, void *stream) {

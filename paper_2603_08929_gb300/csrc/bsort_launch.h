@@ -91,6 +91,19 @@ void launch_msd_segmented(const Work &wk, const uint64_t *d_offsets, uint32_t ns
 template <typename K>
 void msd_prepare();
 
+// Key-value sorting: the pieces around the 8-byte sort of (code << 32 |
+// position) words.  Each launches one kernel.  `err` is a device word that
+// survives the sorts' control-block resets; k_pairs_index folds it into `ctl`.
+void launch_pairs_pack(const void *keys, int key_bytes, uint64_t n, const Codec &codec, int part,
+                       const uint32_t *perm, uint64_t *words, uint32_t *err, cudaStream_t st, int num_sms);
+void launch_pairs_perm(const uint64_t *words, uint64_t n, uint32_t *perm, const Ctl *ctl, uint32_t *err,
+                       cudaStream_t st, int num_sms);
+void launch_pairs_index(const uint64_t *words, const uint32_t *perm, uint64_t n, void *keys, int key_bytes,
+                        const Codec &codec, uint32_t *idx, int64_t *indices, Ctl *ctl, const uint32_t *err,
+                        cudaStream_t st, int num_sms);
+void launch_gather(const void *src, int elem_bytes, const uint32_t *idx, uint64_t n, void *dst, Ctl *ctl,
+                   cudaStream_t st, int num_sms);
+
 // In-place mode: one level's digit permutation inside the caller's buffer
 // (replaces the ping-pong scatter of that level).
 constexpr int kIpBlockBytes = 128;                 // block of the permutation

@@ -117,3 +117,36 @@ def test_more_argument_checks_without_a_gpu(lib):
     assert lib.bsort_server_create(ctypes.byref(C(2, 0, 1 << 30, 1 << 20, 1 << 16, 0, 0)), ctypes.byref(srv)) == 1
     assert lib.bsort_server_create(ctypes.byref(C(2, 1, 1 << 30, 1 << 20, 1 << 16, 5, 0)), ctypes.byref(srv)) == 1
     assert lib.bsort_server_submit(None, None, 0, 6, 0, 0) == 1
+
+
+def test_pairs_argument_checks_without_a_gpu(lib):
+    """Key-value sorting validates everything before any CUDA call."""
+    import paper_2603_08929_gb300 as pkg
+    h = ctypes.c_void_p()
+    assert lib.bsort_handle_create(ctypes.byref(h)) == 0
+    try:
+        k, v, ix = ctypes.c_void_p(0x1000), ctypes.c_void_p(0x2000), ctypes.c_void_p(0x3000)
+        ws = ctypes.c_void_p(0x100000)
+        big = 1 << 30
+        assert lib.bsort_pairs_ws(None, k, v, 4, ix, 10, 6, 0, ws, big, None) == 1      # no handle
+        assert lib.bsort_pairs_ws(h, k, v, 4, ix, 10, 42, 0, ws, big, None) == 1        # bad dtype
+        assert lib.bsort_pairs_ws(h, k, v, 3, ix, 10, 6, 0, ws, big, None) == 1         # 3-byte values
+        assert lib.bsort_pairs_ws(h, k, v, 4, ix, 1 << 32, 6, 0, ws, big, None) == 2    # positions need 32 bits
+        assert lib.bsort_pairs_ws(h, None, v, 4, ix, 0, 6, 0, None, 0, None) == 0       # n == 0
+        assert lib.bsort_pairs_ws(h, k, None, 0, None, 1, 6, 0, None, 0, None) == 0     # n == 1, nothing to write
+        assert lib.bsort_pairs_ws(h, None, v, 4, ix, 10, 6, 0, ws, big, None) == 1      # NULL keys
+        assert lib.bsort_pairs_ws(h, ctypes.c_void_p(0x1002), v, 4, ix, 10, 6, 0, ws, big, None) == 3
+        assert lib.bsort_pairs_ws(h, k, ctypes.c_void_p(0x2004), 8, ix, 10, 6, 0, ws, big, None) == 3
+        assert lib.bsort_pairs_ws(h, k, v, 4, ctypes.c_void_p(0x3004), 10, 6, 0, ws, big, None) == 3
+        assert lib.bsort_pairs_ws(h, k, v, 4, ix, 10, 6, 0, None, big, None) == 1       # no workspace
+        assert lib.bsort_pairs_ws(h, k, v, 4, ix, 10, 6, 0, ctypes.c_void_p(0x100010), big, None) == 3
+        need = pkg.pairs_workspace_bytes(10, "int32")
+        assert lib.bsort_pairs_ws(h, k, v, 4, ix, 10, 6, 0, ws, need - 1, None) == 5
+    finally:
+        lib.bsort_handle_destroy(h)
+    # 8-byte keys keep the first sort's permutation as well; a wider digit grows the inner sort
+    n = 1 << 20
+    assert pkg.pairs_workspace_bytes(n, "float64") > pkg.pairs_workspace_bytes(n, "float32")
+    assert pkg.pairs_workspace_bytes(n, "uint8") == pkg.pairs_workspace_bytes(n, "int32")
+    assert pkg.pairs_workspace_bytes(n, "int32", tuning8={"radix_bits": 11}) > pkg.pairs_workspace_bytes(n, "int32")
+    assert pkg.pairs_workspace_bytes(n, "int32", tuning8={}) == pkg.pairs_workspace_bytes(n, "int32")

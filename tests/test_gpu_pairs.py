@@ -1,0 +1,165 @@
+"""Key-value sorting through the C ABI: the sorted keys, the values carried
+along and the returned positions equal the oracle's stable permutation bit
+for bit; at large sizes, the properties that make a permutation the stable
+sorting one."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from gpu_util import assert_bit_exact, par_first_unsorted, to_device
+
+pytestmark = pytest.mark.gpu
+
+DTYPES = ["uint8", "int8", "uint16", "int16", "float16", "uint32", "int32", "float32", "uint64", "int64", "float64"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    from paper_2603_08929_gb300 import build as b
+    b.build()
+    torch.cuda.set_device(0)
+
+
+def run_pairs(x, values=None, desc=False, indices=True, tuning8=None):
+    import torch
+    import paper_2603_08929_gb300 as bs
+    k = to_device(x)
+    v = to_device(values) if values is not None else None
+    h = bs.Handle()
+    if tuning8:
+        h.set_tuning(8, tuning8)
+    ws = torch.empty(max(1, bs.pairs_workspace_bytes(k.numel(), k.dtype, tuning8=tuning8)), dtype=torch.uint8,
+                     device="cuda")
+    ix = torch.empty(k.numel(), dtype=torch.int64, device="cuda") if indices else None
+    bs.bsort_pairs_ws(h, k, ws, values=v, indices=ix, descending=desc)
+    assert h.get_error() == 0
+    return (k.cpu().numpy(), v.cpu().numpy() if v is not None else None,
+            ix.cpu().numpy() if ix is not None else None, h)
+
+
+def check(x, vals, desc, got):
+    k, v, ix, _ = got
+    p = O.stable_argsort(x, desc)
+    assert_bit_exact(k, x[p], "keys")
+    if vals is not None:
+        assert_bit_exact(v, vals[p], "values")
+    if ix is not None:
+        assert np.array_equal(ix, p), "positions differ from the stable permutation"
+
+
+def _dists(dtype):
+    base = ["uniform", "distinct8", "zipf", "sorted", "reverse"]
+    return base + (["float_edge"] if dtype.startswith("float") else [])
+
+
+@pytest.mark.parametrize("desc", [False, True], ids=["asc", "desc"])
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_pairs_parity(dtype, desc):
+    n = 100003
+    for j, dist in enumerate(_dists(dtype)):
+        x = W.make(dist, dtype, n, seed=40 + j)
+        vals = (np.arange(n, dtype=np.int64) * 7919 + 3).astype(np.int32)
+        check(x, vals, desc, run_pairs(x, vals, desc))
+
+
+@pytest.mark.parametrize("n", [2, 3, 17, 5000, 300001, (1 << 22) + 5])
+@pytest.mark.parametrize("dtype", ["int32", "float64", "uint16"])
+def test_pairs_sizes(dtype, n):
+    x = W.make("distinct8" if n % 2 else "uniform", dtype, n, seed=n % 101)
+    vals = W.make("uniform", "float64", n, seed=7)
+    check(x, vals, n % 3 == 0, run_pairs(x, vals, n % 3 == 0))
+
+
+def test_pairs_tiny_and_empty():
+    import torch
+    import paper_2603_08929_gb300 as bs
+    h = bs.Handle()
+    ws = torch.empty(256, dtype=torch.uint8, device="cuda")
+    k = torch.empty(0, dtype=torch.int32, device="cuda")
+    bs.bsort_pairs_ws(h, k, ws, values=torch.empty(0, dtype=torch.int32, device="cuda"),
+                      indices=torch.empty(0, dtype=torch.int64, device="cuda"))
+    k = torch.tensor([5], dtype=torch.int32, device="cuda")
+    ix = torch.full((1,), 99, dtype=torch.int64, device="cuda")
+    bs.bsort_pairs_ws(h, k, ws, values=torch.tensor([7.0], device="cuda"), indices=ix)
+    assert ix.item() == 0 and k.item() == 5
+
+
+@pytest.mark.parametrize("vdtype", ["uint8", "int16", "float32", "int64"])
+def test_pairs_value_widths(vdtype):
+    n = 70001
+    x = W.make("zipf", "int32", n, seed=3)
+    vals = W.make("uniform", vdtype, n, seed=4)
+    check(x, vals, False, run_pairs(x, vals, False))
+
+
+def test_pairs_without_indices_or_values():
+    n = 50001
+    x = W.make("distinct8", "float32", n, seed=5)
+    vals = W.make("uniform", "int64", n, seed=6)
+    check(x, vals, True, run_pairs(x, vals, True, indices=False))
+    check(x, None, False, run_pairs(x, None, False, indices=True))
+    k, _, _, _ = run_pairs(x, None, False, indices=False)
+    assert_bit_exact(k, O.bsort(x), "keys only")
+
+
+@pytest.mark.parametrize("tuning8", [{"radix_bits": 11}, {"radix_bits": 6, "chunk_tiles": 1}], ids=["r11", "r6c1"])
+def test_pairs_tuned_handle(tuning8):
+    n = 300007
+    for dtype in ("int32", "float64"):
+        x = W.make("distinct8", dtype, n, seed=8)
+        vals = np.arange(n, dtype=np.int32)
+        check(x, vals, False, run_pairs(x, vals, False, tuning8=tuning8))
+
+
+def test_pairs_launch_counts():
+    """Key-value sorting launches its own pack / index / gather kernels plus
+    one (4-byte keys) or two (8-byte keys) sorts of the packed words."""
+    import torch
+    import paper_2603_08929_gb300 as bs
+    n = 1 << 20
+    h = bs.Handle()
+    w = torch.zeros(n, dtype=torch.int64, device="cuda")  # same launch sequence as the 8-byte packed words
+    ws = torch.empty(bs.workspace_bytes(n, "int64"), dtype=torch.uint8, device="cuda")
+    bs.bsort_keys_ws(h, w, ws)
+    c = h.launch_count()
+    for dtype, want in (("int32", c + 3), ("float64", 2 * c + 6)):
+        x = W.make("uniform", dtype, n, seed=9)
+        _, _, _, hp = run_pairs(x, np.arange(n, dtype=np.int32), False)
+        assert hp.launch_count() == want, (dtype, hp.launch_count(), want)
+
+
+def test_python_helpers():
+    import torch
+    import paper_2603_08929_gb300 as bs
+    x = W.make("distinct8", "int64", 123457, seed=10)
+    t = to_device(x)
+    ix = bs.argsort(t, descending=True)
+    assert np.array_equal(ix.cpu().numpy(), O.stable_argsort(x, True))
+    assert_bit_exact(t.cpu().numpy(), x, "argsort leaves its input unchanged")
+    vals = torch.arange(x.size, dtype=torch.float32, device="cuda")
+    k, v, i = bs.sort_pairs_(t, vals, return_indices=True)
+    p = O.stable_argsort(x)
+    assert_bit_exact(k.cpu().numpy(), x[p], "sort_pairs_ keys")
+    assert np.array_equal(v.cpu().numpy(), p.astype(np.float32)) and np.array_equal(i.cpu().numpy(), p)
+
+
+@pytest.mark.parametrize("dtype,log2n", [("int32", 27), ("float64", 26)])
+def test_pairs_large_properties(dtype, log2n):
+    """At 2^27 / 2^26 keys, tie-heavy: the positions form a permutation, the
+    keys they gather are the output keys, the output is monotone under the
+    oracle's order, and ties are in input order -- together the stable
+    sorting permutation, uniquely."""
+    n = 1 << log2n
+    x = W.make("distinct8", dtype, n, seed=11)
+    k, _, ix, _ = run_pairs(x, None, False)
+    assert ix.min() >= 0 and ix.max() < n
+    seen = np.zeros(n, dtype=bool)
+    seen[ix] = True
+    assert seen.all(), "positions are not a permutation"
+    assert_bit_exact(k, x[ix], "keys gathered by the positions")
+    assert par_first_unsorted(k, False) == -1
+    kw = k.view({4: np.uint32, 8: np.uint64}[k.dtype.itemsize])
+    same = kw[1:] == kw[:-1]
+    assert np.all(ix[1:][same] > ix[:-1][same]), "ties out of input order"
