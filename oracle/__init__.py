@@ -54,6 +54,10 @@ FORMATS = {
 
 _UINT_OF_WIDTH = {8: np.uint8, 16: np.uint16, 32: np.uint32, 64: np.uint64}
 
+# bfloat16 (the high half of a binary32), which numpy has no dtype for: its
+# keys travel as uint16 bit patterns with this format passed explicitly.
+BF16 = KeyFormat(16, FLOAT, 8, 7)
+
 
 def _compile(out_path: str, plant: int = 0) -> None:
     tmp = out_path + ".tmp%d" % os.getpid()

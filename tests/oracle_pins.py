@@ -300,6 +300,40 @@ def pin_idempotent_and_modes_agree():
         assert np.array_equal(O.bsort(x, mode=O.STABLE).view(ut), a.view(ut))
 
 
+# --- bfloat16 ------------------------------------------------------------------
+
+def pin_bf16_values_are_binary32_high_halves():
+    """Every finite bfloat16 pattern's value, by the oracle's comparator
+    arithmetic, is the binary32 value of the pattern shifted into the high
+    half (numpy's conversion, exact)."""
+    b = np.arange(1 << 16, dtype=np.uint32)
+    f32 = (b << 16).view(np.float32)
+    for bits in b[((b >> 7) & 0xFF) != 0xFF].tolist():
+        assert O.float_value(bits, O.BF16) == float(f32[bits]), hex(bits)
+
+
+def pin_bf16_exhaustive_order():
+    """All 2^16 bfloat16 patterns: the oracle's sort (both modes, both
+    directions) equals the exact-rational restatement's order, and on the
+    non-NaN patterns numpy's numeric order of the binary32 values with -0
+    before +0."""
+    words = np.arange(1 << 16, dtype=np.uint64)
+    want = sorted(words.tolist(), key=lambda v: py_order_key(v, O.BF16))
+    for mode in (O.LITERAL, O.STABLE):
+        a = words[::-1].copy()
+        O.bsort_words(a, O.BF16, False, mode)
+        assert a.tolist() == want
+        d = words.copy()
+        O.bsort_words(d, O.BF16, True, mode)
+        assert d.tolist() == want[::-1]
+    nonnan = [v for v in want if not (((v >> 7) & 0xFF) == 0xFF and (v & 0x7F))]
+    f = (np.array(nonnan, dtype=np.uint32) << 16).view(np.float32)
+    assert np.all(f[1:] >= f[:-1])
+    sign = np.array(nonnan, dtype=np.uint32) >> 15
+    zeros = np.flatnonzero(f == 0)
+    assert sign[zeros].tolist() == [1, 0]
+
+
 # --- key-value sorting: the stable permutation -------------------------------
 
 def _py_stable_perm(xs, fmt, asc):

@@ -23,7 +23,7 @@ def test_counter_based_slices():
 def test_deterministic_and_typed(dtype, dist):
     a = W.make(dist, dtype, 5000, seed=3)
     b = W.make(dist, dtype, 5000, seed=3)
-    assert a.dtype == np.dtype(dtype) and a.size == 5000
+    assert a.dtype == (np.dtype(np.uint16) if dtype == "bfloat16" else np.dtype(dtype)) and a.size == 5000
     assert np.array_equal(a.view(np.uint8), b.view(np.uint8))
 
 
@@ -46,3 +46,17 @@ def test_segment_sizes_log_uniform():
     s = W.segment_sizes(0, 20000, 20)
     assert s.min() >= 1 and s.max() <= 1 << 20
     assert abs(np.log2(s).mean() - 10) < 0.3
+
+
+def test_bf16_inputs():
+    """bfloat16 comes as uint16 patterns: normal values round to nearest even
+    from binary32, the edge mix has its NaN / inf / subnormal shares."""
+    x = W.make("normal", "bfloat16", 100000, seed=1)
+    f = (x.astype(np.uint32) << 16).view(np.float32)
+    assert np.all(np.isfinite(f)) and 600 < np.std(f) < 1400
+    e = W.make("float_edge", "bfloat16", 200000, seed=2).astype(np.uint32)
+    exp, man = (e >> 7) & 0xFF, e & 0x7F
+    assert 0.03 < ((exp == 0xFF) & (man != 0)).mean() < 0.05
+    assert 0.015 < ((exp == 0xFF) & (man == 0)).mean() < 0.025
+    assert 0.015 < ((exp == 0) & (man != 0)).mean() < 0.025
+    assert W._bf16_bits(np.array([1.0, -2.5, 1.00390625, 1.01171875])).tolist() == [0x3F80, 0xC020, 0x3F80, 0x3F82]

@@ -42,7 +42,7 @@ _M1 = np.uint64(0xBF58476D1CE4E5B9)
 _M2 = np.uint64(0x94D049BB133111EB)
 
 DTYPES = ["uint8", "int8", "uint16", "int16", "float16", "uint32", "int32", "float32",
-          "uint64", "int64", "float64"]
+          "uint64", "int64", "float64", "bfloat16"]
 DISTS = ["uniform", "zipf", "normal", "distinct8", "sorted", "reverse", "float_edge", "normal01"]
 
 _UINT = {1: np.uint8, 2: np.uint16, 4: np.uint32, 8: np.uint64}
@@ -154,8 +154,39 @@ def _distinct_patterns(seed, stream, k, dtype):
     return got[:k].astype(_bits_dtype(dtype))
 
 
+def _bf16_bits(x: np.ndarray) -> np.ndarray:
+    """bfloat16 patterns of finite doubles: to binary32, then the high half
+    rounded to nearest, ties to even."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = (u + np.uint64(0x7FFF) + ((u >> np.uint64(16)) & np.uint64(1))) >> np.uint64(16)
+    return r.astype(np.uint16)
+
+
+def _make_bf16(dist: str, n: int, seed: int) -> np.ndarray:
+    """bfloat16 inputs as uint16 bit patterns (numpy has no bfloat16 dtype);
+    the same distributions as the other float types."""
+    name, u16 = "bfloat16", np.dtype(np.uint16)
+    if dist == "uniform":
+        return _uniform_patterns(seed, stream_id(dist, name), n, u16)
+    if dist in ("sorted", "reverse"):
+        x = _uniform_patterns(seed, stream_id("uniform", name), n, u16)
+        x = x[np.argsort((x.astype(np.uint32) << np.uint32(16)).view(np.float32), kind="stable")]
+        return x if dist == "sorted" else x[::-1].copy()
+    if dist in ("normal", "normal01"):
+        return _bf16_bits(normal(seed, stream_id(dist, name), n, 0.0, 1e3 if dist == "normal" else 1.0))
+    if dist in ("distinct8", "zipf"):
+        return make(dist, np.uint16, n, seed + 0x5BF16)
+    if dist == "float_edge":
+        return _float_edge_bits(seed, n, name, 8, 7, np.uint16,
+                                lambda: _bf16_bits(normal(seed, stream_id("float_edge", name, 0), n, 0.0, 1e3)))
+    raise ValueError("unknown distribution %r" % dist)
+
+
 def make(dist: str, dtype, n: int, seed: int = 0) -> np.ndarray:
-    """One input array of ``n`` keys; identical for identical arguments."""
+    """One input array of ``n`` keys; identical for identical arguments.
+    ``dtype`` "bfloat16" gives uint16 bit patterns."""
+    if str(dtype) == "bfloat16":
+        return _make_bf16(dist, n, seed)
     dtype = np.dtype(dtype)
     name = dtype.name
     if dist == "uniform":
@@ -197,9 +228,18 @@ def _float_edge(seed: int, n: int, dtype: np.dtype) -> np.ndarray:
     name = dtype.name
     w = dtype.itemsize * 8
     f_bits = {16: 10, 32: 23, 64: 52}[w]
-    e_bits = w - 1 - f_bits
     ut = _bits_dtype(dtype)
-    out = _round_to(normal(seed, stream_id("float_edge", name, 0), n, 0.0, 1e3), dtype).view(ut).copy()
+    normal_bits = lambda: _round_to(normal(seed, stream_id("float_edge", name, 0), n, 0.0, 1e3),  # noqa: E731
+                                    dtype).view(ut).copy()
+    return _float_edge_bits(seed, n, name, w - 1 - f_bits, f_bits, ut, normal_bits).view(dtype)
+
+
+def _float_edge_bits(seed: int, n: int, name: str, e_bits: int, f_bits: int, ut, normal_bits) -> np.ndarray:
+    """Bit patterns of the float edge mix (format with e_bits / f_bits, bits
+    type ut): 90% normal(0, 1e3) from normal_bits(), 2% +-0, 2% subnormal, 2%
+    +-inf, 4% NaN (half quiet, half signalling, random payloads and signs)."""
+    w = 1 + e_bits + f_bits
+    out = normal_bits()
     cat = uniform01(seed, stream_id("float_edge", name, 1), n)
     r = words(seed, stream_id("float_edge", name, 2), 0, n)
     sign = ((r >> np.uint64(63)) & np.uint64(1)).astype(ut) << ut(w - 1)
@@ -223,7 +263,7 @@ def _float_edge(seed: int, n: int, dtype: np.dtype) -> np.ndarray:
     out[qn] = sign[qn] | exp_all | quiet | rest[qn]
     rest_nz = np.where(rest == 0, ut(1), rest)
     out[sn] = sign[sn] | exp_all | rest_nz[sn]
-    return out.view(dtype)
+    return out
 
 
 def segment_sizes(seed: int, count: int, max_log2: int = 20, min_size: int = 1,
