@@ -53,7 +53,8 @@ typedef enum {
     BSORT_F32 = 7,
     BSORT_U64 = 8,
     BSORT_I64 = 9,
-    BSORT_F64 = 10
+    BSORT_F64 = 10,
+    BSORT_BF16 = 11  /* bfloat16: 1 sign, 8 exponent, 7 mantissa bits (the high half of a binary32) */
 } bsort_dtype;
 
 typedef enum {

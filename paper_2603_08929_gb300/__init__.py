@@ -27,7 +27,7 @@ MODE_PINGPONG, MODE_INPLACE = 0, 1
 
 # bsort_dtype codes, in the order of include/bsort.h
 DTYPES = ["uint8", "int8", "uint16", "int16", "float16", "uint32", "int32", "float32",
-          "uint64", "int64", "float64"]
+          "uint64", "int64", "float64", "bfloat16"]
 _CODE = {name: i for i, name in enumerate(DTYPES)}
 
 KERNEL_KINDS = ["init", "hist", "scan", "classify", "scatter", "finish", "fill",

@@ -20,10 +20,12 @@ struct DtypeInfo {
 };
 
 bool dtype_info(bsort_dtype dt, DtypeInfo *out) {
+    // bfloat16 takes the binary16 codec: the transform depends only on the
+    // width and the kind (sign-magnitude), not on the exponent/mantissa split
     static const DtypeInfo table[] = {{1, 0}, {1, 1}, {2, 0}, {2, 1}, {2, 2}, {4, 0},
-                                      {4, 1}, {4, 2}, {8, 0}, {8, 1}, {8, 2}};
+                                      {4, 1}, {4, 2}, {8, 0}, {8, 1}, {8, 2}, {2, 2}};
     const int i = static_cast<int>(dt);
-    if (i < 0 || i > 10) return false;
+    if (i < 0 || i > 11) return false;
     *out = table[i];
     return true;
 }

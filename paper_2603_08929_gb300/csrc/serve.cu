@@ -34,9 +34,9 @@ uint64_t now_ns() {
 }
 
 int key_bytes(bsort_dtype dt) {
-    static const int b[] = {1, 1, 2, 2, 2, 4, 4, 4, 8, 8, 8};
+    static const int b[] = {1, 1, 2, 2, 2, 4, 4, 4, 8, 8, 8, 2};
     const int i = static_cast<int>(dt);
-    return i >= 0 && i <= 10 ? b[i] : 0;
+    return i >= 0 && i <= 11 ? b[i] : 0;
 }
 
 struct Request {
@@ -182,7 +182,7 @@ bsort_status bsort_server_create(const bsort_server_config *cfg, bsort_server **
     cudaGetDevice(&s->device);
     // workspace of the widest request any dtype can make
     size_t ws = 0;
-    for (int dt = 0; dt <= 10; ++dt) {
+    for (int dt = 0; dt <= 11; ++dt) {
         size_t b = 0;
         if (bsort_workspace_bytes(cfg->max_request_keys, static_cast<bsort_dtype>(dt),
                                   static_cast<bsort_mode>(cfg->mode), &b) ==
