@@ -42,7 +42,7 @@ METRIC = "Gkeys/s & % HBM roofline per dtype at 2^28 keys; batched vs plain; ser
 UNIT = "Gkeys/s"
 DTYPE_TAG = {"uint8": "u8", "int8": "i8", "uint16": "u16", "int16": "i16", "float16": "f16",
              "uint32": "u32", "int32": "i32", "float32": "f32", "uint64": "u64", "int64": "i64",
-             "float64": "f64"}
+             "float64": "f64", "bfloat16": "bf16"}
 
 
 def parse():
@@ -556,6 +556,8 @@ def main():
     esize = x.dtype.itemsize
     total_steps = args.warmup + args.steps
     base = torch.from_numpy(x).to(dev)
+    if args.dtype == "bfloat16":  # the generator gives bfloat16 as uint16 bit patterns
+        base = base.view(torch.bfloat16)
     bufs = [base.clone() for _ in range(total_steps)]
     del base
     mode = bs.MODE_INPLACE if args.inplace else bs.MODE_PINGPONG

@@ -129,8 +129,9 @@ bsort_status bsort_keys_ws(bsort_handle *handle, void *keys, size_t n, bsort_dty
  * Runtime tuning of the MSD path of a handle (used by bsort_keys_ws on that
  * handle), per key width (key_bytes 4 or 8); 1- and 2-byte keys take the
  * counting path and have nothing to tune.  Zero fields keep the defaults:
- *   radix_bits  digit width of the MSD levels, 4..11 (default 8): r binary
- *               partitions of Alg. 1 fused per pass; ceil(w / r) levels.
+ *   radix_bits  digit width of the MSD levels, 1..11 (default 8): r binary
+ *               partitions of Alg. 1 fused per pass; ceil(w / r) levels
+ *               (r = 1: one partition per bit, as the paper's recursion).
  *               Widths above 8 use 2048-entry digit tables; the in-place
  *               mode runs widths above 8 as 8;
  *   unit_keys   largest bucket the shared-memory finish takes, 256..default

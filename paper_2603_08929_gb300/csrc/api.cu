@@ -3,6 +3,7 @@
 // keys).  Every step of the sort runs in the library's own kernels.
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <new>
@@ -140,7 +141,7 @@ uint32_t grid16_for(size_t n) {
 }
 
 struct CountLayout {
-    size_t hist, starts, partial, total;
+    size_t hist, rstart, rval, nruns, btot, bnnz, partial, total;
 };
 
 CountLayout count_layout(size_t n, int key_bytes) {
@@ -149,8 +150,16 @@ CountLayout count_layout(size_t n, int key_bytes) {
     size_t off = 0;
     L.hist = off;
     off = align_up(off + bins * 8);
-    L.starts = off;
+    L.rstart = off;
     off = align_up(off + (bins + 1) * 8);
+    L.rval = off;
+    off = align_up(off + bins * 4);
+    L.nruns = off;
+    off = align_up(off + 4);
+    L.btot = off;
+    off = align_up(off + 256 * 8);
+    L.bnnz = off;
+    off = align_up(off + 256 * 4);
     L.partial = off;
     if (key_bytes == 2) off = align_up(off + static_cast<size_t>(grid16_for(n)) * 65536 * 4);
     L.total = off;
@@ -291,9 +300,14 @@ bsort_status run_sort(bsort_handle *h, void *keys, size_t n, const DtypeInfo &di
         cw.n = n;
         cw.codec = codec;
         cw.hist = reinterpret_cast<unsigned long long *>(ws + L.hist);
-        cw.starts = reinterpret_cast<unsigned long long *>(ws + L.starts);
+        cw.rstart = reinterpret_cast<unsigned long long *>(ws + L.rstart);
+        cw.rval = reinterpret_cast<uint32_t *>(ws + L.rval);
+        cw.nruns = reinterpret_cast<uint32_t *>(ws + L.nruns);
+        cw.btot = reinterpret_cast<unsigned long long *>(ws + L.btot);
+        cw.bnnz = reinterpret_cast<uint32_t *>(ws + L.bnnz);
         cw.partial = reinterpret_cast<uint32_t *>(ws + L.partial);
-        cw.grid16 = grid16_for(n);
+        // one wave: at most one 128 KB-shared-memory CTA per SM (the partials are sized for grid16_for(n))
+        cw.grid16 = std::min<uint32_t>(grid16_for(n), static_cast<uint32_t>(sms));
         if (di.bytes == 1) launch_count8(cw, st, h->rec, sms);
         else launch_count16(cw, st, h->rec, sms);
         h->last_path = 1;

@@ -19,10 +19,10 @@ namespace bsort {
 
 constexpr int kRadixBits = 8;              // default digit width of the MSD levels
 constexpr int kBins = 1 << kRadixBits;     // digits of an 8-bit pass (narrow tables, LSD finish passes)
-constexpr int kMinRadixBits = 4;           // narrowest tunable digit width
+constexpr int kMinRadixBits = 1;           // narrowest tunable digit width (1: one bit partition per pass)
 constexpr int kMaxRadixBits = 11;          // widest tunable digit width (ping-pong levels)
 constexpr int kWideBins = 1 << kMaxRadixBits;  // table stride of the digit widths above kRadixBits
-constexpr int kMaxLevels = 16;             // ceil(64 / kMinRadixBits)
+constexpr int kMaxLevels = 64;             // ceil(64 / kMinRadixBits)
 
 // device error word bits
 constexpr uint32_t kErrCapacity = 1u;

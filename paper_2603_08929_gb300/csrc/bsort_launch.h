@@ -62,8 +62,9 @@ struct MsdShape {
 // Most tiles per chunk (the scatter stages a whole chunk in shared memory).
 constexpr int kMaxChunkTiles = 2;
 
-// Runtime tuning of the MSD path (0 fields: defaults).  Digit width 4..11
-// bits (the in-place mode caps it at 8); finish threshold between 256 keys
+// Runtime tuning of the MSD path (0 fields: defaults).  Digit width 1..11
+// bits (the in-place mode caps it at 8; 1 is the paper's one partition per
+// bit, kept for measuring what fusing bits saves); finish threshold between 256 keys
 // and the compile-time tile; merge threshold between 64 keys and the finish
 // threshold; chunk of 1 or 2 scatter tiles.
 struct Tuning {
@@ -124,9 +125,13 @@ struct CountWork {
     uint64_t n;
     Codec codec;
     unsigned long long *hist;     // [bins] global counts
-    unsigned long long *starts;   // [bins + 1] exclusive starts
+    unsigned long long *rstart;   // [bins + 1] output start of each nonempty bin's run, then n
+    uint32_t *rval;               // [bins] the nonempty bins, ascending
+    uint32_t *nruns;              // number of nonempty bins
+    unsigned long long *btot;     // 16-bit: [256] keys of each group of 256 bins
+    uint32_t *bnnz;               // 16-bit: [256] nonempty bins of each group
     uint32_t *partial;            // 16-bit: [grid][65536] per-CTA counts
-    uint32_t grid16;              // CTAs of the 16-bit histogram
+    uint32_t grid16;              // CTAs of the 16-bit histogram (at most one per SM)
 };
 
 void launch_count8(const CountWork &cw, cudaStream_t st, Recorder &rec, int num_sms);

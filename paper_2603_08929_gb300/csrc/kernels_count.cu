@@ -11,9 +11,10 @@
 //                 per CTA, one CTA per SM); a half that wraps is carried into
 //                 a global correction word, so counts stay exact at any skew
 //   count_reduce  sums the per-CTA 16-bit partials
-//   count_scan    exclusive bin starts
+//   count_runs    the nonempty bins in ascending order with their output
+//                 starts (256 bins per CTA)
 //   count_fill    position-driven fill: each CTA owns an output span, finds
-//                 the bins overlapping it and writes the decoded values
+//                 the runs overlapping it and writes the decoded values
 #include "bsort_launch.h"
 
 namespace bsort {
@@ -28,7 +29,7 @@ constexpr int kHist16Threads = 1024;
 constexpr int kFillThreads = 256;
 constexpr int kFillPerThread = 32;  // consecutive output keys per thread
 constexpr int kFillSpan = kFillThreads * kFillPerThread;
-constexpr int kFillWindow = 4096;   // bin starts staged in shared memory
+constexpr int kFillWindow = 2048;   // run starts and values staged in shared memory
 
 __global__ void __launch_bounds__(kHist8Threads) k_count_hist8(const uint8_t *keys, uint64_t n, Codec codec,
                                                                unsigned long long *hist) {
@@ -118,11 +119,9 @@ __global__ void __launch_bounds__(kHist16Threads) k_count_hist16(const uint16_t 
     const uint64_t m0 = b0 + head;
     const uint64_t nvec = (b1 - m0) / 8;
     const uint4 *vec = reinterpret_cast<const uint4 *>(s + m0);
-    const uint64_t rounds = (nvec + kHist16Threads - 1) / kHist16Threads;
-    for (uint64_t r = 0; r < rounds; ++r) {
-        const uint64_t v = r * kHist16Threads + threadIdx.x;
-        const bool valid = v < nvec;
-        const uint4 q = valid ? vec[v] : make_uint4(0, 0, 0, 0);
+    // eight keys of one 16-byte vector (valid: the vector is in range); a
+    // warp whose 32 vectors hold one repeated key adds 256 with one atomic
+    auto count_vec = [&](const uint4 q, bool valid) {
         const uint32_t words[4] = {q.x, q.y, q.z, q.w};
         const uint32_t w0 = __shfl_sync(kFull, words[0], 0);
         const bool same = __all_sync(kFull, valid && words[0] == w0 && words[1] == w0 && words[2] == w0 &&
@@ -139,6 +138,22 @@ __global__ void __launch_bounds__(kHist16Threads) k_count_hist16(const uint16_t 
                 count_one16(cnt, encode_key(static_cast<uint16_t>(words[q4] >> 16), codec), corr);
             }
         }
+    };
+    // whole rounds of U vectors per thread: U loads in flight before counting
+    constexpr int U = 4;
+    constexpr uint64_t kRound = static_cast<uint64_t>(U) * kHist16Threads;
+    uint64_t base = 0;
+    for (; base + kRound <= nvec; base += kRound) {
+        uint4 q[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) q[u] = __ldcs(vec + base + u * kHist16Threads + threadIdx.x);
+#pragma unroll
+        for (int u = 0; u < U; ++u) count_vec(q[u], true);
+    }
+    for (; base < nvec; base += kHist16Threads) {  // the rest, one vector per thread (trip count block-uniform)
+        const uint64_t v = base + threadIdx.x;
+        const bool valid = v < nvec;
+        count_vec(valid ? __ldcs(vec + v) : make_uint4(0, 0, 0, 0), valid);
     }
     for (uint64_t i = m0 + nvec * 8 + threadIdx.x; i < b1; i += kHist16Threads)
         count_one16(cnt, encode_key(s[i], codec), corr);
@@ -151,41 +166,139 @@ __global__ void __launch_bounds__(kHist16Threads) k_count_hist16(const uint16_t 
     }
 }
 
-__global__ void k_count_reduce16(const uint32_t *partial, int grid, const unsigned long long *corr,
-                                 unsigned long long *hist) {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= 65536) return;
+// Count of bin v = corr[v] + the CTAs' partials (256 CTAs x 256 bins), and
+// per CTA the keys and the nonempty bins of its 256 bins.
+constexpr int kRunThreads = 256;  // bins per CTA of the reduce and run kernels
+__global__ void __launch_bounds__(kRunThreads) k_count_reduce16(const uint32_t *partial, int grid,
+                                                                const unsigned long long *corr,
+                                                                unsigned long long *hist,
+                                                                unsigned long long *btot, uint32_t *bnnz) {
+    __shared__ unsigned long long ws_c[kRunThreads / 32];
+    __shared__ uint32_t ws_z[kRunThreads / 32];
+    const int v = blockIdx.x * kRunThreads + threadIdx.x;  // the grid covers the 65536 bins exactly
     unsigned long long s = corr[v];
-    for (int g = 0; g < grid; ++g) s += partial[static_cast<size_t>(g) * 65536 + v];
+    int g = 0;
+    for (; g + 4 <= grid; g += 4) {
+        const uint32_t a = partial[static_cast<size_t>(g) * 65536 + v];
+        const uint32_t b = partial[static_cast<size_t>(g + 1) * 65536 + v];
+        const uint32_t c = partial[static_cast<size_t>(g + 2) * 65536 + v];
+        const uint32_t d = partial[static_cast<size_t>(g + 3) * 65536 + v];
+        s += static_cast<unsigned long long>(a) + b + c + d;
+    }
+    for (; g < grid; ++g) s += partial[static_cast<size_t>(g) * 65536 + v];
     hist[v] = s;
-}
-
-// Exclusive starts of `bins` counts (one CTA of 1024 threads).
-__global__ void __launch_bounds__(1024) k_count_scan(const unsigned long long *hist, int bins,
-                                                     unsigned long long *starts) {
-    __shared__ unsigned long long part[1024];
-    const int per = (bins + 1023) / 1024;
-    const int b0 = threadIdx.x * per;
-    unsigned long long s = 0;
-    for (int i = 0; i < per && b0 + i < bins; ++i) s += hist[b0 + i];
-    part[threadIdx.x] = s;
+    unsigned long long c = s;
+    uint32_t z = s != 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        c += __shfl_xor_sync(kFull, c, o);
+        z += __shfl_xor_sync(kFull, z, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        ws_c[threadIdx.x >> 5] = c;
+        ws_z[threadIdx.x >> 5] = z;
+    }
     __syncthreads();
-    // Hillis-Steele inclusive scan over 1024 partial sums
-    for (int o = 1; o < 1024; o <<= 1) {
-        const unsigned long long add = threadIdx.x >= o ? part[threadIdx.x - o] : 0ull;
-        __syncthreads();
-        part[threadIdx.x] += add;
-        __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long tc = 0;
+        uint32_t tz = 0;
+        for (int w = 0; w < kRunThreads / 32; ++w) {
+            tc += ws_c[w];
+            tz += ws_z[w];
+        }
+        btot[blockIdx.x] = tc;
+        bnnz[blockIdx.x] = tz;
     }
-    unsigned long long run = threadIdx.x ? part[threadIdx.x - 1] : 0ull;
-    for (int i = 0; i < per && b0 + i < bins; ++i) {
-        starts[b0 + i] = run;
-        run += hist[b0 + i];
-    }
-    if (threadIdx.x == 1023) starts[bins] = part[1023];
 }
 
-// Largest bin b with starts[b] <= p among [lo, hi] (starts non-decreasing,
+// The output as runs: run r holds `count` copies of bin rval[r] starting at
+// rstart[r], for the nonempty bins in ascending order; rstart[nruns] = n and
+// *nruns the number of runs.  CTA b owns bins [256 b, 256 b + 256): it sums
+// the keys and nonempty bins of the CTAs before it from the reduce's
+// per-CTA totals (btot / bnnz; a single CTA needs none), then scans its own.
+__global__ void __launch_bounds__(kRunThreads) k_count_runs(const unsigned long long *hist,
+                                                            const unsigned long long *btot, const uint32_t *bnnz,
+                                                            unsigned long long *rstart, uint32_t *rval,
+                                                            uint32_t *nruns) {
+    __shared__ unsigned long long red_c[kRunThreads / 32], sc_c[kRunThreads / 32];
+    __shared__ uint32_t red_z[kRunThreads / 32], sc_z[kRunThreads / 32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    // keys and runs of the bins before this CTA (one earlier CTA per thread)
+    unsigned long long c_before = t < static_cast<int>(blockIdx.x) ? btot[t] : 0ull;
+    uint32_t z_before = t < static_cast<int>(blockIdx.x) ? bnnz[t] : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        c_before += __shfl_xor_sync(kFull, c_before, o);
+        z_before += __shfl_xor_sync(kFull, z_before, o);
+    }
+    if (lane == 0) {
+        red_c[warp] = c_before;
+        red_z[warp] = z_before;
+    }
+    // this CTA's bins: inclusive warp scans of counts and of nonempty flags
+    const int v = blockIdx.x * kRunThreads + t;
+    const unsigned long long c = hist[v];
+    unsigned long long x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    const unsigned mask = __ballot_sync(kFull, c != 0);
+    if (lane == 31) {
+        sc_c[warp] = x;
+        sc_z[warp] = __popc(mask);
+    }
+    __syncthreads();
+    unsigned long long base_c = 0, all_c = 0;
+    uint32_t base_z = 0, all_z = 0;
+#pragma unroll
+    for (int w = 0; w < kRunThreads / 32; ++w) {
+        base_c += red_c[w];
+        base_z += red_z[w];
+        if (w < warp) {
+            base_c += sc_c[w];
+            base_z += sc_z[w];
+        }
+        all_c += sc_c[w];
+        all_z += sc_z[w];
+    }
+    if (c) {
+        const uint32_t r = base_z + __popc(mask & ((1u << lane) - 1u));
+        rstart[r] = base_c + x - c;
+        rval[r] = static_cast<uint32_t>(v);
+    }
+    if (blockIdx.x == gridDim.x - 1 && t == kRunThreads - 1) {
+        // the last CTA knows every count: close the run list
+        unsigned long long total = 0;
+        uint32_t runs = 0;
+        for (int w = 0; w < kRunThreads / 32; ++w) {
+            total += red_c[w];
+            runs += red_z[w];
+        }
+        total += all_c;
+        runs += all_z;
+        rstart[runs] = total;
+        *nruns = runs;
+    }
+}
+
+// The same search by a whole warp: 32 probes per round cut [lo, hi] 32-fold
+// (four rounds over 65536 entries).  Every lane returns the index.
+__device__ __forceinline__ int bin_of_warp(const unsigned long long *starts, int lo, int hi, unsigned long long p) {
+    const int lane = threadIdx.x & 31;
+    while (lo < hi) {
+        const int step = (hi - lo + 31) / 32;                    // >= 1
+        const int probe = lo + (lane + 1) * step;
+        const bool ok = probe <= hi && starts[probe] <= p;       // a prefix of the lanes (starts non-decreasing)
+        const int k = __popc(__ballot_sync(kFull, ok));
+        lo += k * step;
+        hi = min(hi, lo + step - 1);
+    }
+    return lo;
+}
+
+// Largest index b with starts[b] <= p among [lo, hi] (starts non-decreasing,
 // starts[lo] <= p).
 __device__ __forceinline__ int bin_of(const unsigned long long *starts, int lo, int hi, unsigned long long p) {
     while (lo < hi) {
@@ -196,51 +309,65 @@ __device__ __forceinline__ int bin_of(const unsigned long long *starts, int lo, 
     return lo;
 }
 
+// Position-driven fill from the runs: each CTA takes output spans of
+// kFillSpan keys; warps 0 and 1 find the runs holding the span's first and
+// last key (warp search), the runs' starts and values between them go to
+// shared memory when they fit, and each thread writes kFillPerThread
+// consecutive keys, stepping through the (nonempty) runs it crosses, as
+// 16-byte vectors where the output is aligned.
 template <typename K>
-__global__ void __launch_bounds__(kFillThreads) k_count_fill(K *keys, uint64_t n, const unsigned long long *starts,
-                                                             int bins, Codec codec) {
+__global__ void __launch_bounds__(kFillThreads) k_count_fill(K *keys, uint64_t n, const unsigned long long *rstart,
+                                                             const uint32_t *rval, const uint32_t *nruns_p,
+                                                             Codec codec) {
     __shared__ unsigned long long win[kFillWindow + 1];
-    __shared__ int sh_v[2];
+    __shared__ uint32_t wval[kFillWindow + 1];
+    __shared__ int sh_r[2];
+    constexpr int kVec = 16 / sizeof(K);
+    const int nr = static_cast<int>(*nruns_p);
     const uint64_t nspan = (n + kFillSpan - 1) / kFillSpan;
     for (uint64_t sp = blockIdx.x; sp < nspan; sp += gridDim.x) {
         const uint64_t p0 = sp * kFillSpan;
         const uint64_t p1 = min(n, p0 + kFillSpan);
-        if (threadIdx.x == 0) {
-            sh_v[0] = bin_of(starts, 0, bins - 1, p0);
-            sh_v[1] = bin_of(starts, 0, bins - 1, p1 - 1);
+        if (threadIdx.x < 64) {  // warp 0: the run of the span's first key, warp 1: of its last
+            const int r = bin_of_warp(rstart, 0, nr - 1, threadIdx.x < 32 ? p0 : p1 - 1);
+            if ((threadIdx.x & 31) == 0) sh_r[threadIdx.x >> 5] = r;
         }
         __syncthreads();
-        const int v0 = sh_v[0], v1 = sh_v[1];
-        const bool windowed = v1 - v0 + 2 <= kFillWindow + 1;
+        const int r0 = sh_r[0], r1 = sh_r[1];
+        const bool windowed = r1 - r0 + 2 <= kFillWindow + 1;
         if (windowed)
-            for (int i = threadIdx.x; i <= v1 - v0 + 1; i += kFillThreads) win[i] = starts[v0 + i];
+            for (int i = threadIdx.x; i <= r1 - r0 + 1; i += kFillThreads) {
+                win[i] = rstart[r0 + i];
+                wval[i] = i <= r1 - r0 ? rval[r0 + i] : 0u;
+            }
         __syncthreads();
         const uint64_t q0 = p0 + static_cast<uint64_t>(threadIdx.x) * kFillPerThread;
         if (q0 < p1) {
-            int v = windowed ? v0 + bin_of(win, 0, v1 - v0, q0) : bin_of(starts, v0, v1, q0);
-            unsigned long long next = windowed ? win[v - v0 + 1] : starts[v + 1];
+            int r = windowed ? r0 + bin_of(win, 0, r1 - r0, q0) : bin_of(rstart, r0, r1, q0);
+            unsigned long long next = windowed ? win[r - r0 + 1] : rstart[r + 1];
+            K val = decode_key(static_cast<K>(windowed ? wval[r - r0] : rval[r]), codec);
             const int cnt = static_cast<int>(umin64(kFillPerThread, p1 - q0));
-            K vals[kFillPerThread];
-#pragma unroll
-            for (int i = 0; i < kFillPerThread; ++i) {
-                const uint64_t p = q0 + i;
-                while (p >= next && v < bins - 1) {
-                    ++v;
-                    next = windowed ? win[v - v0 + 1] : starts[v + 1];
-                }
-                vals[i] = decode_key(static_cast<K>(v), codec);
-            }
             K *dst = keys + q0;
-            constexpr int kVec = 16 / sizeof(K);
+            auto value_at = [&](uint64_t p) {
+                while (p >= next) {  // runs are nonempty: one step per run crossed
+                    ++r;
+                    next = windowed ? win[r - r0 + 1] : rstart[r + 1];
+                    val = decode_key(static_cast<K>(windowed ? wval[r - r0] : rval[r]), codec);
+                }
+                return val;
+            };
             if (cnt == kFillPerThread && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
 #pragma unroll
-                for (int i = 0; i < kFillPerThread; i += kVec) {
+                for (int g = 0; g < kFillPerThread / kVec; ++g) {
+                    K vals[kVec];
+#pragma unroll
+                    for (int e = 0; e < kVec; ++e) vals[e] = value_at(q0 + g * kVec + e);
                     uint4 q;
-                    memcpy(&q, &vals[i], 16);
-                    *reinterpret_cast<uint4 *>(dst + i) = q;
+                    memcpy(&q, vals, 16);
+                    reinterpret_cast<uint4 *>(dst)[g] = q;
                 }
             } else {
-                for (int i = 0; i < cnt; ++i) dst[i] = vals[i];
+                for (int i = 0; i < cnt; ++i) dst[i] = value_at(q0 + i);
             }
         }
         __syncthreads();
@@ -259,13 +386,13 @@ void launch_count8(const CountWork &cw, cudaStream_t st, Recorder &rec, int num_
                                                           cw.hist);
     rec.end();
     rec.begin(BSORT_K_COUNT_SCAN, -1);
-    k_count_scan<<<1, 1024, 0, st>>>(cw.hist, 256, cw.starts);
+    k_count_runs<<<1, kRunThreads, 0, st>>>(cw.hist, nullptr, nullptr, cw.rstart, cw.rval, cw.nruns);
     rec.end();
     rec.begin(BSORT_K_COUNT_FILL, -1);
     const uint64_t spans = (cw.n + kFillSpan - 1) / kFillSpan;
     const int fgrid = static_cast<int>(umin64(static_cast<uint64_t>(num_sms) * 8, spans));
-    k_count_fill<uint8_t><<<max(fgrid, 1), kFillThreads, 0, st>>>(static_cast<uint8_t *>(cw.keys), cw.n, cw.starts,
-                                                                  256, cw.codec);
+    k_count_fill<uint8_t><<<max(fgrid, 1), kFillThreads, 0, st>>>(static_cast<uint8_t *>(cw.keys), cw.n, cw.rstart,
+                                                                  cw.rval, cw.nruns, cw.codec);
     rec.end();
 }
 
@@ -280,17 +407,19 @@ void launch_count16(const CountWork &cw, cudaStream_t st, Recorder &rec, int num
     cudaMemsetAsync(corr, 0, 65536 * sizeof(unsigned long long), st);
     k_count_hist16<<<cw.grid16, kHist16Threads, 32768 * 4, st>>>(static_cast<const uint16_t *>(cw.keys), cw.n,
                                                                  cw.codec, cw.partial, corr);
-    k_count_reduce16<<<256, 256, 0, st>>>(cw.partial, static_cast<int>(cw.grid16), corr, cw.hist);
+    k_count_reduce16<<<65536 / kRunThreads, kRunThreads, 0, st>>>(cw.partial, static_cast<int>(cw.grid16), corr,
+                                                                   cw.hist, cw.btot, cw.bnnz);
     rec.more(1);
     rec.end();
     rec.begin(BSORT_K_COUNT_SCAN, -1);
-    k_count_scan<<<1, 1024, 0, st>>>(cw.hist, 65536, cw.starts);
+    k_count_runs<<<65536 / kRunThreads, kRunThreads, 0, st>>>(cw.hist, cw.btot, cw.bnnz, cw.rstart, cw.rval,
+                                                               cw.nruns);
     rec.end();
     rec.begin(BSORT_K_COUNT_FILL, -1);
     const uint64_t spans = (cw.n + kFillSpan - 1) / kFillSpan;
     const int fgrid = static_cast<int>(umin64(static_cast<uint64_t>(num_sms) * 8, spans));
     k_count_fill<uint16_t><<<max(fgrid, 1), kFillThreads, 0, st>>>(static_cast<uint16_t *>(cw.keys), cw.n,
-                                                                   cw.starts, 65536, cw.codec);
+                                                                   cw.rstart, cw.rval, cw.nruns, cw.codec);
     rec.end();
     (void)num_sms;
 }

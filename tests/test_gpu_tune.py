@@ -1,4 +1,4 @@
-"""Tuned handles (digit width 4..11, smaller finish and merge thresholds,
+"""Tuned handles (digit width 1..11, smaller finish and merge thresholds,
 chunks of one tile) give the same bytes as the oracle, in plain, in-place and
 segmented sorts; the autotuners' choices sort correctly."""
 import numpy as np
@@ -32,7 +32,7 @@ def sort_tuned(x, tuning, descending=False, mode=0):
     return t.cpu().numpy()
 
 
-TUNINGS = [{"radix_bits": 4}, {"radix_bits": 5}, {"radix_bits": 6}, {"radix_bits": 7},
+TUNINGS = [{"radix_bits": 1}, {"radix_bits": 2}, {"radix_bits": 3}, {"radix_bits": 4}, {"radix_bits": 5}, {"radix_bits": 6}, {"radix_bits": 7},
            {"radix_bits": 9}, {"radix_bits": 10}, {"radix_bits": 11}, {"chunk_tiles": 1},
            {"unit_keys": 256}, {"unit_keys": 1024, "merge_keys": 128}, {"radix_bits": 6, "unit_keys": 2048},
            {"radix_bits": 11, "unit_keys": 1024, "chunk_tiles": 1}, {"radix_bits": 10, "unit_keys": 256}]
@@ -54,13 +54,15 @@ def test_tuned_distributions(dist, dtype):
     if dist == "float_edge" and dtype == "int32":
         pytest.skip("float-only distribution")
     x = W.make(dist, dtype, 200003, seed=5)
-    for tuning in ({"radix_bits": 5}, {"unit_keys": 512}, {"radix_bits": 11}, {"radix_bits": 9, "chunk_tiles": 1}):
+    for tuning in ({"radix_bits": 5}, {"unit_keys": 512}, {"radix_bits": 11}, {"radix_bits": 9, "chunk_tiles": 1},
+                   {"radix_bits": 1}, {"radix_bits": 2, "unit_keys": 256}):
         assert_bit_exact(sort_tuned(x, tuning, descending=True), O.bsort(x.copy(), descending=True),
                          "%s %s" % (dist, tuning))
 
 
-@pytest.mark.parametrize("tuning", [{"radix_bits": 6}, {"radix_bits": 11}, {"radix_bits": 10, "chunk_tiles": 1}],
-                         ids=["r6", "r11-as-8", "r10-as-8-chunk1"])
+@pytest.mark.parametrize("tuning", [{"radix_bits": 6}, {"radix_bits": 11}, {"radix_bits": 10, "chunk_tiles": 1},
+                                    {"radix_bits": 1}, {"radix_bits": 3}],
+                         ids=["r6", "r11-as-8", "r10-as-8-chunk1", "r1", "r3"])
 def test_tuned_inplace(tuning):
     """In place, digits wider than 8 bits run as 8 bits: same bytes."""
     x = W.make("uniform", "int32", 1 << 20, seed=6)

@@ -20,6 +20,9 @@ def test_tuned_workspace_sizes(pkg):
     # a smaller finish threshold needs longer work lists; a narrower digit more levels
     assert pkg.workspace_bytes(n, "int32", tuning={"unit_keys": 512}) > base
     assert pkg.workspace_bytes(n, "int32", tuning={"radix_bits": 4}) > base
+    # one bit per level: 32 levels' worth of work lists
+    assert pkg.workspace_bytes(n, "int32", tuning={"radix_bits": 1}) > pkg.workspace_bytes(
+        n, "int32", tuning={"radix_bits": 4})
     # wider digits: 2048-entry tables per chunk and bucket
     assert pkg.workspace_bytes(n, "int32", tuning={"radix_bits": 11}) > base
     assert pkg.workspace_bytes(n, "int32", tuning={"radix_bits": 9}) == pkg.workspace_bytes(
@@ -44,7 +47,7 @@ def test_tuned_segmented_workspace_sizes(pkg):
         pkg.segmented_workspace_bytes(n, s, "float32", tuning={"radix_bits": 12})
 
 
-@pytest.mark.parametrize("bad", [{"radix_bits": 3}, {"radix_bits": 12}, {"unit_keys": 100}, {"unit_keys": 1 << 20},
+@pytest.mark.parametrize("bad", [{"radix_bits": -1}, {"radix_bits": 12}, {"unit_keys": 100}, {"unit_keys": 1 << 20},
                                  {"merge_keys": 10}, {"unit_keys": 1000, "merge_keys": 900}, {"chunk_tiles": 3},
                                  {"chunk_tiles": -1}])
 def test_invalid_tuning_rejected(pkg, bad):
