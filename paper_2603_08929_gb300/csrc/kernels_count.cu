@@ -27,8 +27,10 @@ __host__ __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { re
 constexpr int kHist8Threads = 512;
 constexpr int kHist16Threads = 1024;
 constexpr int kFillThreads = 256;
-constexpr int kFillPerThread = 32;  // consecutive output keys per thread
-constexpr int kFillSpan = kFillThreads * kFillPerThread;
+// Output span of one fill step: a multiple of kFillThreads 16-byte vectors,
+// sized so that each CTA gets about two spans (few per-span searches and
+// barriers per byte written), at least kFillMinVecs vectors per thread.
+constexpr int kFillMinVecs = 4;
 constexpr int kFillWindow = 2048;   // run starts and values staged in shared memory
 
 __global__ void __launch_bounds__(kHist8Threads) k_count_hist8(const uint8_t *keys, uint64_t n, Codec codec,
@@ -309,25 +311,28 @@ __device__ __forceinline__ int bin_of(const unsigned long long *starts, int lo, 
     return lo;
 }
 
-// Position-driven fill from the runs: each CTA takes output spans of
-// kFillSpan keys; warps 0 and 1 find the runs holding the span's first and
-// last key (warp search), the runs' starts and values between them go to
-// shared memory when they fit, and each thread writes kFillPerThread
-// consecutive keys, stepping through the (nonempty) runs it crosses, as
-// 16-byte vectors where the output is aligned.
+// Position-driven fill from the runs: each CTA takes output spans of `span`
+// keys; warps 0 and 1 find the runs holding the span's first and last key
+// (warp search), and the runs' starts and values between them go to shared
+// memory when they fit.  The span is written as 16-byte vectors, vector j by
+// thread j mod kFillThreads, so each warp store covers 512 contiguous bytes;
+// a thread's vectors come in increasing order, so the run of each vector's
+// first key is searched from the thread's previous run on, and the other
+// keys step through the (nonempty) runs they cross.
 template <typename K>
 __global__ void __launch_bounds__(kFillThreads) k_count_fill(K *keys, uint64_t n, const unsigned long long *rstart,
                                                              const uint32_t *rval, const uint32_t *nruns_p,
-                                                             Codec codec) {
+                                                             uint32_t span, Codec codec) {
     __shared__ unsigned long long win[kFillWindow + 1];
     __shared__ uint32_t wval[kFillWindow + 1];
     __shared__ int sh_r[2];
     constexpr int kVec = 16 / sizeof(K);
     const int nr = static_cast<int>(*nruns_p);
-    const uint64_t nspan = (n + kFillSpan - 1) / kFillSpan;
+    const bool vec_ok = (reinterpret_cast<uintptr_t>(keys) & 15) == 0;  // spans start at multiples of kVec keys
+    const uint64_t nspan = (n + span - 1) / span;
     for (uint64_t sp = blockIdx.x; sp < nspan; sp += gridDim.x) {
-        const uint64_t p0 = sp * kFillSpan;
-        const uint64_t p1 = min(n, p0 + kFillSpan);
+        const uint64_t p0 = sp * span;
+        const uint64_t p1 = min(n, p0 + span);
         if (threadIdx.x < 64) {  // warp 0: the run of the span's first key, warp 1: of its last
             const int r = bin_of_warp(rstart, 0, nr - 1, threadIdx.x < 32 ? p0 : p1 - 1);
             if ((threadIdx.x & 31) == 0) sh_r[threadIdx.x >> 5] = r;
@@ -341,37 +346,53 @@ __global__ void __launch_bounds__(kFillThreads) k_count_fill(K *keys, uint64_t n
                 wval[i] = i <= r1 - r0 ? rval[r0 + i] : 0u;
             }
         __syncthreads();
-        const uint64_t q0 = p0 + static_cast<uint64_t>(threadIdx.x) * kFillPerThread;
-        if (q0 < p1) {
-            int r = windowed ? r0 + bin_of(win, 0, r1 - r0, q0) : bin_of(rstart, r0, r1, q0);
+        int r_prev = r0;
+        for (uint32_t j = threadIdx.x; j < span / kVec; j += kFillThreads) {
+            const uint64_t p = p0 + static_cast<uint64_t>(j) * kVec;
+            if (p >= p1) break;  // later vectors of this thread start later still
+            int r = windowed ? r0 + bin_of(win, r_prev - r0, r1 - r0, p) : bin_of(rstart, r_prev, r1, p);
             unsigned long long next = windowed ? win[r - r0 + 1] : rstart[r + 1];
             K val = decode_key(static_cast<K>(windowed ? wval[r - r0] : rval[r]), codec);
-            const int cnt = static_cast<int>(umin64(kFillPerThread, p1 - q0));
-            K *dst = keys + q0;
-            auto value_at = [&](uint64_t p) {
-                while (p >= next) {  // runs are nonempty: one step per run crossed
+            auto value_at = [&](uint64_t q) {
+                while (q >= next) {  // runs are nonempty: one step per run crossed
                     ++r;
                     next = windowed ? win[r - r0 + 1] : rstart[r + 1];
                     val = decode_key(static_cast<K>(windowed ? wval[r - r0] : rval[r]), codec);
                 }
                 return val;
             };
-            if (cnt == kFillPerThread && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+            const int cnt = static_cast<int>(umin64(kVec, p1 - p));
+            if (vec_ok && cnt == kVec) {
+                K vals[kVec];
 #pragma unroll
-                for (int g = 0; g < kFillPerThread / kVec; ++g) {
-                    K vals[kVec];
-#pragma unroll
-                    for (int e = 0; e < kVec; ++e) vals[e] = value_at(q0 + g * kVec + e);
-                    uint4 q;
-                    memcpy(&q, vals, 16);
-                    reinterpret_cast<uint4 *>(dst)[g] = q;
-                }
+                for (int e = 0; e < kVec; ++e) vals[e] = value_at(p + e);
+                uint4 q;
+                memcpy(&q, vals, 16);
+                *reinterpret_cast<uint4 *>(keys + p) = q;
             } else {
-                for (int i = 0; i < cnt; ++i) dst[i] = value_at(q0 + i);
+                for (int e = 0; e < cnt; ++e) keys[p + e] = value_at(p + e);
             }
+            r_prev = r;
         }
         __syncthreads();
     }
+}
+
+// One fill launch: 8 CTAs per SM, spans of ~n / (2 * CTAs) keys (a whole
+// number of kFillThreads vectors, at least kFillMinVecs per thread).
+template <typename K>
+void launch_fill(const CountWork &cw, cudaStream_t st, int num_sms) {
+    constexpr uint64_t kVec = 16 / sizeof(K);
+    constexpr uint64_t unit = kFillThreads * kVec;
+    const uint64_t ctas = static_cast<uint64_t>(num_sms) * 8;
+    uint64_t span = (cw.n + 2 * ctas - 1) / (2 * ctas);
+    span = (span + unit - 1) / unit * unit;
+    if (span < kFillMinVecs * unit) span = kFillMinVecs * unit;
+    if (span > (1u << 30)) span = 1u << 30;
+    const uint64_t spans = (cw.n + span - 1) / span;
+    const int fgrid = static_cast<int>(umin64(ctas, spans));
+    k_count_fill<K><<<max(fgrid, 1), kFillThreads, 0, st>>>(static_cast<K *>(cw.keys), cw.n, cw.rstart, cw.rval,
+                                                           cw.nruns, static_cast<uint32_t>(span), cw.codec);
 }
 
 }  // namespace
@@ -389,10 +410,7 @@ void launch_count8(const CountWork &cw, cudaStream_t st, Recorder &rec, int num_
     k_count_runs<<<1, kRunThreads, 0, st>>>(cw.hist, nullptr, nullptr, cw.rstart, cw.rval, cw.nruns);
     rec.end();
     rec.begin(BSORT_K_COUNT_FILL, -1);
-    const uint64_t spans = (cw.n + kFillSpan - 1) / kFillSpan;
-    const int fgrid = static_cast<int>(umin64(static_cast<uint64_t>(num_sms) * 8, spans));
-    k_count_fill<uint8_t><<<max(fgrid, 1), kFillThreads, 0, st>>>(static_cast<uint8_t *>(cw.keys), cw.n, cw.rstart,
-                                                                  cw.rval, cw.nruns, cw.codec);
+    launch_fill<uint8_t>(cw, st, num_sms);
     rec.end();
 }
 
@@ -416,10 +434,7 @@ void launch_count16(const CountWork &cw, cudaStream_t st, Recorder &rec, int num
                                                                cw.nruns);
     rec.end();
     rec.begin(BSORT_K_COUNT_FILL, -1);
-    const uint64_t spans = (cw.n + kFillSpan - 1) / kFillSpan;
-    const int fgrid = static_cast<int>(umin64(static_cast<uint64_t>(num_sms) * 8, spans));
-    k_count_fill<uint16_t><<<max(fgrid, 1), kFillThreads, 0, st>>>(static_cast<uint16_t *>(cw.keys), cw.n,
-                                                                   cw.rstart, cw.rval, cw.nruns, cw.codec);
+    launch_fill<uint16_t>(cw, st, num_sms);
     rec.end();
     (void)num_sms;
 }
