@@ -350,7 +350,9 @@ __global__ void __launch_bounds__(kFillThreads) k_count_fill(K *keys, uint64_t n
         for (uint32_t j = threadIdx.x; j < span / kVec; j += kFillThreads) {
             const uint64_t p = p0 + static_cast<uint64_t>(j) * kVec;
             if (p >= p1) break;  // later vectors of this thread start later still
-            int r = windowed ? r0 + bin_of(win, r_prev - r0, r1 - r0, p) : bin_of(rstart, r_prev, r1, p);
+            const unsigned long long prev_end = windowed ? win[r_prev - r0 + 1] : rstart[r_prev + 1];
+            int r = p < prev_end ? r_prev  // still inside the thread's previous run
+                    : (windowed ? r0 + bin_of(win, r_prev - r0, r1 - r0, p) : bin_of(rstart, r_prev, r1, p));
             unsigned long long next = windowed ? win[r - r0 + 1] : rstart[r + 1];
             K val = decode_key(static_cast<K>(windowed ? wval[r - r0] : rval[r]), codec);
             auto value_at = [&](uint64_t q) {
@@ -362,7 +364,10 @@ __global__ void __launch_bounds__(kFillThreads) k_count_fill(K *keys, uint64_t n
                 return val;
             };
             const int cnt = static_cast<int>(umin64(kVec, p1 - p));
-            if (vec_ok && cnt == kVec) {
+            if (vec_ok && cnt == kVec && p + kVec <= next) {  // the whole vector inside one run
+                const uint32_t v32 = static_cast<uint32_t>(val) * (sizeof(K) == 1 ? 0x01010101u : 0x00010001u);
+                *reinterpret_cast<uint4 *>(keys + p) = make_uint4(v32, v32, v32, v32);
+            } else if (vec_ok && cnt == kVec) {
                 K vals[kVec];
 #pragma unroll
                 for (int e = 0; e < kVec; ++e) vals[e] = value_at(p + e);
