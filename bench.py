@@ -192,6 +192,32 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def host_cpu() -> dict:
+    """The host's CPU model and logical core count (for the baseline's record)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:  # Arm hosts: /proc/cpuinfo has no model name, lscpu does
+        try:
+            import subprocess
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            model = next((ln.split(":", 1)[1].strip() for ln in out.splitlines()
+                          if ln.lower().startswith("model name")), None)
+        except (OSError, subprocess.SubprocessError):
+            model = None
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    return {"cpu_model": model, "nproc": os.cpu_count()}
+
+
 def cpu_baseline(x, descending, sample_log2):
     """The oracle (literal partition, single thread) on the first 2^k keys."""
     import oracle as O
@@ -201,9 +227,9 @@ def cpu_baseline(x, descending, sample_log2):
     t0 = time.perf_counter()
     O.bsort(sample, descending=descending)
     dt = time.perf_counter() - t0
-    return {"value": m / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "first 2^%d keys of the same input (%d keys), literal partition, one thread, "
-                      "%.1f s" % (sample_log2, m, dt)}
+    return dict({"value": m / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                 "sample": "first 2^%d keys of the same input (%d keys), literal partition, one thread, "
+                           "%.1f s" % (sample_log2, m, dt)}, **host_cpu())
 
 
 def run_reference(args, rank, world):
@@ -235,9 +261,9 @@ def run_reference(args, rank, world):
                                                       "descending" if args.desc else "ascending",
                                                       args.cpu_sample_log2),
                    "n": n, "sample_keys": m},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "2^%d keys per step, literal partition, one thread"
-                                   % args.cpu_sample_log2},
+        "cpu_baseline": dict({"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                              "sample": "2^%d keys per step, literal partition, one thread"
+                                        % args.cpu_sample_log2}, **host_cpu()),
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
