@@ -218,14 +218,23 @@ def host_cpu() -> dict:
     return {"cpu_model": model, "nproc": os.cpu_count()}
 
 
-def cpu_baseline(x, descending, sample_log2):
+def oracle_sort(O, x, descending, dtype):
+    """The oracle's sort of x (bfloat16 arrives as uint16 bit patterns)."""
+    if dtype == "bfloat16":
+        w = x.astype(np.uint64)
+        O.bsort_words(w, O.BF16, descending)
+        return w.astype(np.uint16)
+    return O.bsort(x, descending=descending)
+
+
+def cpu_baseline(x, descending, sample_log2, dtype=None):
     """The oracle (literal partition, single thread) on the first 2^k keys."""
     import oracle as O
     O.build()
     m = min(x.size, 1 << sample_log2)
     sample = np.ascontiguousarray(x[:m])
     t0 = time.perf_counter()
-    O.bsort(sample, descending=descending)
+    oracle_sort(O, sample, descending, dtype)
     dt = time.perf_counter() - t0
     return dict({"value": m / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
                  "sample": "first 2^%d keys of the same input (%d keys), literal partition, one thread, "
@@ -245,7 +254,7 @@ def run_reference(args, rank, world):
     for i in range(args.warmup + args.steps):
         y = x.copy()
         t0 = time.perf_counter()
-        O.bsort(y, descending=args.desc)
+        oracle_sort(O, y, args.desc, args.dtype)
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             times.append(dt)
@@ -688,6 +697,8 @@ def main():
 
     if not args.no_e2e:
         host = torch.from_numpy(x.copy()).pin_memory()
+        if args.dtype == "bfloat16":
+            host = host.view(torch.bfloat16)
         pristine = host.clone()
         for _ in range(2):
             host.copy_(pristine)
@@ -704,7 +715,7 @@ def main():
                        "d2h_bytes_per_step": n * esize, "ms_per_step": e2e_s * 1e3,
                        "api": "bsort_keys_host (pinned host array in and out; library default tuning)"}
     if rank == 0 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(x, args.desc, args.cpu_sample_log2)
+        line["cpu_baseline"] = cpu_baseline(x, args.desc, args.cpu_sample_log2, args.dtype)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
