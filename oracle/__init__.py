@@ -177,12 +177,16 @@ def float_value(bits: int, fmt: KeyFormat) -> float:
     return _load().orc_float_value(bits, fmt.w, fmt.e, fmt.f)
 
 
-def first_unsorted(x: np.ndarray, descending: bool = False) -> int:
-    """Index of the first adjacent pair out of order, or -1."""
-    words = to_words(x)
-    fmt = FORMATS[np.dtype(x.dtype)]
+def first_unsorted_words(words: np.ndarray, fmt: KeyFormat, descending: bool = False) -> int:
+    """Index of the first adjacent pair of raw words out of order, or -1."""
+    words = np.ascontiguousarray(words, dtype=np.uint64)
     return int(_load().orc_first_unsorted(_ptr(words), words.size, fmt.w, fmt.kind, fmt.e,
                                           fmt.f, 0 if descending else 1))
+
+
+def first_unsorted(x: np.ndarray, descending: bool = False) -> int:
+    """Index of the first adjacent pair out of order, or -1."""
+    return first_unsorted_words(to_words(x), FORMATS[np.dtype(x.dtype)], descending)
 
 
 def rank(x_words: np.ndarray, value: int, fmt: KeyFormat, descending: bool = False):
@@ -194,11 +198,16 @@ def rank(x_words: np.ndarray, value: int, fmt: KeyFormat, descending: bool = Fal
     return int(less[0]), int(eq[0])
 
 
-def multiset_digest(x: np.ndarray) -> tuple:
-    words = to_words(x)
+def multiset_digest_words(words: np.ndarray) -> tuple:
+    """Order-independent digest of a multiset of raw words: (sum, sum, xor, count)."""
+    words = np.ascontiguousarray(words, dtype=np.uint64)
     out = np.zeros(4, dtype=np.uint64)
     _load().orc_multiset_digest(_ptr(words), words.size, _ptr(out))
     return tuple(int(v) for v in out)
+
+
+def multiset_digest(x: np.ndarray) -> tuple:
+    return multiset_digest_words(to_words(x))
 
 
 def stable_argsort_words(words: np.ndarray, fmt: KeyFormat, descending: bool = False) -> np.ndarray:

@@ -388,9 +388,17 @@ int orc_sort_by_definition(uint64_t *a, size_t n, int w, int kind, int e_bits, i
  * the array is monotone under the definition order. */
 int64_t orc_first_unsorted(const uint64_t *a, size_t n, int w, int kind, int e_bits, int f_bits, int asc)
 {
+#if ORC_PLANT == 9
+    for (size_t i = 0; i + 2 < n; i++) { /* planted: the last pair is never checked */
+#else
     for (size_t i = 0; i + 1 < n; i++) {
+#endif
         int r = orc_cmp_total(a[i], a[i + 1], w, kind, e_bits, f_bits);
+#if ORC_PLANT == 12
+        if (asc ? r >= 0 : r <= 0) return (int64_t)i; /* planted: equal neighbours flagged */
+#else
         if (asc ? r > 0 : r < 0) return (int64_t)i;
+#endif
     }
     return -1;
 }
@@ -403,7 +411,11 @@ void orc_rank(const uint64_t *a, size_t n, uint64_t x, int w, int kind, int e_bi
 {
     uint64_t less = 0, equal = 0;
     for (size_t i = 0; i < n; i++) {
+#if ORC_PLANT == 10
+        if (a[i] == x) { less++; continue; } /* planted: identical keys counted as before */
+#else
         if (a[i] == x) { equal++; continue; }
+#endif
         int r = orc_cmp_total(a[i], x, w, kind, e_bits, f_bits);
         if (asc ? r < 0 : r > 0) less++;
     }
@@ -425,11 +437,20 @@ static uint64_t mix_a(uint64_t z)
 void orc_multiset_digest(const uint64_t *a, size_t n, uint64_t *out4)
 {
     uint64_t s1 = 0, s2 = 0, x3 = 0;
+#if ORC_PLANT == 11
+    for (size_t i = 1; i < n; i++) { /* planted: the first element is ignored */
+#else
     for (size_t i = 0; i < n; i++) {
-        uint64_t h = mix_a(a[i]);
+#endif
+#if ORC_PLANT == 13
+        const uint64_t v = a[i] & 0xffffffffULL; /* planted: high half of a word ignored */
+#else
+        const uint64_t v = a[i];
+#endif
+        uint64_t h = mix_a(v);
         s1 += h;
-        s2 += mix_a(h ^ 0x5851f42d4c957f2dULL) * (a[i] | 1);
-        x3 ^= mix_a(a[i] + 0x9e3779b97f4a7c15ULL);
+        s2 += mix_a(h ^ 0x5851f42d4c957f2dULL) * (v | 1);
+        x3 ^= mix_a(v + 0x9e3779b97f4a7c15ULL);
     }
     out4[0] = s1; out4[1] = s2; out4[2] = x3; out4[3] = (uint64_t)n;
 }

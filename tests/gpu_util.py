@@ -70,10 +70,101 @@ def par_rank(x, value, fmt, descending):
     return sum(r[0] for r in rs), sum(r[1] for r in rs)
 
 
-def check_full_size(x, got, descending, samples=8, seed=0):
-    """Properties that pin a sort at any size: monotone under the oracle's
-    order and the same multiset as the input (together: the unique sorted
-    sequence), plus sampled positions holding the key of that rank."""
+_UT = {1: np.uint8, 2: np.uint16, 4: np.uint32, 8: np.uint64}
+
+
+def oracle_expected(x, descending=False, fmt=None, split_levels=8):
+    """The oracle's sorted output of a large array, computed by the oracle on
+    pieces that the method itself makes independent.
+
+    Keys of at most 16 bits: the oracle orders every one of the 2^w patterns
+    once, and each pattern is repeated by its count in ``x`` (keys that sort
+    equal are bit-identical, so the sorted output is fixed by the counts).
+
+    Wider keys, following Alg. 2's recursion: after its first
+    ``split_levels`` bit partitions the array is a sequence of ranges, one per
+    pattern of the top ``split_levels`` bits, ordered as the oracle orders
+    those patterns, and each range is then sorted on its own.  So ``x`` is cut
+    into pieces; the oracle partitions every piece by its first
+    ``split_levels`` levels (threads, one piece each); the runs of each top
+    pattern are gathered over the pieces; the oracle sorts each gathered range
+    completely (threads again); the ranges are concatenated in the order the
+    oracle gives the patterns' representatives ``pattern << (w -
+    split_levels)``.  Every ordering decision is the oracle's."""
+    x = np.ascontiguousarray(x)
+    fmt = fmt or O.FORMATS[x.dtype]
+    ut = _UT[x.dtype.itemsize]
+    if fmt.w <= 16:
+        counts = np.bincount(x.view(ut), minlength=1 << fmt.w)
+        order = np.arange(1 << fmt.w, dtype=np.uint64)
+        O.bsort_words(order, fmt, descending)
+        return np.repeat(order.astype(ut), counts[order.astype(np.int64)]).view(x.dtype)
+    k = split_levels
+    words = x.view(ut).astype(np.uint64)
+    pieces = _chunks(words.size, 16)
+
+    def partition(ab):
+        a, b = ab
+        piece = words[a:b]
+        O.bsort_words(piece, fmt, descending, O.LITERAL, max_levels=k)
+        top = piece >> np.uint64(fmt.w - k)
+        cut = np.flatnonzero(top[1:] != top[:-1]) + 1
+        starts = np.concatenate(([0], cut))
+        ends = np.concatenate((cut, [piece.size]))
+        return [(int(top[s]), a + int(s), a + int(e)) for s, e in zip(starts, ends)]
+
+    with _pool() as ex:
+        runs = [r for rs in ex.map(partition, pieces) for r in rs]
+    groups = {}
+    for pat, a, b in runs:
+        groups.setdefault(pat, []).append((a, b))
+    reps = np.array(sorted(groups), dtype=np.uint64) << np.uint64(fmt.w - k)
+    O.bsort_words(reps, fmt, descending)
+    order = [int(r) >> (fmt.w - k) for r in reps]
+    bounds = np.cumsum([0] + [sum(b - a for a, b in groups[p]) for p in order])
+    out = np.empty_like(words)
+
+    def finish(i):
+        dst = out[bounds[i]:bounds[i + 1]]
+        o = 0
+        for a, b in groups[order[i]]:
+            dst[o:o + b - a] = words[a:b]
+            o += b - a
+        O.bsort_words(dst, fmt, descending)
+
+    with _pool() as ex:
+        list(ex.map(finish, sorted(range(len(order)), key=lambda i: bounds[i] - bounds[i + 1])))
+    return out.astype(ut).view(x.dtype)
+
+
+def oracle_segments(x, off, descending=False):
+    """The oracle's sort of every segment [off[i], off[i+1]) of x, the
+    segments spread over threads (each is independent)."""
+    out = x.copy()
+    segs = [(int(a), int(b)) for a, b in zip(off[:-1], off[1:]) if b - a > 1]
+    segs.sort(key=lambda ab: ab[0] - ab[1])  # largest first
+
+    def one(ab):
+        a, b = ab
+        out[a:b] = O.bsort(x[a:b], descending=descending)
+
+    with _pool() as ex:
+        list(ex.map(one, segs))
+    return out
+
+
+def check_full_size(x, got, descending, samples=8, seed=0, fmt=None):
+    """The whole output, byte for byte, against the oracle's sorted output of
+    the same input (``oracle_expected``)."""
+    assert got.size == x.size
+    assert_bit_exact(got, oracle_expected(x, descending, fmt=fmt), "full-size parity")
+
+
+def check_by_properties(x, got, descending, samples=8, seed=0):
+    """Properties that pin a sort at any size, for arrays too large to hold
+    the oracle's output beside them: monotone under the oracle's order and the
+    same multiset as the input (together: the unique sorted sequence), plus
+    sampled positions holding the key of that rank."""
     assert got.size == x.size
     i = par_first_unsorted(got, descending)
     assert i == -1, "out of order at %d: %r %r" % (i, got[i], got[i + 1])

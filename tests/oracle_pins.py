@@ -383,6 +383,182 @@ def pin_stable_argsort_machine_types():
             assert np.all(p[1:][same] > p[:-1][same]), "ties out of input order (%s)" % dt
 
 
+# --- the checkers behind the full-size parity tests ---------------------------
+#
+# first_unsorted, rank and multiset_digest certify GPU outputs too large to
+# compare with a full oracle run inside one test; each is pinned here against
+# a brute-force restatement (py_order_key) or against the arithmetic fact it
+# relies on, and each has planted mistakes that these pins must catch.
+
+_SMALL_FMTS = [O.KeyFormat(3, O.UNSIGNED), O.KeyFormat(4, O.SIGNED), O.KeyFormat(6, O.SIGNED),
+               O.KeyFormat(6, O.FLOAT, 3, 2), O.KeyFormat(5, O.FLOAT, 2, 2), O.KeyFormat(8, O.FLOAT, 4, 3)]
+
+
+def _py_first_unsorted(xs, fmt, asc):
+    ks = [py_order_key(v, fmt) for v in xs]
+    for i in range(len(ks) - 1):
+        if (ks[i] > ks[i + 1]) if asc else (ks[i] < ks[i + 1]):
+            return i
+    return -1
+
+
+def pin_first_unsorted_bruteforce():
+    """first_unsorted equals the first adjacent pair out of order under the
+    exact-rational restatement: random tie-heavy arrays, their sorted forms
+    (answer -1, ties included) and sorted forms with one planted inversion at
+    the front, the back and in between."""
+    rnd = random.Random(2468)
+    for fmt in _SMALL_FMTS:
+        for trial in range(80):
+            n = rnd.randint(0, 10)
+            pool = [rnd.randrange(1 << fmt.w) for _ in range(rnd.randint(1, 4))]
+            xs = [rnd.choice(pool) if rnd.random() < 0.6 else rnd.randrange(1 << fmt.w) for _ in range(n)]
+            for asc in (True, False):
+                ordered = sorted(xs, key=lambda v: py_order_key(v, fmt), reverse=not asc)
+                cases = [xs, ordered]
+                for i in (0, n - 2, n // 2 - 1):
+                    if 0 <= i < n - 1 and py_order_key(ordered[i], fmt) != py_order_key(ordered[i + 1], fmt):
+                        bad = list(ordered)
+                        bad[i], bad[i + 1] = bad[i + 1], bad[i]
+                        cases.append(bad)
+                for c in cases:
+                    got = O.first_unsorted_words(np.array(c, dtype=np.uint64), fmt, not asc)
+                    assert got == _py_first_unsorted(c, fmt, asc), (fmt, c, asc, got)
+                assert O.first_unsorted_words(np.array(ordered, dtype=np.uint64), fmt, not asc) == -1
+
+
+def pin_first_unsorted_machine_types():
+    """On every machine type a sorted output reads as sorted, and one adjacent
+    swap of distinct keys is found at exactly its index (first pair, last pair,
+    middle); for floats also -0/+0 and two same-sign NaN payloads swapped."""
+    rng = np.random.default_rng(13)
+    for dt in O.FORMATS:
+        ut = {8: np.uint8, 16: np.uint16, 32: np.uint32, 64: np.uint64}[dt.itemsize * 8]
+        x = rng.integers(0, np.iinfo(ut).max, size=3000, dtype=ut, endpoint=True).view(dt)
+        x[:40] = x[40:80]  # ties
+        for desc in (False, True):
+            s = O.bsort(x, descending=desc)
+            assert O.first_unsorted(s, desc) == -1, dt
+            sw = s.view(ut)
+            for i in (0, s.size - 2, s.size // 2):
+                j = i
+                while sw[j] == sw[j + 1]:  # nearest distinct pair (back from the end)
+                    j += 1 if i < s.size - 2 else -1
+                bad = s.copy()
+                bad[[j, j + 1]] = bad[[j + 1, j]]
+                assert O.first_unsorted(bad, desc) == j, (dt, desc, j)
+        if dt.kind == "f":
+            w = dt.itemsize * 8
+            f = {16: 10, 32: 23, 64: 52}[w]
+            S, E = 1 << (w - 1), ((1 << (w - 1 - f)) - 1) << f
+            pairs = [(S, 0), (E | 1, E | (1 << (f - 1))), (S | E | (1 << (f - 1)), S | E | 1)]
+            for lo_hi in pairs:
+                for desc in (False, True):
+                    a = np.array(lo_hi if not desc else lo_hi[::-1], dtype=np.uint64)
+                    fmt = O.FORMATS[dt]
+                    assert O.first_unsorted_words(a, fmt, desc) == -1, (dt, lo_hi, desc)
+                    assert O.first_unsorted_words(a[::-1].copy(), fmt, desc) == 0, (dt, lo_hi, desc)
+
+
+def pin_rank_bruteforce():
+    """rank(a, x) = (keys strictly before x, keys bit-identical to x) by a
+    brute count under the exact-rational restatement, for every pattern x of
+    small formats against tie-heavy arrays, both directions."""
+    rnd = random.Random(1357)
+    for fmt in _SMALL_FMTS:
+        for trial in range(12):
+            n = rnd.randint(0, 24)
+            pool = [rnd.randrange(1 << fmt.w) for _ in range(3)]
+            xs = [rnd.choice(pool) if rnd.random() < 0.5 else rnd.randrange(1 << fmt.w) for _ in range(n)]
+            a = np.array(xs, dtype=np.uint64)
+            for x in range(1 << fmt.w):
+                kx = py_order_key(x, fmt)
+                for asc in (True, False):
+                    less = sum(1 for v in xs if v != x and ((py_order_key(v, fmt) < kx) if asc
+                                                            else (py_order_key(v, fmt) > kx)))
+                    eq = xs.count(x)
+                    assert O.rank(a, x, fmt, not asc) == (less, eq), (fmt, xs, x, asc)
+
+
+def pin_rank_places_sorted_keys():
+    """Machine types: the key at every position p of the oracle's sort has
+    rank [less, less + equal) containing p."""
+    rng = np.random.default_rng(17)
+    for dt in O.FORMATS:
+        ut = {8: np.uint8, 16: np.uint16, 32: np.uint32, 64: np.uint64}[dt.itemsize * 8]
+        pool = rng.integers(0, np.iinfo(ut).max, size=5, dtype=ut, endpoint=True)
+        x = np.where(rng.random(400) < 0.5, rng.choice(pool, 400),
+                     rng.integers(0, np.iinfo(ut).max, size=400, dtype=ut, endpoint=True)).astype(ut).view(dt)
+        words = O.to_words(x)
+        for desc in (False, True):
+            s = O.to_words(O.bsort(x, descending=desc))
+            for p in range(0, s.size, 7):
+                less, eq = O.rank(words, int(s[p]), O.FORMATS[dt], desc)
+                assert less <= p < less + eq, (dt, desc, p)
+
+
+def pin_multiset_digest():
+    """The digest is a function of the multiset: equal under any
+    permutation; different after one bit of one element flips (every bit of
+    the first, last and a middle element), after an element is replaced by a
+    copy of another (count unchanged), after one is dropped or duplicated, and
+    for {+0, +0} against {+0, -0}."""
+    rng = np.random.default_rng(19)
+    for dt in (np.uint8, np.int16, np.float16, np.uint32, np.float32, np.int64, np.float64):
+        dt = np.dtype(dt)
+        w = dt.itemsize * 8
+        ut = {8: np.uint8, 16: np.uint16, 32: np.uint32, 64: np.uint64}[w]
+        x = rng.integers(0, np.iinfo(ut).max, size=257, dtype=ut, endpoint=True)
+        x[5] = x[6]
+        words = x.astype(np.uint64)
+        d0 = O.multiset_digest_words(words)
+        assert d0[3] == x.size
+        for trial in range(4):
+            assert O.multiset_digest_words(rng.permutation(words)) == d0
+        for i in (0, x.size - 1, x.size // 2):
+            for b in range(w):
+                y = words.copy()
+                y[i] ^= np.uint64(1) << np.uint64(b)
+                assert O.multiset_digest_words(y) != d0, (dt, i, b)
+        y = words.copy()
+        y[0] = y[1]
+        assert O.multiset_digest_words(y) != d0
+        y = words.copy()
+        y[-1] = y[0]
+        assert O.multiset_digest_words(y) != d0
+        assert O.multiset_digest_words(words[1:]) != d0
+        assert O.multiset_digest_words(np.append(words, words[3])) != d0
+    z = np.array([0, 0], dtype=np.uint64)
+    for w in (16, 32, 64):
+        mz = np.array([0, 1 << (w - 1)], dtype=np.uint64)
+        assert O.multiset_digest_words(z) != O.multiset_digest_words(mz)
+
+
+def pin_parallel_checkers_combine():
+    """The chunked checkers of the GPU tests (threads over 64 chunks) agree
+    with one plain call on arrays spanning several chunks, and an inversion
+    straddling a chunk boundary is found at its index."""
+    import gpu_util as G
+    rng = np.random.default_rng(23)
+    n = 3 * (1 << 20) + 777
+    x = rng.integers(-(1 << 31), (1 << 31) - 1, size=n, dtype=np.int64).astype(np.int32)
+    assert G.par_multiset_digest(x) == O.multiset_digest(x)
+    s = O.bsort(x)
+    assert G.par_first_unsorted(s, False) == -1
+    for i in ((1 << 20) - 1, 2 * (1 << 20) - 1, n - 2, 0):
+        j = i
+        while s[j] == s[j + 1]:
+            j += 1 if i < n - 2 else -1
+        bad = s.copy()
+        bad[[j, j + 1]] = bad[[j + 1, j]]
+        assert G.par_first_unsorted(bad, False) == j, j
+    fmt = O.FORMATS[x.dtype]
+    words = O.to_words(x)
+    for p in (0, n // 3, n - 1):
+        key = int(O.to_words(s[p:p + 1])[0])
+        assert G.par_rank(x, key, fmt, False) == O.rank(words, key, fmt, False)
+
+
 ALL_PINS = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]
 
 

@@ -92,7 +92,7 @@ def test_inplace_equals_pingpong_and_reports_aux():
     assert aux < 0.5 * n * 4, aux / (n * 4)
 
 
-def test_inplace_full_size_properties():
+def test_inplace_full_size():
     n = 1 << 26
     x = W.make("uniform", "int32", n, seed=22)
     got, aux = sort_inplace(x)

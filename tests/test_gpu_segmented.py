@@ -59,6 +59,34 @@ def test_segmented_skewed(dist):
     assert_bit_exact(t.cpu().numpy(), oracle_segments(x, off, False), "segmented %s" % dist)
 
 
+@pytest.mark.parametrize("max_log2", [17, 20], ids=["scaled-2p17", "stated-2p20"])
+def test_batched_workload_at_size(max_log2):
+    """The batched configuration at size: 10,000 int32 and 10,000 float32
+    segments, sizes floor(2^(k*u)) log-uniform in [1, 2^k] (k = 20 as stated,
+    about 1.5e9 keys in all; k = 17, about 2.2e8 keys, the stated total),
+    uniform bits, ascending, generated as the benchmark generates them and
+    sorted by one captured graph per dtype (the benchmark's call); every
+    segment byte for byte against the oracle."""
+    import torch
+    import paper_2603_08929_gb300 as bs
+    from gpu_util import oracle_segments
+    for k, dt in enumerate(("int32", "float32")):
+        sizes = W.segment_sizes(17 * k, 10000, max_log2)
+        x, off = make_segments(sizes, dt, seed=k)
+        t = to_device(x)
+        offs = torch.from_numpy(off).cuda()
+        h = bs.Handle()
+        ws = torch.empty(bs.segmented_workspace_bytes(t.numel(), len(sizes), dt), dtype=torch.uint8, device="cuda")
+        g = bs.Graph(h, t, ws, offsets=offs)
+        g.launch()
+        assert g.error() == 0
+        got = t.cpu().numpy()
+        g.close()
+        del t, ws, offs
+        torch.cuda.empty_cache()
+        assert_bit_exact(got, oracle_segments(x, off, False), "batched %s, sizes in [1, 2^%d]" % (dt, max_log2))
+
+
 def test_segmented_graph_replay_and_ws():
     import torch
     import paper_2603_08929_gb300 as bs

@@ -1,8 +1,10 @@
-"""The serving loop: every request's result equals the same request sorted
-alone, requests overlap on the device, and admission respects the budget."""
+"""The serving loop: every request's result equals the oracle's sort of the
+request and the same request sorted alone, requests overlap on the device,
+and admission respects the budget."""
 import numpy as np
 import pytest
 
+import oracle as O
 import workloads as W
 from gpu_util import assert_bit_exact, to_device
 
@@ -23,8 +25,13 @@ def request_mix(count, seed):
     sizes = np.floor(2.0 ** (10 + 10 * rng.random(count))).astype(np.int64)
     reqs = []
     for i, (dt, n) in enumerate(zip(dts, sizes)):
-        dist = "normal" if i % 2 else "uniform"
-        reqs.append((W.make(dist, dt, int(n), seed=seed * 1000 + i), bool(i % 3 == 0)))
+        # the served workload's value mixes, plus the float edge values (+-0,
+        # subnormals, infinities, NaN payloads of both signs) and tie-heavy ints
+        if i % 3 == 2:
+            dist = "float_edge" if dt.startswith("float") else "zipf"
+        else:
+            dist = "normal01" if i % 3 else "uniform"
+        reqs.append((W.make(dist, dt, int(n), seed=seed * 1000 + i), bool(i % 4 == 0)))
     return reqs
 
 
@@ -53,7 +60,10 @@ def test_same_alone_and_in_the_mix():
     for c in done:
         assert c["t_submit_ns"] <= c["t_admit_ns"] <= c["t_done_ns"]
     for i, b in enumerate(bufs):
-        assert_bit_exact(b.cpu().numpy(), alone[i], "request %d" % i)
+        x, desc = reqs[i]
+        got = b.cpu().numpy()
+        assert_bit_exact(got, O.bsort(x, descending=desc), "request %d (%s) against the oracle" % (i, x.dtype))
+        assert_bit_exact(got, alone[i], "request %d: in the mix against alone" % i)
     st = srv.stats()
     assert st["max_concurrent_slots"] > 1  # requests overlapped on the device
     assert st["batches"] < len(reqs)       # small requests shared slots
@@ -78,7 +88,7 @@ def test_budget_limits_requests_in_flight():
     assert st["peak_in_flight_bytes"] <= budget
     assert st["max_concurrent_slots"] <= 2
     for x, b in zip(xs, bufs):
-        assert np.array_equal(b.cpu().numpy(), np.sort(x))
+        assert_bit_exact(b.cpu().numpy(), O.bsort(x), "budgeted request")
     with pytest.raises(bs.BsortError):
         srv.submit(to_device(np.zeros(n + 1, np.int32)))  # beyond max_request_keys
     srv.close()

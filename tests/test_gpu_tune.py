@@ -71,8 +71,8 @@ def test_tuned_inplace(tuning):
 
 @pytest.mark.parametrize("dtype", ["int32", "float64"])
 def test_wide_digits_full_size(dtype):
-    """11-bit digits at the full sizes (2^28 4-byte, 2^27 8-byte keys):
-    monotone, the input's multiset and sampled ranks."""
+    """11-bit digits at the full sizes (2^28 4-byte, 2^27 8-byte keys),
+    byte for byte against the oracle."""
     from gpu_util import check_full_size
     n = 1 << (28 if dtype == "int32" else 27)
     x = W.make("uniform", dtype, n, seed=11)

@@ -23,6 +23,11 @@ PLANTS = {
     6: "subnormal exponent off by one",
     7: "stable split reverses the back side",
     8: "stable argsort takes ties from the right run",
+    9: "first_unsorted never checks the last pair",
+    10: "rank counts identical keys as before",
+    11: "multiset digest ignores the first element",
+    12: "first_unsorted flags equal neighbours",
+    13: "multiset digest ignores the high half of a word",
 }
 
 
