@@ -343,7 +343,11 @@ def run_segmented(args, rank, world):
         for a in arms:
             a[6].launch(stream)
 
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.start()
     ms_graph = timed(graphs, args.steps, args.warmup)
+    clock_info = clocks.stop() if clocks else None
     for a in arms:
         if a[6].error(stream) != 0:
             raise RuntimeError("device error word set in the segmented sort")
@@ -384,7 +388,10 @@ def run_segmented(args, rank, world):
         "speedup_vs_plain_per_segment": ms_plain / ms_graph,
         "sorted_check": ok,
     }
-    print(json.dumps(line), flush=True)
+    if clock_info:
+        line["clocks"] = clock_info
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def run_serve(args, rank, world):
@@ -512,7 +519,10 @@ def run_pairs_mode(args, rank, world):
         h.set_tuning(8, tuning8)
     stream = torch.cuda.current_stream()
     times = []
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     for i in range(args.warmup + args.steps):
+        if i == args.warmup and clocks:
+            clocks.start()
         keys.copy_(x)
         if vals is not None:
             vals.copy_(v0)
@@ -524,6 +534,7 @@ def run_pairs_mode(args, rank, world):
         torch.cuda.synchronize()
         if i >= args.warmup:
             times.append(e0.elapsed_time(e1))
+    clock_info = clocks.stop() if clocks else None
     if h.get_error(stream) != 0:
         raise RuntimeError("device error word set in the key-value sort")
     ms = sum(times) / len(times)
@@ -550,6 +561,8 @@ def run_pairs_mode(args, rank, world):
                                               peak_src),
         "sorted_check": ok,
     }
+    if clock_info:
+        line["clocks"] = clock_info
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -175,6 +175,29 @@ bsort_status bsort_keys_partial_ws(bsort_handle *handle, void *keys, size_t n, b
                                    int levels, void *workspace, size_t ws_bytes, void *stream);
 
 /*
+ * Counts of the keys by the top `bits` bits of their position in the sorted
+ * order, for ranks that sort one array together (each holding a shard): the
+ * key is mapped by the library's order-preserving encoding (unsigned: as
+ * is; signed: sign bit inverted, Alg. 3's inverted sign pass; float: the sign
+ * pass inverted and the negative half's other bits inverted, Algs. 4/5 as
+ * Sec. III-B requires; descending: all bits inverted) and its top `bits`
+ * bits form digit d.  Digit d's keys precede digit d + 1's in the sorted
+ * output, so prefix sums of the counts, summed over the shards, are output
+ * positions -- the split that the method's first `bits` MSB partitions make
+ * (Thm. 3's refinement).
+ *   keys      device pointer, n keys of dtype dt (read only, any alignment
+ *             that dt itself needs)
+ *   bits      1 .. min(12, key bits)
+ *   d_counts  device array of 2^bits uint64 words, owned by the caller,
+ *             overwritten: d_counts[d] = keys of digit d
+ * Asynchronous on `stream`.  Errors: BSORT_ERR_INVALID_ARG (bits out of
+ * range, NULL pointers with n > 0), BSORT_ERR_MISALIGNED, BSORT_ERR_CUDA.
+ * n == 0 writes zeros.
+ */
+bsort_status bsort_top_digit_counts(const void *keys, size_t n, bsort_dtype dt, int descending, int bits,
+                                    uint64_t *d_counts, void *stream);
+
+/*
  * Failure-detection self-test: launches one device wait of the kind the
  * library uses (a bounded poll, a fraction of a second) on a flag that nothing
  * sets, on `stream`, and synchronises.  Returns BSORT_ERR_TIMEOUT when the
@@ -277,19 +300,29 @@ bsort_status bsort_graph_destroy(bsort_graph *graph);
 
 /* ---- serving: continuous batching of sort requests ------------------------
  *
- * A server owns num_slots slots (a CUDA stream, a handle and a workspace of
- * the largest request each) and a scheduler thread.  Requests queue in
- * arrival order; the oldest waiting request is admitted when a slot is free
- * and the HBM budget -- payload bytes plus the workspace a standalone sort of
- * the request needs, summed over admitted requests -- has room (a request is
- * always admitted when nothing else is in flight).  A slot takes up to
- * max_batch requests at once while their keys stay <= batch_keys.  Requests
- * in different slots overlap on the device.  Each request is sorted in place
- * by the plain sort, so its result is the same alone and in the mix.
- * Timestamps are host steady-clock nanoseconds.  The caller keeps each
- * request's device buffer alive, and does not touch it, until its completion
- * is polled.
+ * A server owns lanes, one per entry of its device list, and a scheduler
+ * thread.  A lane has num_slots slots (a CUDA stream, a handle, a workspace
+ * of the largest request, and a staging buffer plus segmented workspace of
+ * batch_keys keys) and its own HBM budget.  A request joins the queue of the
+ * least-loaded lane of the device its buffer lives on (in-flight plus queued
+ * bytes over the lane's budget; ties: the lower lane); a device listed twice
+ * is two lanes sharing one GPU.  In each lane, the oldest waiting request is
+ * admitted when a slot is free and the lane's budget -- payload bytes plus
+ * the workspace a standalone sort of the request needs, summed over the
+ * lane's admitted requests -- has room (a request is always admitted when
+ * nothing else is in flight on its lane).  The budget covers the requests'
+ * own footprints; the slots' workspaces (slot_workspace_bytes each, reported
+ * by bsort_server_stats) are held on top of it from creation on.  A slot
+ * takes up to max_batch requests at once while their keys stay <=
+ * batch_keys; those of one 4- or 8-byte dtype and direction are gathered into
+ * the slot's staging buffer and sorted by one segmented sort (one launch
+ * sequence), the rest by the plain sort.  Requests in different slots
+ * overlap on the device.  A segment is sorted exactly as a plain array, so a
+ * request's result is the same alone and in the mix.  Timestamps are host
+ * steady-clock nanoseconds.  The caller keeps each request's device buffer
+ * alive, and does not touch it, until its completion is polled.
  */
+#define BSORT_SERVER_MAX_LANES 64
 typedef struct bsort_server bsort_server;
 typedef struct {
     int32_t num_slots;          /* 1..64 */
@@ -303,21 +336,43 @@ typedef struct {
 typedef struct {
     uint64_t tag;
     int32_t status;             /* bsort_status of this request's sort */
-    int32_t slot;
+    int32_t slot;               /* server-wide slot index: lane * num_slots + slot of the lane */
+    int32_t lane;               /* lane that sorted it */
+    int32_t pad;
     uint64_t t_submit_ns, t_admit_ns, t_done_ns;
 } bsort_completion;
 typedef struct {
     uint64_t submitted, completed, batches, pending;
-    size_t in_flight_bytes, peak_in_flight_bytes;
+    size_t in_flight_bytes, peak_in_flight_bytes;  /* summed over the lanes */
     int32_t max_concurrent_slots;
-    int32_t pad;
-    size_t slot_workspace_bytes;
+    int32_t num_lanes;
+    size_t slot_workspace_bytes;  /* device bytes each slot holds: plain and segmented workspaces, staging */
     uint64_t launches;          /* kernel launches (and memsets) enqueued so far */
+    uint64_t grouped_sorts;     /* segmented sorts that took several requests at once */
 } bsort_server_info;
+typedef struct {
+    int32_t device;
+    int32_t num_slots;
+    size_t budget_bytes;
+    size_t in_flight_bytes, peak_in_flight_bytes, queued_bytes;
+    uint64_t admitted, completed;
+} bsort_server_lane_info;
+/* One lane on the current device. */
 bsort_status bsort_server_create(const bsort_server_config *cfg, bsort_server **server);
-/* Queues a request (non-blocking).  n > max_request_keys: BSORT_ERR_UNSUPPORTED. */
+/* One lane per entry of devices[0, num_devices) (CUDA device ordinals,
+ * 1..BSORT_SERVER_MAX_LANES entries, repeats allowed), each with cfg's slots
+ * and budget.  Bad ordinals or config: BSORT_ERR_INVALID_ARG. */
+bsort_status bsort_server_create_multi(const bsort_server_config *cfg, const int32_t *devices, int32_t num_devices,
+                                       bsort_server **server);
+/* The device of the least-loaded lane: where to put the next request. */
+bsort_status bsort_server_pick_device(bsort_server *server, int32_t *device);
+/* Queues a request (non-blocking) on the least-loaded lane of the device
+ * holding `keys`.  n > max_request_keys: BSORT_ERR_UNSUPPORTED; keys not in
+ * device memory of a served device: BSORT_ERR_INVALID_ARG. */
 bsort_status bsort_server_submit(bsort_server *server, void *keys, size_t n, bsort_dtype dt, int descending,
                                  uint64_t tag);
+/* Counters of one lane. */
+bsort_status bsort_server_lane_stats(bsort_server *server, int32_t lane, bsort_server_lane_info *out);
 /* Moves up to max completions into out; *count = how many. */
 bsort_status bsort_server_poll(bsort_server *server, bsort_completion *out, size_t max, size_t *count);
 bsort_status bsort_server_stats(bsort_server *server, bsort_server_info *out);
@@ -397,6 +452,9 @@ typedef struct {
     /* shared-memory finish units of those calls, by method: one counting pass,
      * split + comparison ranks, LSD passes */
     uint64_t finish_units_counting, finish_units_compare, finish_units_lsd;
+    /* of the counting units, those finished by the vector-load counting pass
+     * for keys known to agree above their low 16 bits */
+    uint64_t finish_units_counting_fast;
     bsort_profile_record rec[BSORT_PROFILE_MAX];
 } bsort_profile;
 

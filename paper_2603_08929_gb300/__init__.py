@@ -18,7 +18,7 @@ from . import build as _build
 __all__ = [
     "DTYPES", "BsortError", "lib", "bsort_keys", "bsort_keys_ws", "bsort_keys_host", "bsort_keys_noalloc",
     "bsort_keys_segmented", "segmented_workspace_bytes", "Graph", "Server", "sort_", "sort_segmented_",
-    "bsort_keys_partial_ws", "selftest_bounded_wait",
+    "bsort_keys_partial_ws", "selftest_bounded_wait", "top_digit_counts",
     "workspace_bytes", "Handle", "sort_", "status_string",
 ]
 
@@ -45,7 +45,8 @@ class _Profile(ctypes.Structure):
     _fields_ = [("num_records", ctypes.c_int32), ("num_calls", ctypes.c_int32),
                 ("num_launches", ctypes.c_int32), ("pad", ctypes.c_int32),
                 ("finish_units_counting", ctypes.c_uint64), ("finish_units_compare", ctypes.c_uint64),
-                ("finish_units_lsd", ctypes.c_uint64), ("rec", _Record * _PROFILE_MAX)]
+                ("finish_units_lsd", ctypes.c_uint64), ("finish_units_counting_fast", ctypes.c_uint64),
+                ("rec", _Record * _PROFILE_MAX)]
 
 
 class _ServerConfig(ctypes.Structure):
@@ -56,6 +57,7 @@ class _ServerConfig(ctypes.Structure):
 
 class _Completion(ctypes.Structure):
     _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int32), ("slot", ctypes.c_int32),
+                ("lane", ctypes.c_int32), ("pad", ctypes.c_int32),
                 ("t_submit_ns", ctypes.c_uint64), ("t_admit_ns", ctypes.c_uint64), ("t_done_ns", ctypes.c_uint64)]
 
 
@@ -63,7 +65,14 @@ class _ServerInfo(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("batches", ctypes.c_uint64),
                 ("pending", ctypes.c_uint64), ("in_flight_bytes", ctypes.c_size_t),
                 ("peak_in_flight_bytes", ctypes.c_size_t), ("max_concurrent_slots", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("slot_workspace_bytes", ctypes.c_size_t), ("launches", ctypes.c_uint64)]
+                ("num_lanes", ctypes.c_int32), ("slot_workspace_bytes", ctypes.c_size_t),
+                ("launches", ctypes.c_uint64), ("grouped_sorts", ctypes.c_uint64)]
+
+
+class _LaneInfo(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("num_slots", ctypes.c_int32), ("budget_bytes", ctypes.c_size_t),
+                ("in_flight_bytes", ctypes.c_size_t), ("peak_in_flight_bytes", ctypes.c_size_t),
+                ("queued_bytes", ctypes.c_size_t), ("admitted", ctypes.c_uint64), ("completed", ctypes.c_uint64)]
 
 
 class _Tuning(ctypes.Structure):
@@ -146,6 +155,8 @@ def lib():
         L.bsort_keys_partial_ws.restype = i
         L.bsort_selftest_bounded_wait.argtypes = [vp]
         L.bsort_selftest_bounded_wait.restype = i
+        L.bsort_top_digit_counts.argtypes = [vp, sz, i, i, i, vp, vp]
+        L.bsort_top_digit_counts.restype = i
         L.bsort_last_aux_bytes.argtypes = [vp, ctypes.POINTER(sz)]
         L.bsort_last_aux_bytes.restype = i
         L.bsort_server_create.argtypes = [ctypes.POINTER(_ServerConfig), ctypes.POINTER(vp)]
@@ -155,6 +166,13 @@ def lib():
         L.bsort_server_poll.argtypes = [vp, ctypes.POINTER(_Completion), sz, ctypes.POINTER(sz)]
         L.bsort_server_poll.restype = i
         L.bsort_server_stats.argtypes = [vp, ctypes.POINTER(_ServerInfo)]
+        L.bsort_server_create_multi.argtypes = [ctypes.POINTER(_ServerConfig), ctypes.POINTER(ctypes.c_int32),
+                                                ctypes.c_int32, ctypes.POINTER(vp)]
+        L.bsort_server_create_multi.restype = i
+        L.bsort_server_pick_device.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
+        L.bsort_server_pick_device.restype = i
+        L.bsort_server_lane_stats.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(_LaneInfo)]
+        L.bsort_server_lane_stats.restype = i
         L.bsort_server_stats.restype = i
         L.bsort_server_drain.argtypes = [vp, ctypes.c_double]
         L.bsort_server_drain.restype = i
@@ -291,7 +309,8 @@ class Handle:
                          "counted_bytes": int(r.counted_bytes)})
         return {"calls": int(p.num_calls), "launches": int(p.num_launches), "records": recs,
                 "finish_units": {"counting": int(p.finish_units_counting), "compare": int(p.finish_units_compare),
-                                 "lsd": int(p.finish_units_lsd)}}
+                                 "lsd": int(p.finish_units_lsd),
+                                 "counting_fast": int(p.finish_units_counting_fast)}}
 
     def set_tuning(self, key_bytes: int, tuning: dict = None) -> None:
         """MSD tuning for 4- or 8-byte keys (``bsort_handle_set_tuning``);
@@ -482,14 +501,21 @@ class Graph:
 
 
 class Server:
-    """Continuous-batching sort server (C ABI ``bsort_server_*``).  ``submit``
-    keeps a reference to each request's tensor until its completion is polled."""
+    """Continuous-batching sort server (C ABI ``bsort_server_*``), one lane
+    per entry of ``devices`` (default: the current device), each with
+    ``num_slots`` slots and its own ``hbm_budget_bytes``.  ``submit`` keeps a
+    reference to each request's tensor until its completion is polled."""
 
     def __init__(self, num_slots: int = 8, hbm_budget_bytes: int = 64 << 30, max_request_keys: int = 1 << 24,
-                 max_batch: int = 8, batch_keys: int = 1 << 20, mode: int = MODE_PINGPONG):
+                 max_batch: int = 8, batch_keys: int = 1 << 20, mode: int = MODE_PINGPONG, devices=None):
         cfg = _ServerConfig(num_slots, max_batch, hbm_budget_bytes, max_request_keys, batch_keys, int(mode), 0)
         srv = ctypes.c_void_p()
-        _check(lib().bsort_server_create(ctypes.byref(cfg), ctypes.byref(srv)), "bsort_server_create")
+        if devices is None:
+            _check(lib().bsort_server_create(ctypes.byref(cfg), ctypes.byref(srv)), "bsort_server_create")
+        else:
+            arr = (ctypes.c_int32 * len(devices))(*[int(d) for d in devices])
+            _check(lib().bsort_server_create_multi(ctypes.byref(cfg), arr, len(devices), ctypes.byref(srv)),
+                   "bsort_server_create_multi")
         self._s = srv
         self._live = {}
         self._buf = (_Completion * 4096)()
@@ -509,7 +535,7 @@ class Server:
                    "bsort_server_poll")
             for c in self._buf[: cnt.value]:
                 self._live.pop(int(c.tag), None)
-                out.append({"tag": int(c.tag), "status": int(c.status), "slot": int(c.slot),
+                out.append({"tag": int(c.tag), "status": int(c.status), "slot": int(c.slot), "lane": int(c.lane),
                             "t_submit_ns": int(c.t_submit_ns), "t_admit_ns": int(c.t_admit_ns),
                             "t_done_ns": int(c.t_done_ns)})
             if cnt.value < len(self._buf):
@@ -519,6 +545,17 @@ class Server:
         info = _ServerInfo()
         _check(lib().bsort_server_stats(self._s, ctypes.byref(info)), "bsort_server_stats")
         return {f: int(getattr(info, f)) for f, _ in _ServerInfo._fields_ if f != "pad"}
+
+    def lane_stats(self, lane: int) -> dict:
+        info = _LaneInfo()
+        _check(lib().bsort_server_lane_stats(self._s, int(lane), ctypes.byref(info)), "bsort_server_lane_stats")
+        return {f: int(getattr(info, f)) for f, _ in _LaneInfo._fields_}
+
+    def pick_device(self) -> int:
+        """Device of the least-loaded lane (``bsort_server_pick_device``)."""
+        d = ctypes.c_int32(0)
+        _check(lib().bsort_server_pick_device(self._s, ctypes.byref(d)), "bsort_server_pick_device")
+        return int(d.value)
 
     def pause(self, paused: bool = True) -> None:
         _check(lib().bsort_server_pause(self._s, int(bool(paused))), "bsort_server_pause")
@@ -548,6 +585,19 @@ def bsort_keys_partial_ws(handle: Handle, keys, workspace, levels: int, descendi
                                        ctypes.c_void_p(workspace.data_ptr()),
                                        workspace.numel() * workspace.element_size(), _stream_ptr(stream)),
            "bsort_keys_partial_ws")
+
+
+def top_digit_counts(keys, bits: int, descending: bool = False, stream=None):
+    """Keys per value of the top ``bits`` bits of their sort-order code
+    (``bsort_top_digit_counts``): an int64 tensor of 2^bits counts on the
+    keys' device; digit d's keys precede digit d + 1's in the sorted output."""
+    import torch
+    _device_tensor(keys)
+    counts = torch.empty(1 << int(bits), dtype=torch.int64, device=keys.device)
+    _check(lib().bsort_top_digit_counts(ctypes.c_void_p(keys.data_ptr()), keys.numel(), _dtype_code(keys.dtype),
+                                        int(bool(descending)), int(bits), ctypes.c_void_p(counts.data_ptr()),
+                                        _stream_ptr(stream)), "bsort_top_digit_counts")
+    return counts
 
 
 def selftest_bounded_wait(stream=None) -> int:

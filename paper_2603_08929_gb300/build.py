@@ -19,7 +19,7 @@ OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libbsort.so")
 
 SOURCES = ["api.cu", "kernels_msd.cu", "kernels_inplace.cu", "kernels_count.cu", "kernels_pairs.cu", "noalloc.cu",
-           "serve.cu"]
+           "serve.cu", "kernels_dist.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

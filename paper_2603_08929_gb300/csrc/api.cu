@@ -837,6 +837,24 @@ bsort_status bsort_keys_partial_ws(bsort_handle *handle, void *keys, size_t n, b
     return rs;
 }
 
+bsort_status bsort_top_digit_counts(const void *keys, size_t n, bsort_dtype dt, int descending, int bits,
+                                    uint64_t *d_counts, void *stream) {
+    DtypeInfo di;
+    if (!dtype_info(dt, &di)) return BSORT_ERR_INVALID_ARG;
+    if (bits < 1 || bits > kDigitCountsMaxBits || bits > di.bytes * 8 || !d_counts) return BSORT_ERR_INVALID_ARG;
+    if (n > 0 && !keys) return BSORT_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(keys) % di.bytes || reinterpret_cast<uintptr_t>(d_counts) % 8)
+        return BSORT_ERR_MISALIGNED;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(d_counts, 0, sizeof(uint64_t) << bits, st) != cudaSuccess) return BSORT_ERR_CUDA;
+    if (n == 0) return BSORT_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return BSORT_ERR_CUDA;
+    launch_digit_counts(keys, di.bytes, n, codec_for(di, descending), bits,
+                        reinterpret_cast<unsigned long long *>(d_counts), st, num_sms_of(dev));
+    return cudaGetLastError() == cudaSuccess ? BSORT_OK : BSORT_ERR_CUDA;
+}
+
 bsort_status bsort_selftest_bounded_wait(void *stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     uint32_t *d = nullptr;
@@ -904,6 +922,7 @@ bsort_status bsort_handle_get_profile(bsort_handle *handle, bsort_profile *out) 
         out->finish_units_counting += ctls[c].fin_counting;
         out->finish_units_compare += ctls[c].fin_compare;
         out->finish_units_lsd += ctls[c].n_fb;
+        out->finish_units_counting_fast += ctls[c].fin_fast;
     }
     const int nrec = handle->rec.count;
     for (int i = 0; i < nrec; ++i) {

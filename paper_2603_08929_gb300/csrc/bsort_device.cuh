@@ -57,13 +57,15 @@ struct Chunk {
 };
 
 // A run of keys (one or several adjacent small buckets) sorted entirely in
-// shared memory and written, decoded, to its final place.
+// shared memory and written, decoded, to its final place.  Its keys agree on
+// every bit at or above `vbits` (0: not known).
 struct Unit {
     uint64_t start;
     uint32_t len;
     uint8_t src;
     uint8_t raw;
-    uint8_t pad[2];
+    uint8_t vbits;
+    uint8_t pad;
 };
 
 // A run of identical keys written without reading (value is encoded).
@@ -107,6 +109,7 @@ struct Ctl {
     unsigned long long fill_keys;
     unsigned long long raw_reads;                 // keys read while still raw (diagnostic)
     unsigned long long fin_counting, fin_compare; // finish units by method (diagnostic)
+    unsigned long long fin_fast;                  // of fin_counting: the vector-load counting pass
     uint32_t n_big, n_stripes, n_slots, ip_pad;   // in-place lists of the current level
     unsigned long long aux_used;                  // in-place: largest auxiliary bytes any level used
 };

@@ -134,6 +134,13 @@ struct CountWork {
     uint32_t grid16;              // CTAs of the 16-bit histogram (at most one per SM)
 };
 
+// Multi-GPU sort of one array: counts[d] += number of keys whose encoded
+// top `bits` bits equal d (1 <= bits <= kDigitCountsMaxBits, bits <= key
+// bits); `counts` holds 2^bits entries, zeroed by the caller.
+constexpr int kDigitCountsMaxBits = 12;
+void launch_digit_counts(const void *keys, int key_bytes, uint64_t n, const Codec &codec, int bits,
+                         unsigned long long *counts, cudaStream_t st, int num_sms);
+
 void launch_count8(const CountWork &cw, cudaStream_t st, Recorder &rec, int num_sms);
 void launch_count16(const CountWork &cw, cudaStream_t st, Recorder &rec, int num_sms);
 

@@ -465,7 +465,8 @@ __global__ void k_init(Work wk, uint32_t n_chunks0, int direct_unit) {
             u.len = static_cast<uint32_t>(wk.n);
             u.src = 0;
             u.raw = 1;
-            u.pad[0] = u.pad[1] = 0;
+            u.vbits = 0;
+            u.pad = 0;
             wk.units[0] = u;
             c->n_units = 1;
             c->finish_keys = wk.n;
@@ -529,7 +530,8 @@ __global__ void k_seg_init(Work wk, const uint64_t *__restrict__ off, uint32_t n
             un.len = static_cast<uint32_t>(len);
             un.src = 0;
             un.raw = 1;
-            un.pad[0] = un.pad[1] = 0;
+            un.vbits = 0;
+            un.pad = 0;
             wk.units[u] = un;
             continue;
         }
@@ -937,7 +939,9 @@ __global__ void __launch_bounds__(THREADS) k_classify(Work wk, int level) {
                 un.len = ulen;
                 un.src = static_cast<uint8_t>(dst);
                 un.raw = 0;
-                un.pad[0] = un.pad[1] = 0;
+                // one child agrees above the digit; a merged group above the parent's bits
+                un.vbits = static_cast<uint8_t>(head ? b.h : hc);
+                un.pad = 0;
                 wk.units[sh_bases[0] + slot] = un;
             }
             __syncthreads();
@@ -1228,11 +1232,15 @@ constexpr size_t scatter_smem() {
     return scatter_pre_offset<K, THREADS, ITEMS, CHUNK_TILES, NB>() + 3 * sizeof(ScatterPre<NB>);
 }
 
-// Shared-memory layout of k_finish.  Two alternatives share the first region:
+// Shared-memory layout of k_finish.  Three alternatives share the first region:
 //   counting path: words[sb] (u64: sixteen 4-bit counters, one per value of
 //                  the unit's low 4 varying bits, in sub-bucket sb of the bits
 //                  above), totals[sb] and starts[sb] (u16), and the output
 //                  staging buffer over the words once positions are known;
+//   fast counting path (keys known to agree above bit 16): the same words,
+//                  then fstarts[sb] (u16) over the totals and the output
+//                  staging of the keys' low 16 bits, stage16[TILE + V], from
+//                  the starts on;
 //   compare path:  keys[TILE] then the split counters cnt[split_pad(d)].
 // The per-warp AND/OR slots and the scan scratch follow the shared region.
 template <typename K, int THREADS, int ITEMS>
@@ -1245,10 +1253,14 @@ struct FinLayout {
     static constexpr size_t kTotals = kWords + 8 * kSplitCap;     // u16[kSplitCap]
     static constexpr size_t kStarts = kTotals + 2 * kSplitCap;    // u16[kSplitCap]
     static constexpr size_t kNibEnd = kStarts + 2 * kSplitCap;
+    static constexpr size_t kFStarts = kTotals;                   // u16[kSplitCap]
+    static constexpr size_t kStage16 = kStarts;                   // u16[kTile + V]
+    static constexpr size_t kFastEnd = kStage16 + 2 * (kTile + V);
     static constexpr size_t kStage = kWords;                      // K[kTile + V]
     static constexpr size_t kCnt = sizeof(K) * kTile;
     static constexpr size_t kCmpEnd = kCnt + 4 * kPadded;
-    static constexpr size_t kShared = ((kNibEnd > kCmpEnd ? kNibEnd : kCmpEnd) + 15) & ~size_t(15);
+    static constexpr size_t kShared0 = kNibEnd > kCmpEnd ? kNibEnd : kCmpEnd;
+    static constexpr size_t kShared = ((kShared0 > kFastEnd ? kShared0 : kFastEnd) + 15) & ~size_t(15);
     static constexpr size_t kTa = kShared;
     static constexpr size_t kTo = kTa + sizeof(K) * WARPS;
     static constexpr size_t kScan = kTo + sizeof(K) * WARPS;
@@ -1257,6 +1269,195 @@ struct FinLayout {
     static_assert(sizeof(K) * (kTile + V) <= kTotals, "staging overlaps only the counter words");
     static_assert(kSplitCap == 16 * THREADS, "the scan gives each thread 16 sub-buckets");
 };
+
+// Counting finish of a unit whose keys agree on every bit at or above vb
+// (8 <= vb <= 16, 16-byte aligned buffers): the keys' low vb bits f are the
+// whole sort key.  Keys arrive as 16-byte vectors; one shared atomic per key
+// on a 4-bit counter of (sub-bucket f >> 4, low value f & 15) gives its
+// arrival rank; multiplying a sub-bucket's counter word by 0x1111... leaves
+// in nibble i the count of the values below i and in the top nibble the
+// sub-bucket's total (exact while the total is under 16, which the sum of the
+// totals confirms: a larger total always reads smaller); the totals' scan and
+// those nibbles place every key.  The low bits are staged as u16 and the
+// output rebuilt from the unit's common upper bits, decoded by one xor (the
+// key's top bit lies in the common part).  Expects the counter words zero and
+// leaves them zero.  Returns false with nothing written when a counter would
+// overflow or a sub-bucket holds 16 keys or more (counter words then dirty).
+template <typename K, int THREADS, int ITEMS>
+__device__ __forceinline__ bool finish_count_fast(const Work &wk, const Unit &un, int vb) {
+    using FL = FinLayout<K, THREADS, ITEMS>;
+    constexpr int V = FL::V;
+    constexpr int NV = ITEMS / V;  // 16-byte vectors per thread
+    static_assert(ITEMS % V == 0, "whole vectors per thread");
+    static_assert(kSplitCap == 16 * THREADS, "one thread scans 16 sub-buckets");
+    uint32_t *w32 = reinterpret_cast<uint32_t *>(g_dyn_smem + FL::kWords);
+    uint16_t *fst = reinterpret_cast<uint16_t *>(g_dyn_smem + FL::kFStarts);
+    uint16_t *stage = reinterpret_cast<uint16_t *>(g_dyn_smem + FL::kStage16);
+    uint32_t *scan_tmp = reinterpret_cast<uint32_t *>(g_dyn_smem + FL::kScan);
+    const int t = threadIdx.x;
+    const K *__restrict__ src = src_of<K>(wk, un.src);
+    const int len = static_cast<int>(un.len);
+    const uint64_t wstart = un.start - un.start % V;
+    const int lo_r = static_cast<int>(un.start - wstart);
+    const int hi_r = lo_r + len;
+    const int nvec = (hi_r + V - 1) / V;
+    const int rows = (nvec + THREADS - 1) / THREADS;  // vector rows in use (block-uniform, <= NV)
+    const uint32_t fmask = (1u << vb) - 1u;
+    const K common = src[un.start] & ~static_cast<K>(fmask);  // encoded bits shared by the unit
+    // every load first (nothing between them, so all are in flight at once),
+    // then the counting atomics; fr[i] = f | rank << 16 | valid << 20.  Rows
+    // past the unit's last vector are skipped by block-uniform branches.
+    uint32_t fr[ITEMS];
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) fr[i] = 0;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        if (j < rows) {
+            const int q = j * THREADS + t;
+            K kk[V];
+            uint32_t ok = 0;
+#pragma unroll
+            for (int e = 0; e < V; ++e) kk[e] = 0;
+            if (q < nvec) {
+                const int r0 = q * V;
+                if (r0 >= lo_r && r0 + V <= hi_r) {
+                    const uint4 v = *reinterpret_cast<const uint4 *>(src + wstart + r0);
+                    memcpy(kk, &v, 16);
+                    ok = (1u << V) - 1u;
+                } else {
+#pragma unroll
+                    for (int e = 0; e < V; ++e) {
+                        const bool in = r0 + e >= lo_r && r0 + e < hi_r;
+                        if (in) kk[e] = src[wstart + r0 + e];
+                        ok |= static_cast<uint32_t>(in) << e;
+                    }
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < V; ++e)
+                fr[j * V + e] = (static_cast<uint32_t>(kk[e]) & fmask) | (((ok >> e) & 1u) << 20);
+        }
+    }
+    uint32_t ovf = 0;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        if (j < rows) {
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                const uint32_t v = fr[j * V + e];
+                if (v >> 20) {
+                    const uint32_t f = v & 0xffffu;
+                    const int sh = static_cast<int>(f & 7u) << 2;
+                    const uint32_t old = atomicAdd(&w32[f >> 3], 1u << sh);
+                    const uint32_t r = (old >> sh) & 15u;
+                    ovf |= r + 1u;  // bit 4 set iff r == 15
+                    fr[j * V + e] = v | (r << 16);
+                }
+            }
+        }
+    }
+    if (__syncthreads_or(ovf & 16u)) return false;
+    // counter words to exclusive prefix nibbles in place, 32-bit halves: the
+    // low half (values 0-7) times 0x11111111 holds in nibble i the keys of
+    // values <= i and in its top nibble the half's total s; the high half
+    // times 0x11111111 plus s times 0x11111111 continues the count, its top
+    // nibble the sub-bucket's total (exact while under 16; a larger total
+    // always reads smaller, so the sum over the unit exposes it).  Thread t
+    // owns sub-buckets [16t, 16t + 16), visited from pair (e + t) % 8 on so
+    // that the eight threads of one shared-memory phase touch eight
+    // different 16-byte bank groups.
+    constexpr uint32_t kOnes = 0x11111111u;
+    const int nsb = 1 << (vb - 4);
+    const bool owner = 16 * t < nsb;
+    uint64_t tops = 0;
+    uint32_t sum = 0;
+    if (owner) {
+        uint4 *wv = reinterpret_cast<uint4 *>(w32) + 8 * t;
+#pragma unroll
+        for (int ee = 0; ee < 8; ++ee) {
+            const int e = (ee + t) & 7;
+            const uint4 q = wv[e];
+            const uint32_t l0 = q.x * kOnes, s0 = l0 >> 28, h0 = q.y * kOnes + s0 * kOnes, t0 = h0 >> 28;
+            const uint32_t l1 = q.z * kOnes, s1 = l1 >> 28, h1 = q.w * kOnes + s1 * kOnes, t1 = h1 >> 28;
+            tops |= static_cast<uint64_t>(t0 | (t1 << 4)) << (8 * e);
+            sum += t0 + t1;
+            wv[e] = make_uint4(l0 << 4, (h0 << 4) | s0, l1 << 4, (h1 << 4) | s1);
+        }
+    }
+    uint32_t total;
+    uint32_t run = block_exclusive_scan<THREADS>(sum, scan_tmp, total);
+    if (total != static_cast<uint32_t>(len)) return false;  // a sub-bucket of 16 or more keys
+    if (owner) {
+        uint32_t st[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const uint32_t a = run;
+            run += static_cast<uint32_t>(tops >> (8 * e)) & 15u;
+            st[e] = a | (run << 16);
+            run += static_cast<uint32_t>(tops >> (8 * e + 4)) & 15u;
+        }
+        uint4 *sv = reinterpret_cast<uint4 *>(fst) + 2 * t;
+        sv[0] = make_uint4(st[0], st[1], st[2], st[3]);
+        sv[1] = make_uint4(st[4], st[5], st[6], st[7]);
+    }
+    __syncthreads();
+    // positions: sub-bucket start + keys of lower low values + arrival rank
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        if (j < rows) {
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                const uint32_t v = fr[j * V + e];
+                if (v >> 20) {
+                    const uint32_t f = v & 0xffffu;
+                    const int sh = static_cast<int>(f & 7u) << 2;
+                    const uint32_t pos = fst[f >> 4] + ((w32[f >> 3] >> sh) & 15u) + ((v >> 16) & 15u);
+                    if (pos < static_cast<uint32_t>(len)) stage[lo_r + pos] = static_cast<uint16_t>(f);
+                    else bad = true;
+                }
+            }
+        }
+    }
+    if (bad) set_error(wk.ctl, kErrBounds);
+    __syncthreads();
+    // counters back to zero for the next unit, then the keys out
+    for (int i = t; i < nsb / 2; i += THREADS) reinterpret_cast<uint4 *>(w32)[i] = make_uint4(0, 0, 0, 0);
+    const K base = decode_key(common, wk.codec);  // decode flips by the top bit, which f never holds
+    K *__restrict__ dstp = static_cast<K *>(wk.keys) + un.start;
+    if (wk.keys_vec_ok) {
+        const int a_i = (V - lo_r) % V;  // first key of a whole 16-byte group of the output
+        const int nout = (len - a_i) > 0 ? (len - a_i) / V : 0;
+        const int b_i = a_i + nout * V;
+        for (int q = t; q < nout; q += THREADS) {
+            const uint16_t *sp = stage + lo_r + a_i + q * V;
+            K kv[V];
+            if (V == 4) {
+                const uint2 h = *reinterpret_cast<const uint2 *>(sp);
+                kv[0] = base ^ static_cast<K>(h.x & 0xffffu);
+                kv[1 % V] = base ^ static_cast<K>(h.x >> 16);
+                kv[2 % V] = base ^ static_cast<K>(h.y & 0xffffu);
+                kv[3 % V] = base ^ static_cast<K>(h.y >> 16);
+            } else {
+                const uint32_t h = *reinterpret_cast<const uint32_t *>(sp);
+                kv[0] = base ^ static_cast<K>(h & 0xffffu);
+                kv[1 % V] = base ^ static_cast<K>(h >> 16);
+            }
+            reinterpret_cast<uint4 *>(dstp + a_i)[q] = *reinterpret_cast<const uint4 *>(kv);
+        }
+        if (t < 2 * V) {
+            const int i = t < V ? t : b_i + (t - V);
+            if ((t < V && i < a_i && i < len) || (t >= V && i < len)) dstp[i] = base ^ static_cast<K>(stage[lo_r + i]);
+        }
+    } else {
+        for (int i = t; i < len; i += THREADS) dstp[i] = base ^ static_cast<K>(stage[lo_r + i]);
+    }
+    if (t == 0) {
+        atomicAdd(&wk.ctl->fin_counting, 1ull);
+        atomicAdd(&wk.ctl->fin_fast, 1ull);
+    }
+    return true;
+}
 
 // Sorts every unit in shared memory and writes it, decoded, to its final
 // place.  With at most 16 varying bits (and enough keys to fill the
@@ -1294,12 +1495,28 @@ __global__ void __launch_bounds__(THREADS, 4) k_finish(Work wk) {
     Unit *next = reinterpret_cast<Unit *>(g_dyn_smem + FL::kNext);  // descriptors, double-buffered
     if (t == 0 && blockIdx.x < nu) cp_async16(&next[0], &wk.units[blockIdx.x]);
     int it = 0;
+    bool clean = false;  // every counter word of the fast counting path is zero
     for (uint32_t u = blockIdx.x; u < nu; u += gridDim.x, ++it) {
         if (t == 0) cp_async_wait_all();
         __syncthreads();
         const Unit un = next[it & 1];
         if (t == 0 && u + gridDim.x < nu) cp_async16(&next[(it + 1) & 1], &wk.units[u + gridDim.x]);
         const bool raw = un.raw;
+        {
+            const int vb = un.vbits;
+            const bool vec = un.src ? true : wk.keys_vec_ok;
+            if (!raw && vec && vb >= 8 && vb <= 16 && (1 << (vb - 4)) <= 4 * static_cast<int>(un.len)) {
+                if (!clean) {
+                    uint4 *z = reinterpret_cast<uint4 *>(g_dyn_smem + FL::kWords);
+                    for (int i = t; i < kSplitCap / 2; i += THREADS) z[i] = make_uint4(0, 0, 0, 0);
+                    __syncthreads();
+                }
+                clean = finish_count_fast<K, THREADS, ITEMS>(wk, un, vb);
+                if (clean) continue;
+                __syncthreads();  // the general path below reuses the counter words
+            }
+        }
+        clean = false;
         const K *__restrict__ src = src_of<K>(wk, un.src) + un.start;
         K *__restrict__ dstp = out + un.start;
         const int len = static_cast<int>(un.len);

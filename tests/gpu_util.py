@@ -18,6 +18,7 @@ def gpu_sort(x, descending=False):
 
 def assert_bit_exact(got, want, what=""):
     assert got.dtype == want.dtype and got.shape == want.shape, what
+    got, want = np.ascontiguousarray(got), np.ascontiguousarray(want)
     g = got.view(np.uint8).reshape(got.size, -1) if got.size else got.view(np.uint8)
     w = want.view(np.uint8).reshape(want.size, -1) if want.size else want.view(np.uint8)
     if not np.array_equal(g, w):

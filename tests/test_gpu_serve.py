@@ -92,3 +92,74 @@ def test_budget_limits_requests_in_flight():
     with pytest.raises(bs.BsortError):
         srv.submit(to_device(np.zeros(n + 1, np.int32)))  # beyond max_request_keys
     srv.close()
+
+
+def test_two_lanes_share_the_load():
+    """Two lanes on this one GPU (the device listed twice): requests go to
+    the less loaded lane of their device, both lanes sort, each lane keeps
+    its own budget, and every result equals the oracle's."""
+    import torch
+    import paper_2603_08929_gb300 as bs
+    reqs = request_mix(80, 2)
+    budget = 48 << 20
+    srv = bs.Server(num_slots=2, hbm_budget_bytes=budget, max_request_keys=1 << 20, max_batch=4,
+                    batch_keys=1 << 16, devices=[0, 0])
+    assert srv.stats()["num_lanes"] == 2
+    assert srv.pick_device() == 0
+    bufs = [to_device(x) for x, _ in reqs]
+    torch.cuda.synchronize()
+    srv.pause(True)  # all queued first: the dispatch then depends on queued bytes only
+    for i, (b, (_, desc)) in enumerate(zip(bufs, reqs)):
+        srv.submit(b, descending=desc, tag=i)
+    lanes = [srv.lane_stats(0), srv.lane_stats(1)]
+    assert all(ln["queued_bytes"] > 0 for ln in lanes), lanes
+    srv.pause(False)
+    srv.drain(120)
+    done = srv.poll()
+    assert sorted(c["tag"] for c in done) == list(range(len(reqs)))
+    assert all(c["status"] == 0 for c in done)
+    assert {c["lane"] for c in done} == {0, 1}
+    for ln in (srv.lane_stats(0), srv.lane_stats(1)):
+        assert ln["completed"] > 0 and ln["queued_bytes"] == 0 and ln["in_flight_bytes"] == 0
+        assert ln["device"] == 0 and ln["budget_bytes"] == budget
+    for i, b in enumerate(bufs):
+        x, desc = reqs[i]
+        assert_bit_exact(b.cpu().numpy(), O.bsort(x, descending=desc), "request %d (%s)" % (i, x.dtype))
+    srv.close()
+
+
+def test_grouped_requests_take_one_segmented_sort():
+    """Small requests of one dtype and direction admitted together share one
+    segmented sort: fewer launches than one plain sort each, same bytes."""
+    import torch
+    import paper_2603_08929_gb300 as bs
+    rng = np.random.default_rng(7)
+    reqs = []
+    for i in range(48):
+        dt = ["int32", "float32", "float64", "uint64"][i % 4]
+        n = int(2 ** (10 + 6 * rng.random()))
+        reqs.append((W.make("float_edge" if dt.startswith("float") else "uniform", dt, n, seed=700 + i), i % 8 == 0))
+
+    def serve(max_batch):
+        srv = bs.Server(num_slots=2, max_request_keys=1 << 20, max_batch=max_batch, batch_keys=1 << 18)
+        bufs = [to_device(x) for x, _ in reqs]
+        torch.cuda.synchronize()
+        srv.pause(True)
+        for i, (b, (_, desc)) in enumerate(zip(bufs, reqs)):
+            srv.submit(b, descending=desc, tag=i)
+        srv.pause(False)
+        srv.drain(120)
+        done = srv.poll()
+        assert len(done) == len(reqs) and all(c["status"] == 0 for c in done)
+        st = srv.stats()
+        srv.close()
+        return [b.cpu().numpy() for b in bufs], st
+
+    grouped, st_g = serve(16)
+    plain, st_p = serve(1)
+    assert st_g["grouped_sorts"] > 0 and st_p["grouped_sorts"] == 0
+    assert st_g["launches"] < st_p["launches"] / 2, (st_g["launches"], st_p["launches"])
+    for i, (x, desc) in enumerate(reqs):
+        want = O.bsort(x, descending=desc)
+        assert_bit_exact(grouped[i], want, "grouped request %d" % i)
+        assert_bit_exact(plain[i], want, "plain request %d" % i)
