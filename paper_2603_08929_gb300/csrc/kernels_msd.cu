@@ -30,6 +30,15 @@ constexpr uint32_t kCmpMaxBucket = 64;
 constexpr int kSplitBits = 12;  // finish split: up to 4096 sub-buckets per unit
 constexpr int kSplitCap = 1 << kSplitBits;
 
+// Programmatic dependent launch: every kernel of the sequence is launched
+// with programmatic stream serialization, so it may be scheduled while its
+// predecessor still runs; it first waits for the predecessor's completion
+// (and memory) and then lets its own successor start launching.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 template <int THREADS>
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *tmp, uint32_t &total) {
     constexpr int WARPS = THREADS / 32;
@@ -455,6 +464,7 @@ __device__ __forceinline__ K *dst_of(const Work &wk, int src) {
 // ---------------------------------------------------------------------------
 
 __global__ void k_init(Work wk, uint32_t n_chunks0, int direct_unit) {
+    pdl_enter();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         Ctl *c = wk.ctl;
         uint32_t *words = reinterpret_cast<uint32_t *>(c);
@@ -500,6 +510,7 @@ __global__ void k_init(Work wk, uint32_t n_chunks0, int direct_unit) {
 
 // Clears the work lists and counters.
 __global__ void k_zero_ctl(Work wk) {
+    pdl_enter();
     uint32_t *words = reinterpret_cast<uint32_t *>(wk.ctl);
     for (size_t i = threadIdx.x; i < sizeof(Ctl) / 4; i += blockDim.x) words[i] = 0;
 }
@@ -509,6 +520,7 @@ __global__ void k_zero_ctl(Work wk) {
 // keys); segments of 0 or 1 key are already sorted.  Offsets that decrease
 // or pass n set the bounds error and the segment is skipped.
 __global__ void k_seg_init(Work wk, const uint64_t *__restrict__ off, uint32_t nseg) {
+    pdl_enter();
     const uint64_t vk = 128u / static_cast<uint32_t>(wk.w);
     for (uint32_t sg = blockIdx.x * blockDim.x + threadIdx.x; sg < nseg; sg += gridDim.x * blockDim.x) {
         const uint64_t a = off[sg], b = off[sg + 1];
@@ -638,6 +650,7 @@ __device__ __forceinline__ void hist_range(const K *__restrict__ src, uint64_t l
 // histogram column are written.
 template <typename K, int THREADS, int NB>
 __global__ void __launch_bounds__(THREADS) k_hist(Work wk, int level) {
+    pdl_enter();
     constexpr int WARPS = THREADS / 32;
     constexpr int ROWS = NB <= kBins ? WARPS : 4;
     __shared__ uint32_t sh[ROWS * NB];
@@ -689,6 +702,7 @@ __global__ void __launch_bounds__(THREADS) k_hist(Work wk, int level) {
 // (in place), and the bucket's digit total into bucket_base[bucket][d].
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS) k_colscan(Work wk, int level) {
+    pdl_enter();
     __shared__ uint32_t tmp[THREADS / 32 + 1];
     __shared__ int itmp[THREADS / 32 + 1];
     __shared__ unsigned long long sm_excl[THREADS];
@@ -701,13 +715,23 @@ __global__ void __launch_bounds__(THREADS) k_colscan(Work wk, int level) {
     uint32_t *col = wk.hist + static_cast<size_t>(d) * wk.max_chunks;
     unsigned long long carry_total = 0;  // unsegmented prefix before this block
     unsigned long long carry_seg = 0;    // unsegmented prefix at the latest segment head
+    // this step's chunk data was loaded during the previous step's scans
+    auto fetch = [&](uint32_t c, uint32_t &b, uint32_t &v, uint32_t &bp, uint32_t &bn) {
+        const bool in = c < nch;
+        b = in ? chunks[c].bucket : 0xffffffffu;
+        v = in ? col[c] : 0;
+        bp = in && c > 0 ? chunks[c - 1].bucket : 0xfffffffeu;
+        bn = in && c + 1 < nch ? chunks[c + 1].bucket : 0xfffffffeu;
+    };
+    uint32_t nb_, nv_, nbp_, nbn_;
+    fetch(threadIdx.x, nb_, nv_, nbp_, nbn_);
     for (uint32_t base = 0; base < nch; base += THREADS) {
         const uint32_t c = base + threadIdx.x;
         const bool in = c < nch;
-        const uint32_t b = in ? chunks[c].bucket : 0xffffffffu;
-        const uint32_t v = in ? col[c] : 0;
-        const bool head = in && (c == 0 || chunks[c - 1].bucket != b);
-        const bool last = in && (c + 1 == nch || chunks[c + 1].bucket != b);
+        const uint32_t b = nb_, v = nv_, bprev = nbp_, bnext = nbn_;
+        if (base + THREADS < nch) fetch(c + THREADS, nb_, nv_, nbp_, nbn_);
+        const bool head = in && (c == 0 || bprev != b);
+        const bool last = in && (c + 1 == nch || bnext != b);
         uint32_t block_total;
         const uint32_t ex = block_exclusive_scan<THREADS>(v, tmp, block_total);
         const unsigned long long ex_global = carry_total + ex;
@@ -734,7 +758,8 @@ __global__ void __launch_bounds__(THREADS) k_colscan(Work wk, int level) {
 // children that become buckets, with their start/len/h/src in the arguments.
 template <int THREADS>
 __device__ void emit_buckets(const Work &wk, int q, bool take, uint64_t start, uint64_t len, int h, int src, int raw,
-                             uint32_t *tmp, uint32_t *sh_choff, uint32_t *sh_slot, uint32_t *sh_bases) {
+                             uint32_t *tmp, uint32_t *sh_choff, uint32_t *sh_slot, uint32_t *sh_bases,
+                             unsigned long long *sh_cstart, unsigned long long *sh_cend) {
     // chunk boundaries sit on 16-byte boundaries of the buffer except the
     // bucket's own start, so every tile after the first is an aligned window
     const uint64_t vk = 128u / static_cast<uint32_t>(wk.w);
@@ -755,6 +780,8 @@ __device__ void emit_buckets(const Work &wk, int q, bool take, uint64_t start, u
     }
     sh_choff[threadIdx.x] = ch_off;
     sh_slot[threadIdx.x] = take ? slot_off : 0xffffffffu;
+    sh_cstart[threadIdx.x] = start;  // the children's extents, for the chunk records below
+    sh_cend[threadIdx.x] = start + len;
     __syncthreads();
     const uint32_t b0 = sh_bases[0], c0 = sh_bases[1];
     if (b0 != 0xffffffffu) {
@@ -783,12 +810,12 @@ __device__ void emit_buckets(const Work &wk, int q, bool take, uint64_t start, u
             }
             // children without chunks never satisfy choff <= k past the owner
             const int d = lo;
-            const Bucket &nbk = wk.buckets[q][b0 + sh_slot[d]];
+            const uint64_t cstart = sh_cstart[d], cend = sh_cend[d];
             const uint32_t i = k - sh_choff[d];
-            const uint64_t nb_base = nbk.start - nbk.start % vk;
-            const uint64_t cs = i == 0 ? nbk.start : nb_base + static_cast<uint64_t>(i) * wk.chunk_keys;
+            const uint64_t nb_base = cstart - cstart % vk;
+            const uint64_t cs = i == 0 ? cstart : nb_base + static_cast<uint64_t>(i) * wk.chunk_keys;
             const uint64_t ce_lim = nb_base + static_cast<uint64_t>(i + 1) * wk.chunk_keys;
-            const uint64_t ce = ce_lim < nbk.start + nbk.len ? ce_lim : nbk.start + nbk.len;
+            const uint64_t ce = ce_lim < cend ? ce_lim : cend;
             Chunk ch;
             ch.start = cs;
             ch.len = static_cast<uint32_t>(ce - cs);
@@ -825,11 +852,13 @@ __device__ void emit_fill(const Work &wk, uint64_t start, uint64_t len, uint64_t
 // merged small children ends at a page boundary).
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS) k_classify(Work wk, int level) {
+    pdl_enter();
     static_assert(THREADS == kBins, "one thread per digit of a page");
     __shared__ unsigned long long ta[THREADS / 32], to[THREADS / 32];
     __shared__ unsigned long long tmp64[THREADS / 32 + 1];
     __shared__ uint32_t tmp[THREADS / 32 + 1];
     __shared__ uint32_t sh_choff[THREADS], sh_slot[THREADS], sh_bases[2];
+    __shared__ unsigned long long sh_cstart[THREADS], sh_cend[THREADS];
     __shared__ int itmp[THREADS / 32 + 1], sh_i2[THREADS];
     __shared__ uint32_t sh_u[THREADS], sh_u2[THREADS];
     const int p = level & 1, q = p ^ 1;
@@ -839,9 +868,27 @@ __global__ void __launch_bounds__(THREADS) k_classify(Work wk, int level) {
     for (uint32_t i = blockIdx.x; i < nb; i += gridDim.x) {
         const Bucket b = wk.buckets[p][i];
         unsigned long long a = ~0ull, o = 0;
-        for (uint32_t c = b.first_chunk + threadIdx.x; c < b.first_chunk + b.num_chunks; c += THREADS) {
-            a &= wk.chunk_and[c];
-            o |= wk.chunk_or[c];
+        {
+            // eight chunks per thread in flight at once (a big bucket has thousands)
+            const uint32_t c_end = b.first_chunk + b.num_chunks;
+            uint32_t c = b.first_chunk + threadIdx.x;
+            for (; c + 7 * THREADS < c_end; c += 8 * THREADS) {
+                unsigned long long ra[8], ro[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    ra[u] = wk.chunk_and[c + u * THREADS];
+                    ro[u] = wk.chunk_or[c + u * THREADS];
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    a &= ra[u];
+                    o |= ro[u];
+                }
+            }
+            for (; c < c_end; c += THREADS) {
+                a &= wk.chunk_and[c];
+                o |= wk.chunk_or[c];
+            }
         }
         block_and_or<THREADS>(a, o, ta, to);
         if (threadIdx.x == 0) atomicAdd(&wk.ctl->hist_keys[level], static_cast<unsigned long long>(b.len));
@@ -860,7 +907,7 @@ __global__ void __launch_bounds__(THREADS) k_classify(Work wk, int level) {
             // the digit is constant: re-open the bucket at its highest varying bit
             if (threadIdx.x == 0) wk.buckets[p][i].scatter = 0;
             emit_buckets<THREADS>(wk, q, threadIdx.x == 0, b.start, b.len, hb + 1, b.src, b.raw, tmp, sh_choff,
-                                  sh_slot, sh_bases);
+                                  sh_slot, sh_bases, sh_cstart, sh_cend);
             continue;
         }
         if (threadIdx.x == 0) {
@@ -887,7 +934,8 @@ __global__ void __launch_bounds__(THREADS) k_classify(Work wk, int level) {
                 const unsigned long long hi_mask = b.h >= 64 ? 0ull : (~0ull << b.h);
                 emit_fill(wk, base, tot, (a & hi_mask) | static_cast<unsigned long long>(d));
             }
-            emit_buckets<THREADS>(wk, q, big && hc > 0, base, tot, hc, dst, 0, tmp, sh_choff, sh_slot, sh_bases);
+            emit_buckets<THREADS>(wk, q, big && hc > 0, base, tot, hc, dst, 0, tmp, sh_choff, sh_slot, sh_bases,
+                                  sh_cstart, sh_cend);
             // Small children become finish units.  Children of at most
             // merge_cap / 4 keys ("tiny") merge with their tiny neighbours:
             // inside a run of adjacent tiny children (empty children do not
@@ -1056,6 +1104,7 @@ __host__ __device__ constexpr size_t scatter_pre_offset() {
 
 template <typename K, int THREADS, int ITEMS, int CHUNK_TILES, int NB>
 __global__ void __launch_bounds__(THREADS, 2) k_scatter(Work wk, int level) {
+    pdl_enter();
     using L = TileLoad<K, THREADS, ITEMS>;
     using Pre = ScatterPre<NB>;
     constexpr int TILE = THREADS * ITEMS;
@@ -1476,6 +1525,7 @@ __device__ __forceinline__ bool finish_count_fast(const Work &wk, const Unit &un
 // caller's encoding (an array or segment that fits one tile).
 template <typename K, int THREADS, int ITEMS>
 __global__ void __launch_bounds__(THREADS, 4) k_finish(Work wk) {
+    pdl_enter();
     using FL = FinLayout<K, THREADS, ITEMS>;
     K *sm_keys = reinterpret_cast<K *>(g_dyn_smem);
     K *ta = reinterpret_cast<K *>(g_dyn_smem + FL::kTa);
@@ -1788,6 +1838,7 @@ constexpr size_t finish_smem() {
 // then the decoded keys go to their final place.
 template <typename K, int THREADS, int ITEMS>
 __global__ void __launch_bounds__(THREADS, 4) k_finish_lsd(Work wk) {
+    pdl_enter();
     using L = TileLoad<K, THREADS, ITEMS>;
     constexpr int TILE = THREADS * ITEMS;
     constexpr int V = L::V;
@@ -1848,6 +1899,7 @@ constexpr size_t finish_lsd_smem() {
 
 template <typename K>
 __global__ void k_fill(Work wk) {
+    pdl_enter();
     if (wk.ctl->error) return;
     const uint32_t nf = wk.ctl->n_fills;
     K *out = static_cast<K *>(wk.keys);
@@ -1867,6 +1919,7 @@ __global__ void k_fill(Work wk) {
 // place in the caller's buffer as they are.
 template <typename K>
 __global__ void k_drain(Work wk, int level) {
+    pdl_enter();
     if (wk.ctl->error) return;
     const int p = level & 1;
     const uint32_t nb = wk.ctl->n_buckets[p];
@@ -1931,6 +1984,23 @@ bool tuning_valid(int key_bytes, const Tuning &t) {
     return true;
 }
 
+// Launches `kern` on `st` with programmatic stream serialization (the
+// kernel calls pdl_enter() before touching memory).
+template <typename... P, typename... A>
+void launch_pdl(void (*kern)(P...), unsigned grid, unsigned block, size_t smem, cudaStream_t st, A... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, static_cast<P>(args)...);
+}
+
 template <typename K>
 void msd_prepare() {
     constexpr int T = Cfg<K>::kThreads, I = Cfg<K>::kItems, CT = kMaxChunkTiles;
@@ -1960,41 +2030,41 @@ void msd_levels_and_finish(const Work &wk, cudaStream_t st, Recorder &rec, int n
     if (levels) {
         for (int level = 0; level < wk.stop_level; ++level) {
             rec.begin(BSORT_K_HIST, level);
-            if (wide) k_hist<K, 512, kWideBins><<<num_sms * 4, 512, 0, st>>>(wk, level);
-            else k_hist<K, 512, kBins><<<num_sms * 4, 512, 0, st>>>(wk, level);
+            if (wide) launch_pdl(k_hist<K, 512, kWideBins>, num_sms * 4, 512, 0, st, wk, level);
+            else launch_pdl(k_hist<K, 512, kBins>, num_sms * 4, 512, 0, st, wk, level);
             rec.end();
             rec.begin(BSORT_K_SCAN, level);
-            k_colscan<1024><<<1 << wk.radix_bits, 1024, 0, st>>>(wk, level);
+            launch_pdl(k_colscan<1024>, 1u << wk.radix_bits, 1024, 0, st, wk, level);
             rec.end();
             rec.begin(BSORT_K_CLASSIFY, level);
-            k_classify<kBins><<<num_sms * 4, kBins, 0, st>>>(wk, level);
+            launch_pdl(k_classify<kBins>, num_sms * 4, kBins, 0, st, wk, level);
             rec.end();
             if (wk.inplace) {
                 launch_ip_level<K>(wk, st, rec, num_sms, level);
             } else {
                 rec.begin(BSORT_K_SCATTER, level);
                 if (wide)
-                    k_scatter<K, T, I, CT, kWideBins>
-                        <<<num_sms * 2, T, scatter_smem<K, T, I, CT, kWideBins>(), st>>>(wk, level);
+                    launch_pdl(k_scatter<K, T, I, CT, kWideBins>, num_sms * 2, T, scatter_smem<K, T, I, CT, kWideBins>(),
+                               st, wk, level);
                 else
-                    k_scatter<K, T, I, CT, kBins><<<num_sms * 2, T, scatter_smem<K, T, I, CT, kBins>(), st>>>(wk, level);
+                    launch_pdl(k_scatter<K, T, I, CT, kBins>, num_sms * 2, T, scatter_smem<K, T, I, CT, kBins>(), st, wk, level);
                 rec.end();
             }
         }
     }
     if (levels && wk.stop_level < wk.levels) {
         rec.begin(BSORT_K_FILL, wk.stop_level);
-        k_drain<K><<<num_sms * 2, 256, 0, st>>>(wk, wk.stop_level);
+        launch_pdl(k_drain<K>, num_sms * 2, 256, 0, st, wk, wk.stop_level);
         rec.end();
     }
     rec.begin(BSORT_K_FINISH, -1);
-    k_finish<K, FT, FI><<<num_sms * 8, FT, finish_smem<K, FT, FI>(), st>>>(wk);
-    k_finish_lsd<K, FT, FI><<<num_sms * 4, FT, finish_lsd_smem<K, FT, FI>(), st>>>(wk);
+    launch_pdl(k_finish<K, FT, FI>, num_sms * 8, FT, finish_smem<K, FT, FI>(), st, wk);
+    launch_pdl(k_finish_lsd<K, FT, FI>, num_sms * 4, FT, finish_lsd_smem<K, FT, FI>(), st, wk);
     rec.more(1);
     rec.end();
     if (levels) {
         rec.begin(BSORT_K_FILL, -1);
-        k_fill<K><<<num_sms * 2, 256, 0, st>>>(wk);
+        launch_pdl(k_fill<K>, num_sms * 2, 256, 0, st, wk);
         rec.end();
     }
 }
