@@ -138,3 +138,45 @@ def sort_distributed(keys, descending: bool = False, group=None, bits: int = 12,
     ops.sort(mine, descending)
     start = int(np.sum(glob[: bounds[rank]]))
     return mine, start
+
+
+# ---- batched form: independent segments spread over the ranks ----------------
+
+def plan_segments(sizes, world: int) -> np.ndarray:
+    """Boundaries s[0..world] in segment indices: rank r sorts segments
+    [s[r], s[r+1]), a contiguous run whose keys are as close to r * N / world
+    as a segment boundary allows (the same closest-prefix rule as the digit
+    plan), so each rank's part is one slice of the batch buffer and no rank
+    holds more than N / world plus twice the largest segment."""
+    return plan_digit_ranges(np.asarray(sizes, dtype=np.int64), world)
+
+
+class LibrarySegmentOps:
+    """The device step of the batched form: one segmented sort."""
+
+    def sort_segments(self, keys, offsets, descending):
+        import torch
+        from . import bsort_keys_segmented
+        if keys.numel() > 1 and offsets.numel() > 1:
+            off = torch.as_tensor(offsets, dtype=torch.int64, device=keys.device)
+            bsort_keys_segmented(keys, off, descending=descending)
+
+
+def sort_segments_distributed(keys, offsets, descending: bool = False, group=None, ops=None):
+    """Sorts every segment [offsets[i], offsets[i+1]) of a batch that each rank
+    of ``group`` holds in full (``keys``, ``offsets``: the same on every rank;
+    the segments are independent, so no data moves between ranks).  This rank
+    sorts its planned run of segments in place in ``keys`` and returns the
+    run (first segment, end segment).  Whichever rank sorts a segment, its
+    bytes are those of the segment sorted alone."""
+    import torch.distributed as dist
+    ops = ops or LibrarySegmentOps()
+    off = np.asarray(offsets.cpu() if hasattr(offsets, "cpu") else offsets, dtype=np.int64)
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    s = plan_segments(np.diff(off), world)
+    a, b = int(s[rank]), int(s[rank + 1])
+    if b > a:
+        lo, hi = int(off[a]), int(off[b])
+        ops.sort_segments(keys[lo:hi], off[a:b + 1] - lo, descending)
+    return a, b

@@ -152,3 +152,73 @@ def test_gloo_ranks_sort_one_array(case, world):
     assert [r[1] for r in res] == list(np.concatenate(([0], np.cumsum(sizes)))[:-1])
     digits = np.bincount(oracle_digits(allx, case[4], case[5]), minlength=1 << case[5])
     assert max(sizes) <= allx.size / world + 2 * digits.max()
+
+
+# --- batched form: segments spread over gloo ranks -------------------------------
+
+class OracleSegmentOps:
+    def sort_segments(self, keys, offsets, descending):
+        import torch
+        x = keys.numpy()
+        for a, b in zip(offsets[:-1], offsets[1:]):
+            if b - a > 1:
+                x[a:b] = O.bsort(x[a:b].copy(), descending=descending)
+        keys.copy_(torch.from_numpy(x))
+
+
+def _batch(world_seed):
+    sizes = W.segment_sizes(world_seed, 300, 14)
+    sizes[::37] = 0
+    x = W.make("float_edge", "float32", int(sizes.sum()), seed=world_seed)
+    return x, np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+
+
+def _seg_rank(rank, world, port, q):
+    sys.path[:0] = [ROOT, os.path.join(ROOT, "tests")]
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import torch
+    import torch.distributed as dist
+    from paper_2603_08929_gb300 import distributed as D
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    x, off = _batch(5)
+    t = torch.from_numpy(x.copy())
+    a, b = D.sort_segments_distributed(t, off, descending=True, ops=OracleSegmentOps())
+    dist.destroy_process_group()
+    q.put((rank, a, b, t.numpy()[off[a]:off[b]].copy()))
+
+
+def test_plan_segments_balances_keys():
+    from paper_2603_08929_gb300.distributed import plan_segments
+    rng = np.random.default_rng(3)
+    for trial in range(200):
+        sizes = rng.integers(0, 1000, int(rng.integers(1, 200)))
+        world = int(rng.integers(1, 9))
+        s = plan_segments(sizes, world)
+        _brute_plan_ok(sizes, world, s)
+
+
+@pytest.mark.parametrize("world", [2, 4])
+def test_gloo_ranks_sort_a_batch(world):
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_seg_rank, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted((q.get(timeout=240) for _ in procs), key=lambda t: t[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    x, off = _batch(5)
+    # the runs tile the batch in rank order
+    assert res[0][1] == 0 and res[-1][2] == off.size - 1
+    assert all(res[i][2] == res[i + 1][1] for i in range(world - 1))
+    got = np.concatenate([r[3] for r in res])
+    want = x.copy()
+    for a, b in zip(off[:-1], off[1:]):
+        if b - a > 1:
+            want[a:b] = O.bsort(x[a:b].copy(), descending=True)
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+    sizes = np.diff(off)
+    assert max(off[r[2]] - off[r[1]] for r in res) <= sizes.sum() / world + 2 * sizes.max()

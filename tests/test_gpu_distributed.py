@@ -105,3 +105,44 @@ def test_sort_distributed(world):
         assert_bit_exact(np.concatenate([p[1] for p in parts]), O.bsort(allx, descending=case[3]), str(case))
         sizes = [p[1].size for p in parts]
         assert [p[0] for p in parts] == list(np.concatenate(([0], np.cumsum(sizes)))[:-1])
+
+
+def _seg_rank(rank, world, port, q):
+    sys.path[:0] = [ROOT, os.path.join(ROOT, "tests")]
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import torch
+    import torch.distributed as dist
+    from paper_2603_08929_gb300 import distributed as D
+    torch.cuda.set_device(0)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    sizes = W.segment_sizes(9, 2000, 16)
+    x = W.make("uniform", "int32", int(sizes.sum()), seed=9)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    t = torch.from_numpy(x).cuda()
+    a, b = D.sort_segments_distributed(t, off)
+    torch.cuda.synchronize()
+    dist.destroy_process_group()
+    q.put((rank, a, b, t.cpu().numpy()[off[a]:off[b]].copy()))
+
+
+@pytest.mark.parametrize("world", [1, 2])
+def test_sort_segments_distributed(world):
+    """The batched form split over ranks by key count: each rank sorts its run
+    of segments with the segmented sort; every segment equals the oracle's."""
+    import multiprocessing as mp
+    from gpu_util import oracle_segments
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_seg_rank, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted((q.get(timeout=600) for _ in procs), key=lambda t: t[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    sizes = W.segment_sizes(9, 2000, 16)
+    x = W.make("uniform", "int32", int(sizes.sum()), seed=9)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    assert res[0][1] == 0 and res[-1][2] == sizes.size
+    assert_bit_exact(np.concatenate([r[3] for r in res]), oracle_segments(x, off, False), "segments over ranks")
