@@ -109,6 +109,10 @@ def _load():
         lib.orc_multiset_digest.restype = None
         lib.orc_stable_argsort.argtypes = [u64p, sz, i, i, i, i, i, u64p]
         lib.orc_stable_argsort.restype = i
+        lib.orc_bsort2.argtypes = [u64p, u64p, sz, i, i, i, i, i, i, u64p]
+        lib.orc_bsort2.restype = i
+        lib.orc_cmp2.argtypes = [ctypes.c_uint64] * 4 + [i, i]
+        lib.orc_cmp2.restype = i
         _lib = lib
     return _lib
 
@@ -227,3 +231,42 @@ def stable_argsort(x: np.ndarray, descending: bool = False) -> np.ndarray:
     stable sort of ``x`` under the paper's order applies; ``x[p]`` is the
     sorted keys and ``v[p]`` the values carried along."""
     return stable_argsort_words(to_words(x), FORMATS[np.dtype(x.dtype)], descending)
+
+
+# --- keys of two words (up to 128 bits): unsigned and signed integers --------
+#
+# A key array is a uint64 array of shape (n, 2): column 0 the low word, column
+# 1 the high word (the little-endian layout of a 16-byte integer), so the same
+# memory is the GPU library's 128-bit keys.
+
+U128 = KeyFormat(128, UNSIGNED)
+I128 = KeyFormat(128, SIGNED)
+
+
+def bsort_words2(hi: np.ndarray, lo: np.ndarray, w: int, kind: int, descending: bool = False,
+                 mode: int = LITERAL, max_levels: int = 0, check: bool = False):
+    """Sorts the two-word keys (hi[i], lo[i]) of w bits in place with Algs.
+    1-3; returns (invariant violations, partitions)."""
+    assert hi.dtype == lo.dtype == np.uint64 and hi.flags.c_contiguous and lo.flags.c_contiguous
+    stats = np.zeros(2, dtype=np.uint64)
+    st = _load().orc_bsort2(_ptr(hi), _ptr(lo), hi.size, w, kind, 0 if descending else 1, mode, max_levels,
+                            int(check), _ptr(stats))
+    if st != 0:
+        raise ValueError("oracle rejected the input (status %d)" % st)
+    return int(stats[0]), int(stats[1])
+
+
+def bsort128(x: np.ndarray, signed: bool = False, descending: bool = False, mode: int = LITERAL,
+             check: bool = False) -> np.ndarray:
+    """Sorted copy of 128-bit keys given as a uint64 (n, 2) array [lo, hi]."""
+    x = np.asarray(x, dtype=np.uint64).reshape(-1, 2)
+    lo = np.ascontiguousarray(x[:, 0])
+    hi = np.ascontiguousarray(x[:, 1])
+    v, _ = bsort_words2(hi, lo, 128, SIGNED if signed else UNSIGNED, descending, mode, check=check)
+    if check and v:
+        raise AssertionError("invariants (i)/(ii) violated %d times" % v)
+    return np.stack([lo, hi], axis=1)
+
+
+def cmp2(xh: int, xl: int, yh: int, yl: int, w: int, kind: int) -> int:
+    return _load().orc_cmp2(xh, xl, yh, yl, w, kind)

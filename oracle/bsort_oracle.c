@@ -494,3 +494,129 @@ int orc_stable_argsort(const uint64_t *a, size_t n, int w, int kind, int e_bits,
     free(tmp);
     return ORC_OK;
 }
+
+/* ---------------------------------------------------------------------------
+ * Keys wider than one word: unsigned and signed integers of w bits, 64 < w
+ * <= 128 (any 1 <= w <= 128 is accepted), each key a (hi, lo) pair of words,
+ * the pattern's bits 64.. in hi and 0..63 in lo.  The same Algs. 1-3 as
+ * above -- the partition on one bit, the MSB-first recursion, the signed
+ * key's inverted sign pass -- with the mask given as a bit position, since a
+ * 128-bit mask no longer fits one word (Sec. III-C: the method applies to any
+ * word size).  The definition side compares the words as one integer.
+ * ------------------------------------------------------------------------- */
+
+typedef struct {
+    int mode, check, max_levels;
+    uint64_t violations, partitions;
+    uint64_t *thi, *tlo; /* scratch for the stable split */
+} orc_ctx2;
+
+static int bit_of(const uint64_t *hi, const uint64_t *lo, size_t i, int b)
+{
+    return b >= 64 ? (int)((hi[i] >> (b - 64)) & 1) : (int)((lo[i] >> b) & 1);
+}
+
+/* Alg. 1 on the bit at position b of two-word keys. */
+static size_t single_pass2(orc_ctx2 *c, uint64_t *hi, uint64_t *lo, int b, size_t ps, size_t pe, int asc)
+{
+    size_t k = ps;
+    c->partitions++;
+    if (c->mode == ORC_LITERAL) {
+        for (size_t i = ps; i < pe; i++) {
+            int bit = bit_of(hi, lo, i, b);
+            if ((asc && !bit) || (!asc && bit)) {
+                uint64_t th = hi[i], tl = lo[i];
+                hi[i] = hi[k]; lo[i] = lo[k];
+                hi[k] = th; lo[k] = tl;
+                k++;
+            }
+        }
+    } else {
+        size_t t = 0;
+        for (size_t i = ps; i < pe; i++) {
+            int bit = bit_of(hi, lo, i, b);
+            if ((asc && !bit) || (!asc && bit)) { c->thi[t] = hi[i]; c->tlo[t] = lo[i]; t++; }
+        }
+        k = ps + t;
+        for (size_t i = ps; i < pe; i++) {
+            int bit = bit_of(hi, lo, i, b);
+            if (!((asc && !bit) || (!asc && bit))) { c->thi[t] = hi[i]; c->tlo[t] = lo[i]; t++; }
+        }
+        memcpy(hi + ps, c->thi, (pe - ps) * sizeof(uint64_t));
+        memcpy(lo + ps, c->tlo, (pe - ps) * sizeof(uint64_t));
+    }
+    if (c->check) {
+        for (size_t i = ps; i < k; i++)
+            if (bit_of(hi, lo, i, b) != !asc) c->violations++;
+        for (size_t j = k; j < pe; j++)
+            if (bit_of(hi, lo, j, b) != asc) c->violations++;
+    }
+    return k;
+}
+
+/* Alg. 2 from bit position b down to bit 0. */
+static void binary_quicksort2(orc_ctx2 *c, uint64_t *hi, uint64_t *lo, int b, size_t ps, size_t pe, int asc,
+                              int level)
+{
+    if (pe - ps <= 1) return; /* R3 */
+    size_t k = single_pass2(c, hi, lo, b, ps, pe, asc);
+    if (b == 0 || (c->max_levels > 0 && level >= c->max_levels)) return;
+#if ORC_PLANT == 14
+    binary_quicksort2(c, hi, lo, b - 1, ps, k, !asc, level + 1); /* planted: lower side in the wrong direction */
+#else
+    binary_quicksort2(c, hi, lo, b - 1, ps, k, asc, level + 1);
+#endif
+    binary_quicksort2(c, hi, lo, b - 1, k, pe, asc, level + 1);
+}
+
+/* Sorts the two-word keys (hi[i], lo[i]), i < n, of w bits (1..128):
+ * kind ORC_UNSIGNED (Alg. 2) or ORC_SIGNED (Alg. 3: sign pass inverted).
+ * Arguments as orc_bsort; bits at or above w must be zero. */
+int orc_bsort2(uint64_t *hi, uint64_t *lo, size_t n, int w, int kind, int asc, int mode, int max_levels, int check,
+               uint64_t *stats_out)
+{
+    if (w < 1 || w > 128 || (kind != ORC_UNSIGNED && kind != ORC_SIGNED)) return ORC_ERR_ARG;
+    for (size_t i = 0; i < n; i++) {
+        if (w <= 64 && (hi[i] || (w < 64 && (lo[i] >> w)))) return ORC_ERR_BITS;
+        if (w > 64 && w < 128 && (hi[i] >> (w - 64))) return ORC_ERR_BITS;
+    }
+    orc_ctx2 c;
+    memset(&c, 0, sizeof c);
+    c.mode = mode == ORC_STABLE ? ORC_STABLE : ORC_LITERAL;
+    c.check = check;
+    c.max_levels = max_levels;
+    if (c.mode == ORC_STABLE && n > 0) {
+        c.thi = (uint64_t *)malloc(n * sizeof(uint64_t));
+        c.tlo = (uint64_t *)malloc(n * sizeof(uint64_t));
+        if (!c.thi || !c.tlo) { free(c.thi); free(c.tlo); return ORC_ERR_MEM; }
+    }
+    asc = asc ? 1 : 0;
+    if (kind == ORC_UNSIGNED) {
+        binary_quicksort2(&c, hi, lo, w - 1, 0, n, asc, 1);
+    } else if (n > 1) {
+        size_t k = single_pass2(&c, hi, lo, w - 1, 0, n, !asc);
+        if (w > 1 && !(max_levels > 0 && 1 >= max_levels)) {
+            binary_quicksort2(&c, hi, lo, w - 2, 0, k, asc, 2);
+            binary_quicksort2(&c, hi, lo, w - 2, k, n, asc, 2);
+        }
+    }
+    free(c.thi);
+    free(c.tlo);
+    if (stats_out) { stats_out[0] = c.violations; stats_out[1] = c.partitions; }
+    return ORC_OK;
+}
+
+/* Definition side for two-word keys: numeric order of the w-bit pattern as
+ * an unsigned or a two's-complement integer.  -1, 0, +1. */
+int orc_cmp2(uint64_t xh, uint64_t xl, uint64_t yh, uint64_t yl, int w, int kind)
+{
+    if (kind == ORC_SIGNED) {
+        /* the sign bit decides first: a set sign bit is the smaller number */
+        int sx = w > 64 ? (int)((xh >> (w - 65)) & 1) : (int)((xl >> (w - 1)) & 1);
+        int sy = w > 64 ? (int)((yh >> (w - 65)) & 1) : (int)((yl >> (w - 1)) & 1);
+        if (sx != sy) return sx ? -1 : 1;
+    }
+    if (xh != yh) return xh < yh ? -1 : 1;
+    if (xl != yl) return xl < yl ? -1 : 1;
+    return 0;
+}

@@ -559,6 +559,78 @@ def pin_parallel_checkers_combine():
         assert G.par_rank(x, key, fmt, False) == O.rank(words, key, fmt, False)
 
 
+# --- keys of two words (65..128 bits) -----------------------------------------
+
+_M64 = (1 << 64) - 1
+
+
+def _two_word(keys):
+    hi = np.array([v >> 64 for v in keys], dtype=np.uint64)
+    lo = np.array([v & _M64 for v in keys], dtype=np.uint64)
+    return hi, lo
+
+
+def _int_value(v, w, kind):
+    return v - (1 << w) if kind == O.SIGNED and v >> (w - 1) else v
+
+
+def pin_two_word_traces():
+    """Figs. 1 and 2 through the two-word path: every printed row (stable
+    split, level limit) and the final row (swap loop)."""
+    for name in ("fig1_unsigned_trace.txt", "fig2_signed_trace.txt"):
+        fmt, asc, rows = load_trace(name)
+        for lvl, row in rows.items():
+            hi, lo = _two_word(rows[0])
+            if lvl:
+                v, _ = O.bsort_words2(hi, lo, fmt.w, fmt.kind, not asc, O.STABLE, lvl, check=True)
+                assert v == 0
+            assert lo.tolist() == row and not hi.any(), (name, lvl, lo.tolist())
+        hi, lo = _two_word(rows[0])
+        O.bsort_words2(hi, lo, fmt.w, fmt.kind, not asc, O.LITERAL)
+        assert lo.tolist() == rows[max(rows)]
+
+
+def pin_two_word_random_vs_integers():
+    """Unsigned and signed keys of 65..128 bits, tie-heavy and spread over
+    the word boundary: both partition modes and directions give the order of
+    the numbers they encode (Python integers), with invariants (i)/(ii) after
+    every partition."""
+    rnd = random.Random(77)
+    for w in (65, 66, 100, 127, 128):
+        for kind in (O.UNSIGNED, O.SIGNED):
+            pool = [rnd.getrandbits(w) for _ in range(6)]
+            keys = [rnd.choice(pool) if rnd.random() < 0.4 else rnd.getrandbits(w) for _ in range(600)]
+            keys += [1 << 63, 1 << 64, (1 << 64) - 1, (1 << 64) + 1, 0, (1 << w) - 1, 1 << (w - 1),
+                     (1 << (w - 1)) - 1]
+            for desc in (False, True):
+                want = sorted(keys, key=lambda v: _int_value(v, w, kind), reverse=desc)
+                for mode in (O.LITERAL, O.STABLE):
+                    hi, lo = _two_word(keys)
+                    v, _ = O.bsort_words2(hi, lo, w, kind, desc, mode, check=True)
+                    assert v == 0
+                    got = [(int(h) << 64) | int(l) for h, l in zip(hi, lo)]
+                    assert got == want, (w, kind, desc, mode)
+
+
+def pin_two_word_window_exhaustive():
+    """Every pattern of bits 61..66 (across the word boundary) in 128-bit
+    keys whose other bits are fixed, shuffled: sorted as the integers, and
+    the definition comparator agrees with integer comparison."""
+    rnd = random.Random(5)
+    for kind in (O.UNSIGNED, O.SIGNED):
+        for fixed in (0, (1 << 127) | 0xABCDEF, (1 << 70) | 3):
+            keys = [(fixed & ~(63 << 61)) | (p << 61) for p in range(64)]
+            rnd.shuffle(keys)
+            for desc in (False, True):
+                hi, lo = _two_word(keys)
+                O.bsort_words2(hi, lo, 128, kind, desc)
+                got = [(int(h) << 64) | int(l) for h, l in zip(hi, lo)]
+                assert got == sorted(keys, key=lambda v: _int_value(v, 128, kind), reverse=desc)
+            for x, y in zip(keys, keys[1:] + keys[:1]):
+                a, b = _int_value(x, 128, kind), _int_value(y, 128, kind)
+                assert O.cmp2(x >> 64, x & _M64, y >> 64, y & _M64, 128, kind) == (a > b) - (a < b)
+
+
 ALL_PINS = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]
 
 

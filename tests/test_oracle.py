@@ -28,6 +28,7 @@ PLANTS = {
     11: "multiset digest ignores the first element",
     12: "first_unsorted flags equal neighbours",
     13: "multiset digest ignores the high half of a word",
+    14: "two-word recursion sorts the lower side in the wrong direction",
 }
 
 
