@@ -54,7 +54,13 @@ typedef enum {
     BSORT_U64 = 8,
     BSORT_I64 = 9,
     BSORT_F64 = 10,
-    BSORT_BF16 = 11  /* bfloat16: 1 sign, 8 exponent, 7 mantissa bits (the high half of a binary32) */
+    BSORT_BF16 = 11, /* bfloat16: 1 sign, 8 exponent, 7 mantissa bits (the high half of a binary32) */
+    /* 128-bit integers (Sec. III-C: the method holds for any word size): a key
+     * is 16 bytes, little-endian -- the low 64 bits first -- and the buffer is
+     * aligned to 16 bytes.  Ping-pong and segmented sorts; the in-place mode,
+     * the key-value sort and the serving loop take keys of up to 8 bytes. */
+    BSORT_U128 = 12,
+    BSORT_I128 = 13
 } bsort_dtype;
 
 typedef enum {

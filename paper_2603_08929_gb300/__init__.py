@@ -27,7 +27,9 @@ MODE_PINGPONG, MODE_INPLACE = 0, 1
 
 # bsort_dtype codes, in the order of include/bsort.h
 DTYPES = ["uint8", "int8", "uint16", "int16", "float16", "uint32", "int32", "float32",
-          "uint64", "int64", "float64", "bfloat16"]
+          "uint64", "int64", "float64", "bfloat16", "uint128", "int128"]
+KEY_BYTES = {"uint8": 1, "int8": 1, "uint16": 2, "int16": 2, "float16": 2, "bfloat16": 2, "uint32": 4, "int32": 4,
+             "float32": 4, "uint64": 8, "int64": 8, "float64": 8, "uint128": 16, "int128": 16}
 _CODE = {name: i for i, name in enumerate(DTYPES)}
 
 KERNEL_KINDS = ["init", "hist", "scan", "classify", "scatter", "finish", "fill",
@@ -217,11 +219,27 @@ def _device_tensor(t):
     return t
 
 
-def bsort_keys(keys, descending: bool = False, stream=None) -> None:
-    """Sorts a contiguous CUDA tensor in place (C ABI ``bsort_keys``)."""
+def _keys(keys, dtype=None):
+    """(pointer, key count, dtype code) of a contiguous CUDA tensor.  With
+    ``dtype`` ("uint128" / "int128", which torch lacks, or any other name)
+    the tensor's bytes are read as keys of that dtype: 16-byte keys, low
+    64 bits first, e.g. an int64 tensor of shape (n, 2)."""
     _device_tensor(keys)
-    _check(lib().bsort_keys(ctypes.c_void_p(keys.data_ptr()), keys.numel(), _dtype_code(keys.dtype),
-                            int(bool(descending)), _stream_ptr(stream)), "bsort_keys")
+    if dtype is None:
+        return ctypes.c_void_p(keys.data_ptr()), keys.numel(), _dtype_code(keys.dtype)
+    name = str(dtype).replace("torch.", "")
+    nbytes = keys.numel() * keys.element_size()
+    kb = KEY_BYTES[name]
+    if nbytes % kb:
+        raise ValueError("%d bytes are not whole %s keys" % (nbytes, name))
+    return ctypes.c_void_p(keys.data_ptr()), nbytes // kb, _dtype_code(name)
+
+
+def bsort_keys(keys, descending: bool = False, stream=None, dtype=None) -> None:
+    """Sorts a contiguous CUDA tensor in place (C ABI ``bsort_keys``);
+    ``dtype`` reads its bytes as keys of another dtype (see ``_keys``)."""
+    ptr, n, code = _keys(keys, dtype)
+    _check(lib().bsort_keys(ptr, n, code, int(bool(descending)), _stream_ptr(stream)), "bsort_keys")
 
 
 _inplace_handle = None
@@ -328,12 +346,12 @@ class Handle:
 
 
 def bsort_keys_ws(handle: Handle, keys, workspace, descending: bool = False, stream=None,
-                  mode: int = MODE_PINGPONG) -> None:
-    """Sorts with a caller-provided device workspace (a uint8 CUDA tensor)."""
-    _device_tensor(keys)
+                  mode: int = MODE_PINGPONG, dtype=None) -> None:
+    """Sorts with a caller-provided device workspace (a uint8 CUDA tensor);
+    ``dtype`` as for ``bsort_keys``."""
+    kp, kn, code = _keys(keys, dtype)
     _device_tensor(workspace)
-    _check(lib().bsort_keys_ws(handle.ptr, ctypes.c_void_p(keys.data_ptr()), keys.numel(),
-                               _dtype_code(keys.dtype), int(bool(descending)), int(mode),
+    _check(lib().bsort_keys_ws(handle.ptr, kp, kn, code, int(bool(descending)), int(mode),
                                ctypes.c_void_p(workspace.data_ptr()),
                                workspace.numel() * workspace.element_size(), _stream_ptr(stream)),
            "bsort_keys_ws")
@@ -434,20 +452,20 @@ def _offsets(offsets):
     return ctypes.c_void_p(offsets.data_ptr()), offsets.numel() - 1
 
 
-def bsort_keys_segmented(keys, offsets, descending: bool = False, stream=None, handle=None, workspace=None) -> None:
+def bsort_keys_segmented(keys, offsets, descending: bool = False, stream=None, handle=None, workspace=None,
+                         dtype=None) -> None:
     """Sorts every segment keys[offsets[s]:offsets[s+1]] in place (C ABI
     ``bsort_keys_segmented``; with ``handle`` and ``workspace``:
-    ``bsort_keys_segmented_ws``).  ``offsets``: int64 CUDA tensor, S + 1 entries."""
-    _device_tensor(keys)
+    ``bsort_keys_segmented_ws``).  ``offsets``: int64 CUDA tensor, S + 1
+    entries, in keys; ``dtype`` as for ``bsort_keys``."""
+    kp, kn, code = _keys(keys, dtype)
     op, nseg = _offsets(offsets)
     if handle is None:
-        _check(lib().bsort_keys_segmented(ctypes.c_void_p(keys.data_ptr()), keys.numel(), op, nseg,
-                                          _dtype_code(keys.dtype), int(bool(descending)), _stream_ptr(stream)),
+        _check(lib().bsort_keys_segmented(kp, kn, op, nseg, code, int(bool(descending)), _stream_ptr(stream)),
                "bsort_keys_segmented")
     else:
         _device_tensor(workspace)
-        _check(lib().bsort_keys_segmented_ws(handle.ptr, ctypes.c_void_p(keys.data_ptr()), keys.numel(), op, nseg,
-                                             _dtype_code(keys.dtype), int(bool(descending)),
+        _check(lib().bsort_keys_segmented_ws(handle.ptr, kp, kn, op, nseg, code, int(bool(descending)),
                                              ctypes.c_void_p(workspace.data_ptr()),
                                              workspace.numel() * workspace.element_size(), _stream_ptr(stream)),
                "bsort_keys_segmented_ws")

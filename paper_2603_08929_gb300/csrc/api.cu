@@ -23,10 +23,10 @@ struct DtypeInfo {
 bool dtype_info(bsort_dtype dt, DtypeInfo *out) {
     // bfloat16 takes the binary16 codec: the transform depends only on the
     // width and the kind (sign-magnitude), not on the exponent/mantissa split
-    static const DtypeInfo table[] = {{1, 0}, {1, 1}, {2, 0}, {2, 1}, {2, 2}, {4, 0},
-                                      {4, 1}, {4, 2}, {8, 0}, {8, 1}, {8, 2}, {2, 2}};
+    static const DtypeInfo table[] = {{1, 0}, {1, 1}, {2, 0}, {2, 1}, {2, 2}, {4, 0}, {4, 1},
+                                      {4, 2}, {8, 0}, {8, 1}, {8, 2}, {2, 2}, {16, 0}, {16, 1}};
     const int i = static_cast<int>(dt);
-    if (i < 0 || i > 11) return false;
+    if (i < 0 || i > 13) return false;
     *out = table[i];
     return true;
 }
@@ -35,6 +35,13 @@ bool dtype_info(bsort_dtype dt, DtypeInfo *out) {
 // the sign pass of Algs. 3/4 runs in the inverted direction; negative floats
 // run in the inverted direction on exponent and mantissa).
 Codec codec_for(const DtypeInfo &di, int descending) {
+    if (di.bytes == 16) {  // integers: one xor, f0/d0 the low word and f1/d1 the high word
+        const uint64_t dm = descending ? ~0ull : 0ull;
+        Codec c;
+        c.f0 = c.d0 = dm;
+        c.f1 = c.d1 = dm ^ (di.kind == 1 ? 1ull << 63 : 0ull);
+        return c;
+    }
     const int w = di.bytes * 8;
     const uint64_t all = w == 64 ? ~0ull : ((1ull << w) - 1);
     const uint64_t sb = 1ull << (w - 1);
@@ -102,8 +109,9 @@ MsdLayout msd_layout(size_t n, int key_bytes, size_t nseg = 0, bool inplace = fa
     L.chunks0 = take(sizeof(Chunk) * L.max_chunks);
     L.chunks1 = take(sizeof(Chunk) * L.max_chunks);
     L.hist = take(sizeof(uint32_t) * s.bins * static_cast<size_t>(L.max_chunks));
-    L.cand = take(sizeof(uint64_t) * L.max_chunks);
-    L.cor = take(sizeof(uint64_t) * L.max_chunks);
+    const size_t and_words = key_bytes > 8 ? 2 : 1;  // per chunk
+    L.cand = take(sizeof(uint64_t) * and_words * L.max_chunks);
+    L.cor = take(sizeof(uint64_t) * and_words * L.max_chunks);
     L.bbase = take(sizeof(uint32_t) * s.bins * static_cast<size_t>(L.max_buckets));
     L.units = take(sizeof(Unit) * L.max_units);
     L.fb_units = take(sizeof(Unit) * L.max_units);
@@ -276,6 +284,13 @@ void end_call(bsort_handle *h, cudaStream_t st, size_t n, int key_bytes) {
     }
 }
 
+// The handle's MSD tuning for 4- and 8-byte keys; 16-byte keys run the
+// library defaults.
+const Tuning &tune_of(const bsort_handle *h, int key_bytes) {
+    static const Tuning defaults;
+    return key_bytes == 16 ? defaults : h->tune[key_bytes == 8];
+}
+
 bsort_status run_sort(bsort_handle *h, void *keys, size_t n, const DtypeInfo &di, int descending,
                       void *workspace, size_t ws_bytes, cudaStream_t st, bool inplace = false) {
     (void)cudaGetLastError();  // clear a stale non-sticky error
@@ -315,7 +330,8 @@ bsort_status run_sort(bsort_handle *h, void *keys, size_t n, const DtypeInfo &di
         h->last_inplace = inplace;  // the counting path writes the keys from counts: in place either way
         h->last_fixed_aux = L.total;
     } else {
-        const Tuning &tune = h->tune[di.bytes == 8];
+        if (inplace && di.bytes > 8) return BSORT_ERR_UNSUPPORTED;
+        const Tuning &tune = tune_of(h, di.bytes);
         const MsdLayout L = msd_layout(n, di.bytes, 0, inplace, tune);
         if (ws_bytes < L.total) return BSORT_ERR_WORKSPACE_TOO_SMALL;
         h->last_inplace = inplace;
@@ -323,7 +339,8 @@ bsort_status run_sort(bsort_handle *h, void *keys, size_t n, const DtypeInfo &di
         Work wk = make_work(L, ws, keys, n, di, codec, tune);
         if (h->stop_levels > 0 && h->stop_levels < wk.levels) wk.stop_level = h->stop_levels;
         if (di.bytes == 4) launch_msd<uint32_t>(wk, st, h->rec, sms);
-        else launch_msd<uint64_t>(wk, st, h->rec, sms);
+        else if (di.bytes == 8) launch_msd<uint64_t>(wk, st, h->rec, sms);
+        else launch_msd<u128>(wk, st, h->rec, sms);
         h->last_path = 2;
         h->last_ctl = wk.ctl;
     }
@@ -358,12 +375,13 @@ bsort_status run_segmented(bsort_handle *h, void *keys, size_t n, const uint64_t
     }
     begin_call(h, st);
     if (!record) h->rec.active = false;
-    const Tuning &tune = h->tune[di.bytes == 8];
+    const Tuning &tune = tune_of(h, di.bytes);
     const MsdLayout L = msd_layout(n, di.bytes, nseg, false, tune);
     if (ws_bytes < L.total) return BSORT_ERR_WORKSPACE_TOO_SMALL;
     const Work wk = make_work(L, static_cast<char *>(workspace), keys, n, di, codec_for(di, descending), tune);
     if (di.bytes == 4) launch_msd_segmented<uint32_t>(wk, d_offsets, static_cast<uint32_t>(nseg), st, h->rec, sms);
-    else launch_msd_segmented<uint64_t>(wk, d_offsets, static_cast<uint32_t>(nseg), st, h->rec, sms);
+    else if (di.bytes == 8) launch_msd_segmented<uint64_t>(wk, d_offsets, static_cast<uint32_t>(nseg), st, h->rec, sms);
+    else launch_msd_segmented<u128>(wk, d_offsets, static_cast<uint32_t>(nseg), st, h->rec, sms);
     h->last_path = 2;
     h->last_ctl = wk.ctl;
     h->last_stream = st;
@@ -456,6 +474,7 @@ bsort_status bsort_workspace_bytes(size_t n, bsort_dtype dt, bsort_mode mode, si
     DtypeInfo di;
     if (!bytes || !dtype_info(dt, &di)) return BSORT_ERR_INVALID_ARG;
     if (mode != BSORT_MODE_PINGPONG && mode != BSORT_MODE_INPLACE) return BSORT_ERR_INVALID_ARG;
+    if (mode == BSORT_MODE_INPLACE && di.bytes > 8) return BSORT_ERR_UNSUPPORTED;
     *bytes = workspace_for(n, di, mode == BSORT_MODE_INPLACE);
     return BSORT_OK;
 }
@@ -503,6 +522,7 @@ bsort_status bsort_keys_ws(bsort_handle *handle, void *keys, size_t n, bsort_dty
 bsort_status bsort_pairs_workspace_bytes(size_t n, bsort_dtype dt, size_t *bytes) {
     DtypeInfo di;
     if (!bytes || !dtype_info(dt, &di)) return BSORT_ERR_INVALID_ARG;
+    if (di.bytes > 8) return BSORT_ERR_UNSUPPORTED;
     *bytes = pairs_layout(n, di.bytes, Tuning()).total;
     return BSORT_OK;
 }
@@ -510,6 +530,7 @@ bsort_status bsort_pairs_workspace_bytes(size_t n, bsort_dtype dt, size_t *bytes
 bsort_status bsort_pairs_workspace_bytes_tuned(size_t n, bsort_dtype dt, const bsort_tuning *tuning8, size_t *bytes) {
     DtypeInfo di;
     if (!bytes || !dtype_info(dt, &di)) return BSORT_ERR_INVALID_ARG;
+    if (di.bytes > 8) return BSORT_ERR_UNSUPPORTED;
     Tuning t;
     if (!to_tuning(tuning8, 8, &t)) return BSORT_ERR_INVALID_ARG;
     *bytes = pairs_layout(n, di.bytes, t).total;
@@ -524,7 +545,7 @@ bsort_status bsort_pairs_ws(bsort_handle *handle, void *keys, void *values, size
     if (!dtype_info(dt, &di)) return BSORT_ERR_INVALID_ARG;
     if (values && value_bytes != 1 && value_bytes != 2 && value_bytes != 4 && value_bytes != 8)
         return BSORT_ERR_INVALID_ARG;
-    if (n >= (1ull << 32)) return BSORT_ERR_UNSUPPORTED;  // positions travel in 32 bits
+    if (n >= (1ull << 32) || di.bytes > 8) return BSORT_ERR_UNSUPPORTED;  // positions travel in 32 bits
     if (n == 0) return BSORT_OK;
     if (!keys) return BSORT_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(keys) % di.bytes || (values && reinterpret_cast<uintptr_t>(values) % value_bytes) ||
@@ -651,6 +672,7 @@ bsort_status bsort_segmented_workspace_bytes_tuned(size_t n, size_t num_segments
     if (di.bytes < 4) return BSORT_ERR_UNSUPPORTED;
     Tuning t;
     if (!to_tuning(tuning, di.bytes, &t)) return BSORT_ERR_INVALID_ARG;
+    if (di.bytes == 16) t = Tuning();  // 16-byte keys run the defaults
     *bytes = msd_layout(n, di.bytes, num_segments, false, t).total;
     return BSORT_OK;
 }
@@ -680,7 +702,7 @@ bsort_status bsort_keys_segmented(void *keys, size_t n, const uint64_t *d_offset
     if (!h) return BSORT_ERR_NO_MEMORY;
     std::lock_guard<std::mutex> lk(h->mu);
     const bsort_status gs =
-        grow(&h->ws, &h->ws_bytes, msd_layout(n, di.bytes, num_segments, false, h->tune[di.bytes == 8]).total);
+        grow(&h->ws, &h->ws_bytes, msd_layout(n, di.bytes, num_segments, false, tune_of(h, di.bytes)).total);
     if (gs != BSORT_OK) return gs;
     return run_segmented(h, keys, n, d_offsets, num_segments, di, descending, h->ws, h->ws_bytes,
                          static_cast<cudaStream_t>(stream), true);
@@ -698,6 +720,7 @@ bsort_status capture(bsort_handle *h, void *keys, size_t n, const uint64_t *d_of
                      const DtypeInfo &di, int descending, void *ws, size_t ws_bytes, bsort_graph **out) {
     if (di.bytes == 4) msd_prepare<uint32_t>();
     else if (di.bytes == 8) msd_prepare<uint64_t>();
+    else if (di.bytes == 16) msd_prepare<u128>();
     cudaStream_t cs;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return BSORT_ERR_CUDA;
     bsort_graph *g = new (std::nothrow) bsort_graph();
@@ -796,8 +819,10 @@ bsort_status bsort_workspace_bytes_tuned(size_t n, bsort_dtype dt, bsort_mode mo
     DtypeInfo di;
     if (!bytes || !dtype_info(dt, &di)) return BSORT_ERR_INVALID_ARG;
     if (mode != BSORT_MODE_PINGPONG && mode != BSORT_MODE_INPLACE) return BSORT_ERR_INVALID_ARG;
+    if (mode == BSORT_MODE_INPLACE && di.bytes > 8) return BSORT_ERR_UNSUPPORTED;
     Tuning t;
     if (di.bytes >= 4 && !to_tuning(tuning, di.bytes, &t)) return BSORT_ERR_INVALID_ARG;
+    if (di.bytes == 16) t = Tuning();  // 16-byte keys run the defaults
     *bytes = workspace_for(n, di, mode == BSORT_MODE_INPLACE, t);
     return BSORT_OK;
 }
@@ -841,6 +866,7 @@ bsort_status bsort_top_digit_counts(const void *keys, size_t n, bsort_dtype dt, 
                                     uint64_t *d_counts, void *stream) {
     DtypeInfo di;
     if (!dtype_info(dt, &di)) return BSORT_ERR_INVALID_ARG;
+    if (di.bytes > 8) return BSORT_ERR_UNSUPPORTED;
     if (bits < 1 || bits > kDigitCountsMaxBits || bits > di.bytes * 8 || !d_counts) return BSORT_ERR_INVALID_ARG;
     if (n > 0 && !keys) return BSORT_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(keys) % di.bytes || reinterpret_cast<uintptr_t>(d_counts) % 8)

@@ -68,10 +68,12 @@ struct Unit {
     uint8_t pad;
 };
 
-// A run of identical keys written without reading (value is encoded).
+// A run of identical keys written without reading (value is encoded; its
+// bits 64..127 in value_hi for 16-byte keys).
 struct Fill {
     uint64_t start;
     uint64_t value;
+    uint64_t value_hi;
     uint32_t len;
     uint32_t pad;
 };
@@ -120,8 +122,8 @@ struct Work {
     Bucket *buckets[2];
     Chunk *chunks[2];
     uint32_t *hist;         // [bins][max_chunks], digit-major; excl. prefix after the scan
-    uint64_t *chunk_and;    // [max_chunks]
-    uint64_t *chunk_or;     // [max_chunks]
+    uint64_t *chunk_and;    // [max_chunks] (16-byte keys: two words per chunk, low word first)
+    uint64_t *chunk_or;     // [max_chunks] (likewise)
     uint32_t *bucket_base;  // [max_buckets][bins]: digit totals, then digit bases relative to the bucket start
     Unit *units;
     Unit *fb_units;  // [max_units] skewed units for the LSD finish
@@ -164,6 +166,84 @@ template <typename K>
 __device__ __forceinline__ K decode_key(K k, const Codec &c) {
     constexpr int W = sizeof(K) * 8;
     return k ^ static_cast<K>((k >> (W - 1)) ? c.d1 : c.d0);
+}
+
+// 16-byte keys are integers only: the transform is one xor with a constant
+// whose low word is f0 (d0) and high word f1 (d1) -- all ones for a
+// descending sort, the sign bit for signed keys.
+typedef unsigned __int128 u128;
+
+template <>
+__device__ __forceinline__ u128 encode_key<u128>(u128 x, const Codec &c) {
+    return x ^ ((static_cast<u128>(c.f1) << 64) | c.f0);
+}
+
+template <>
+__device__ __forceinline__ u128 decode_key<u128>(u128 k, const Codec &c) {
+    return k ^ ((static_cast<u128>(c.d1) << 64) | c.d0);
+}
+
+// Warp shuffle of a key of any width.
+template <typename K>
+__device__ __forceinline__ K shfl_xor_k(K v, int m) {
+    return __shfl_xor_sync(0xffffffffu, v, m);
+}
+
+template <>
+__device__ __forceinline__ u128 shfl_xor_k<u128>(u128 v, int m) {
+    const unsigned long long lo = __shfl_xor_sync(0xffffffffu, static_cast<unsigned long long>(v), m);
+    const unsigned long long hi = __shfl_xor_sync(0xffffffffu, static_cast<unsigned long long>(v >> 64), m);
+    return (static_cast<u128>(hi) << 64) | lo;
+}
+
+// Positions of the highest and the lowest set bit of x (x != 0).
+template <typename K>
+__device__ __forceinline__ int msb_pos(K x) {
+    return 63 - __clzll(static_cast<unsigned long long>(x));
+}
+
+template <>
+__device__ __forceinline__ int msb_pos<u128>(u128 x) {
+    const unsigned long long hi = static_cast<unsigned long long>(x >> 64);
+    return hi ? 127 - __clzll(hi) : 63 - __clzll(static_cast<unsigned long long>(x));
+}
+
+template <typename K>
+__device__ __forceinline__ int lsb_pos(K x) {
+    return __ffsll(static_cast<long long>(static_cast<unsigned long long>(x))) - 1;
+}
+
+template <>
+__device__ __forceinline__ int lsb_pos<u128>(u128 x) {
+    const unsigned long long lo = static_cast<unsigned long long>(x);
+    return lo ? __ffsll(static_cast<long long>(lo)) - 1
+              : 64 + __ffsll(static_cast<long long>(static_cast<unsigned long long>(x >> 64))) - 1;
+}
+
+// Keys with bits [0, h) cleared (h >= width: no bit kept).
+template <typename K>
+__device__ __forceinline__ K high_bits(K x, int h) {
+    return h >= static_cast<int>(sizeof(K) * 8) ? K(0) : static_cast<K>(x & (~K(0) << h));
+}
+
+// The AND and OR of a chunk's keys in the chunk_and / chunk_or words.
+template <typename K>
+__device__ __forceinline__ void store_and_or(uint64_t *wa, uint64_t *wo, size_t c, K a, K o) {
+    if constexpr (sizeof(K) > 8) {
+        wa[2 * c] = static_cast<uint64_t>(a);
+        wa[2 * c + 1] = static_cast<uint64_t>(a >> 64);
+        wo[2 * c] = static_cast<uint64_t>(o);
+        wo[2 * c + 1] = static_cast<uint64_t>(o >> 64);
+    } else {
+        wa[c] = a;
+        wo[c] = o;
+    }
+}
+
+template <typename K>
+__device__ __forceinline__ K load_word_k(const uint64_t *w, size_t c) {
+    if constexpr (sizeof(K) > 8) return (static_cast<K>(w[2 * c + 1]) << 64) | w[2 * c];
+    else return static_cast<K>(w[c]);
 }
 
 __device__ __forceinline__ unsigned lanemask_lt() {

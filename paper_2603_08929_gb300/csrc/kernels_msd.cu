@@ -433,8 +433,8 @@ __device__ __forceinline__ void block_and_or_k(K &a, K &o, K *ta, K *to) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int s = 16; s > 0; s >>= 1) {
-        a &= __shfl_xor_sync(kFull, a, s);
-        o |= __shfl_xor_sync(kFull, o, s);
+        a &= shfl_xor_k(a, s);
+        o |= shfl_xor_k(o, s);
     }
     if (lane == 0) {
         ta[warp] = a;
@@ -654,7 +654,7 @@ __global__ void __launch_bounds__(THREADS) k_hist(Work wk, int level) {
     constexpr int WARPS = THREADS / 32;
     constexpr int ROWS = NB <= kBins ? WARPS : 4;
     __shared__ uint32_t sh[ROWS * NB];
-    __shared__ unsigned long long ta[WARPS], to[WARPS];
+    __shared__ K ta[WARPS], to[WARPS];
     const int p = level & 1;
     if (wk.ctl->error) return;  // an earlier launch found a problem: stop touching memory
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -688,12 +688,8 @@ __global__ void __launch_bounds__(THREADS) k_hist(Work wk, int level) {
             for (int w = 0; w < ROWS; ++w) sum += sh[w * NB + d];
             wk.hist[static_cast<size_t>(d) * wk.max_chunks + c] = sum;
         }
-        unsigned long long aa = a, oo = o;
-        block_and_or<THREADS>(aa, oo, ta, to);
-        if (threadIdx.x == 0) {
-            wk.chunk_and[c] = aa;
-            wk.chunk_or[c] = oo;
-        }
+        block_and_or_k<K, THREADS>(a, o, ta, to);
+        if (threadIdx.x == 0) store_and_or<K>(wk.chunk_and, wk.chunk_or, c, a, o);
         __syncthreads();
     }
 }
@@ -827,7 +823,8 @@ __device__ void emit_buckets(const Work &wk, int q, bool take, uint64_t start, u
 }
 
 // Fill pieces for every thread whose `take` is set (thread-private loop).
-__device__ void emit_fill(const Work &wk, uint64_t start, uint64_t len, uint64_t value) {
+template <typename K>
+__device__ void emit_fill(const Work &wk, uint64_t start, uint64_t len, K value) {
     const uint32_t pieces = static_cast<uint32_t>((len + kFillPiece - 1) / kFillPiece);
     const uint32_t f0 = atomicAdd(&wk.ctl->n_fills, pieces);
     if (f0 + pieces > wk.max_fills) {
@@ -840,7 +837,9 @@ __device__ void emit_fill(const Work &wk, uint64_t start, uint64_t len, uint64_t
         f.start = start + static_cast<uint64_t>(i) * kFillPiece;
         const uint64_t rem = len - static_cast<uint64_t>(i) * kFillPiece;
         f.len = static_cast<uint32_t>(rem < kFillPiece ? rem : kFillPiece);
-        f.value = value;
+        f.value = static_cast<uint64_t>(value);
+        if constexpr (sizeof(K) > 8) f.value_hi = static_cast<uint64_t>(value >> 64);
+        else f.value_hi = 0;
         f.pad = 0;
         wk.fills[f0 + i] = f;
     }
@@ -850,11 +849,11 @@ __device__ void emit_fill(const Work &wk, uint64_t start, uint64_t len, uint64_t
 // Thread t takes digit page * THREADS + t; digits wider than 8 bits take
 // several pages, with the running digit base carried between them (a run of
 // merged small children ends at a page boundary).
-template <int THREADS>
+template <int THREADS, typename K>
 __global__ void __launch_bounds__(THREADS) k_classify(Work wk, int level) {
     pdl_enter();
     static_assert(THREADS == kBins, "one thread per digit of a page");
-    __shared__ unsigned long long ta[THREADS / 32], to[THREADS / 32];
+    __shared__ K ta[THREADS / 32], to[THREADS / 32];
     __shared__ unsigned long long tmp64[THREADS / 32 + 1];
     __shared__ uint32_t tmp[THREADS / 32 + 1];
     __shared__ uint32_t sh_choff[THREADS], sh_slot[THREADS], sh_bases[2];
@@ -867,17 +866,17 @@ __global__ void __launch_bounds__(THREADS) k_classify(Work wk, int level) {
     const int t = threadIdx.x;
     for (uint32_t i = blockIdx.x; i < nb; i += gridDim.x) {
         const Bucket b = wk.buckets[p][i];
-        unsigned long long a = ~0ull, o = 0;
+        K a = static_cast<K>(~K(0)), o = 0;
         {
             // eight chunks per thread in flight at once (a big bucket has thousands)
             const uint32_t c_end = b.first_chunk + b.num_chunks;
             uint32_t c = b.first_chunk + threadIdx.x;
             for (; c + 7 * THREADS < c_end; c += 8 * THREADS) {
-                unsigned long long ra[8], ro[8];
+                K ra[8], ro[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
-                    ra[u] = wk.chunk_and[c + u * THREADS];
-                    ro[u] = wk.chunk_or[c + u * THREADS];
+                    ra[u] = load_word_k<K>(wk.chunk_and, c + u * THREADS);
+                    ro[u] = load_word_k<K>(wk.chunk_or, c + u * THREADS);
                 }
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
@@ -886,23 +885,23 @@ __global__ void __launch_bounds__(THREADS) k_classify(Work wk, int level) {
                 }
             }
             for (; c < c_end; c += THREADS) {
-                a &= wk.chunk_and[c];
-                o |= wk.chunk_or[c];
+                a &= load_word_k<K>(wk.chunk_and, c);
+                o |= load_word_k<K>(wk.chunk_or, c);
             }
         }
-        block_and_or<THREADS>(a, o, ta, to);
+        block_and_or_k<K, THREADS>(a, o, ta, to);
         if (threadIdx.x == 0) atomicAdd(&wk.ctl->hist_keys[level], static_cast<unsigned long long>(b.len));
         if (a == o) {  // every key identical: write the value, no sort needed
             if (threadIdx.x == 0) {
                 wk.buckets[p][i].scatter = 0;
-                emit_fill(wk, b.start, b.len, a);
+                emit_fill<K>(wk, b.start, b.len, a);
             }
             continue;
         }
         const int r_eff = min(wk.radix_bits, b.h);
         const int shift = b.h - r_eff;
         const uint32_t mask = (1u << r_eff) - 1;
-        const int hb = 63 - __clzll(a ^ o);
+        const int hb = msb_pos<K>(a ^ o);
         if (hb < shift) {
             // the digit is constant: re-open the bucket at its highest varying bit
             if (threadIdx.x == 0) wk.buckets[p][i].scatter = 0;
@@ -931,8 +930,7 @@ __global__ void __launch_bounds__(THREADS) k_classify(Work wk, int level) {
             const bool big = tot > wk.unit_cap;
             // children with no bits left are constant: value = common prefix | digit
             if (big && hc == 0) {
-                const unsigned long long hi_mask = b.h >= 64 ? 0ull : (~0ull << b.h);
-                emit_fill(wk, base, tot, (a & hi_mask) | static_cast<unsigned long long>(d));
+                emit_fill<K>(wk, base, tot, static_cast<K>(high_bits<K>(a, b.h) | static_cast<K>(d)));
             }
             emit_buckets<THREADS>(wk, q, big && hc > 0, base, tot, hc, dst, 0, tmp, sh_choff, sh_slot, sh_bases,
                                   sh_cstart, sh_cend);
@@ -1481,16 +1479,18 @@ __device__ __forceinline__ bool finish_count_fast(const Work &wk, const Unit &un
         for (int q = t; q < nout; q += THREADS) {
             const uint16_t *sp = stage + lo_r + a_i + q * V;
             K kv[V];
-            if (V == 4) {
+            if constexpr (V == 4) {
                 const uint2 h = *reinterpret_cast<const uint2 *>(sp);
                 kv[0] = base ^ static_cast<K>(h.x & 0xffffu);
                 kv[1 % V] = base ^ static_cast<K>(h.x >> 16);
                 kv[2 % V] = base ^ static_cast<K>(h.y & 0xffffu);
                 kv[3 % V] = base ^ static_cast<K>(h.y >> 16);
-            } else {
+            } else if constexpr (V == 2) {
                 const uint32_t h = *reinterpret_cast<const uint32_t *>(sp);
                 kv[0] = base ^ static_cast<K>(h & 0xffffu);
                 kv[1 % V] = base ^ static_cast<K>(h >> 16);
+            } else {
+                kv[0] = base ^ static_cast<K>(sp[0]);
             }
             reinterpret_cast<uint4 *>(dstp + a_i)[q] = *reinterpret_cast<const uint4 *>(kv);
         }
@@ -1590,14 +1590,14 @@ __global__ void __launch_bounds__(THREADS, 4) k_finish(Work wk) {
             }
         }
         block_and_or_k<K, THREADS>(a, o, ta, to);
-        const unsigned long long v = static_cast<unsigned long long>(a ^ o);
+        const K v = a ^ o;
         if (v == 0) {  // one repeated key: write it len times
             const K val = decode_key(a, wk.codec);
             for (int i = t; i < len; i += THREADS) dstp[i] = val;
             continue;
         }
-        const int lo = __ffsll(static_cast<long long>(v)) - 1;
-        const int hi = 64 - __clzll(v);
+        const int lo = lsb_pos<K>(v);
+        const int hi = msb_pos<K>(v) + 1;
         const int span = hi - lo;
         const int lbits = span < 4 ? span : 4;
         const int sbits = span - lbits;
@@ -1873,9 +1873,9 @@ __global__ void __launch_bounds__(THREADS, 4) k_finish_lsd(Work wk) {
         }
         block_and_or_k<K, THREADS>(a, o, ta, to);
         K *__restrict__ dstp = out + un.start;
-        const unsigned long long v = static_cast<unsigned long long>(a ^ o);
-        const int lo = v ? __ffsll(static_cast<long long>(v)) - 1 : 0;
-        const int hi = v ? 64 - __clzll(v) : 1;
+        const K v = a ^ o;
+        const int lo = v ? lsb_pos<K>(v) : 0;
+        const int hi = v ? msb_pos<K>(v) + 1 : 1;
         const int passes = (hi - lo + kRadixBits - 1) / kRadixBits;
         const int width = (hi - lo + passes - 1) / passes;
         R::template rank_and_place<false>(k, vmask, lo, (1u << width) - 1, sm_keys);
@@ -1909,7 +1909,9 @@ __global__ void k_fill(Work wk) {
             set_error(wk.ctl, kErrBounds);
             continue;
         }
-        const K v = decode_key(static_cast<K>(fl.value), wk.codec);
+        K val = static_cast<K>(fl.value);
+        if constexpr (sizeof(K) > 8) val |= static_cast<K>(fl.value_hi) << 64;
+        const K v = decode_key(val, wk.codec);
         for (uint32_t i = threadIdx.x; i < fl.len; i += blockDim.x) out[fl.start + i] = v;
     }
 }
@@ -1949,6 +1951,13 @@ struct Cfg<uint64_t> {
     static constexpr int kFinThreads = 256;  // 256 x 10 = 2560 keys
     static constexpr int kFinItems = 10;
 };
+template <>
+struct Cfg<u128> {
+    static constexpr int kThreads = 512;  // 512 x 4 = 2048 keys
+    static constexpr int kItems = 4;
+    static constexpr int kFinThreads = 256;  // 256 x 5 = 1280 keys
+    static constexpr int kFinItems = 5;
+};
 
 }  // namespace
 
@@ -1958,6 +1967,9 @@ MsdShape msd_shape(int key_bytes, const Tuning &t, bool inplace) {
     if (key_bytes == 4) {
         s.tile = Cfg<uint32_t>::kThreads * Cfg<uint32_t>::kItems;
         fin = Cfg<uint32_t>::kFinThreads * Cfg<uint32_t>::kFinItems;
+    } else if (key_bytes == 16) {
+        s.tile = Cfg<u128>::kThreads * Cfg<u128>::kItems;
+        fin = Cfg<u128>::kFinThreads * Cfg<u128>::kFinItems;
     } else {
         s.tile = Cfg<uint64_t>::kThreads * Cfg<uint64_t>::kItems;
         fin = Cfg<uint64_t>::kFinThreads * Cfg<uint64_t>::kFinItems;
@@ -2005,7 +2017,7 @@ template <typename K>
 void msd_prepare() {
     constexpr int T = Cfg<K>::kThreads, I = Cfg<K>::kItems, CT = kMaxChunkTiles;
     constexpr int FT = Cfg<K>::kFinThreads, FI = Cfg<K>::kFinItems;
-    ip_prepare<K>();
+    if constexpr (sizeof(K) <= 8) ip_prepare<K>();  // the in-place mode takes keys of up to 8 bytes
     static const bool attrs = [] {  // once per process; thread-safe static initialisation
         cudaFuncSetAttribute(k_scatter<K, T, I, CT, kBins>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(scatter_smem<K, T, I, CT, kBins>()));
@@ -2037,10 +2049,10 @@ void msd_levels_and_finish(const Work &wk, cudaStream_t st, Recorder &rec, int n
             launch_pdl(k_colscan<1024>, 1u << wk.radix_bits, 1024, 0, st, wk, level);
             rec.end();
             rec.begin(BSORT_K_CLASSIFY, level);
-            launch_pdl(k_classify<kBins>, num_sms * 4, kBins, 0, st, wk, level);
+            launch_pdl(k_classify<kBins, K>, num_sms * 4, kBins, 0, st, wk, level);
             rec.end();
             if (wk.inplace) {
-                launch_ip_level<K>(wk, st, rec, num_sms, level);
+                if constexpr (sizeof(K) <= 8) launch_ip_level<K>(wk, st, rec, num_sms, level);
             } else {
                 rec.begin(BSORT_K_SCATTER, level);
                 if (wide)
@@ -2095,6 +2107,9 @@ void launch_msd_segmented(const Work &wk, const uint64_t *d_offsets, uint32_t ns
 
 template void msd_prepare<uint32_t>();
 template void msd_prepare<uint64_t>();
+template void msd_prepare<u128>();
+template void launch_msd_segmented<u128>(const Work &, const uint64_t *, uint32_t, cudaStream_t, Recorder &, int);
+template void launch_msd<u128>(const Work &, cudaStream_t, Recorder &, int);
 template void launch_msd_segmented<uint32_t>(const Work &, const uint64_t *, uint32_t, cudaStream_t, Recorder &, int);
 template void launch_msd_segmented<uint64_t>(const Work &, const uint64_t *, uint32_t, cudaStream_t, Recorder &, int);
 template void launch_msd<uint32_t>(const Work &, cudaStream_t, Recorder &, int);

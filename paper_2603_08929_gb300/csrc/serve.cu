@@ -43,9 +43,9 @@ uint64_t now_ns() {
 }
 
 int key_bytes(bsort_dtype dt) {
-    static const int b[] = {1, 1, 2, 2, 2, 4, 4, 4, 8, 8, 8, 2};
+    static const int b[] = {1, 1, 2, 2, 2, 4, 4, 4, 8, 8, 8, 2, 16, 16};
     const int i = static_cast<int>(dt);
-    return i >= 0 && i <= 11 ? b[i] : 0;
+    return i >= 0 && i <= 13 ? b[i] : 0;
 }
 
 // Requests one segmented sort gathers (descriptor passed by value).
@@ -339,7 +339,7 @@ bsort_status bsort_server_create_multi(const bsort_server_config *cfg, const int
     // segmented workspace and staging of batch_keys keys (8-byte keys at most)
     size_t ws = 0, seg_ws = 0;
     const size_t gkeys = cfg->batch_keys;
-    for (int dt = 0; dt <= 11; ++dt) {
+    for (int dt = 0; dt <= 11; ++dt) {  // the dtypes the loop serves
         size_t b = 0;
         if (bsort_workspace_bytes(cfg->max_request_keys, static_cast<bsort_dtype>(dt),
                                   static_cast<bsort_mode>(cfg->mode), &b) == BSORT_OK &&
@@ -404,7 +404,7 @@ bsort_status bsort_server_submit(bsort_server *s, void *keys, size_t n, bsort_dt
     if (!s) return BSORT_ERR_INVALID_ARG;
     const int b = key_bytes(dt);
     if (!b) return BSORT_ERR_INVALID_ARG;
-    if (n > s->cfg.max_request_keys) return BSORT_ERR_UNSUPPORTED;
+    if (b > 8 || n > s->cfg.max_request_keys) return BSORT_ERR_UNSUPPORTED;  // keys of up to 8 bytes
     if (n > 1 && !keys) return BSORT_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(keys) % b) return BSORT_ERR_MISALIGNED;
     if (s->fatal.load()) return static_cast<bsort_status>(s->fatal.load());

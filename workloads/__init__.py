@@ -43,6 +43,7 @@ _M2 = np.uint64(0x94D049BB133111EB)
 
 DTYPES = ["uint8", "int8", "uint16", "int16", "float16", "uint32", "int32", "float32",
           "uint64", "int64", "float64", "bfloat16"]
+WIDE_DTYPES = ["uint128", "int128"]  # uint64 (n, 2) arrays, low word first
 DISTS = ["uniform", "zipf", "normal", "distinct8", "sorted", "reverse", "float_edge", "normal01"]
 
 _UINT = {1: np.uint8, 2: np.uint16, 4: np.uint32, 8: np.uint64}
@@ -112,7 +113,7 @@ def normal(seed: int, stream: int, count: int, mean: float = 0.0, std: float = 1
 
 def stream_id(dist: str, dtype: str, sub: int = 0) -> int:
     """Stream number of (distribution, dtype, sub-stream); fits in 24 bits."""
-    return ((DISTS.index(dist) << 8 | DTYPES.index(dtype)) << 4) | sub
+    return ((DISTS.index(dist) << 8 | (DTYPES + WIDE_DTYPES).index(dtype)) << 4) | sub
 
 
 def _bits_dtype(dtype: np.dtype):
@@ -182,11 +183,44 @@ def _make_bf16(dist: str, n: int, seed: int) -> np.ndarray:
     raise ValueError("unknown distribution %r" % dist)
 
 
+def _make_wide(dist: str, n: int, seed: int, name: str) -> np.ndarray:
+    """128-bit integer inputs as a uint64 array of shape (n, 2), low word
+    first (numpy has no 128-bit dtype): uniform bits; Zipf(1.2) over 2^16
+    patterns and 8 patterns, both drawn as uniform 128-bit words (repeats
+    among 2^16 such draws are vanishingly unlikely); normal(0, 1) rounded to
+    the nearest integer (clipped at 0 for unsigned keys), sign-extended."""
+    if dist == "uniform":
+        return np.stack([words(seed, stream_id(dist, name, 0), 0, n), words(seed, stream_id(dist, name, 1), 0, n)],
+                        axis=1)
+    if dist in ("zipf", "distinct8"):
+        k = 1 << 16 if dist == "zipf" else 8
+        vals = np.stack([words(seed, stream_id(dist, name, 3), 0, k), words(seed, stream_id(dist, name, 4), 0, k)],
+                        axis=1)
+        if dist == "distinct8":
+            pick = (words(seed, stream_id(dist, name, 2), 0, n) >> np.uint64(61)).astype(np.int64)
+        else:
+            cdf = np.cumsum(np.arange(1, k + 1, dtype=np.float64) ** -1.2)
+            cdf /= cdf[-1]
+            pick = np.minimum(np.searchsorted(cdf, uniform01(seed, stream_id(dist, name, 2), n), side="right"), k - 1)
+        return vals[pick]
+    if dist == "normal01":
+        v = np.rint(normal(seed, stream_id(dist, name), n, 0.0, 1.0)).astype(np.int64)
+        if name == "uint128":
+            v = np.maximum(v, 0)
+        lo = v.view(np.uint64)
+        hi = np.where(v < 0, np.uint64(0xFFFFFFFFFFFFFFFF), np.uint64(0))
+        return np.stack([lo, hi], axis=1)
+    raise ValueError("unknown distribution %r for 128-bit keys" % dist)
+
+
 def make(dist: str, dtype, n: int, seed: int = 0) -> np.ndarray:
     """One input array of ``n`` keys; identical for identical arguments.
-    ``dtype`` "bfloat16" gives uint16 bit patterns."""
+    ``dtype`` "bfloat16" gives uint16 bit patterns; "uint128" / "int128" a
+    uint64 array of shape (n, 2), low word first."""
     if str(dtype) == "bfloat16":
         return _make_bf16(dist, n, seed)
+    if str(dtype) in ("uint128", "int128"):
+        return _make_wide(dist, n, seed, str(dtype))
     dtype = np.dtype(dtype)
     name = dtype.name
     if dist == "uniform":
