@@ -219,7 +219,10 @@ def host_cpu() -> dict:
 
 
 def oracle_sort(O, x, descending, dtype):
-    """The oracle's sort of x (bfloat16 arrives as uint16 bit patterns)."""
+    """The oracle's sort of x (bfloat16 arrives as uint16 bit patterns,
+    128-bit keys as uint64 (n, 2) arrays)."""
+    if dtype in ("uint128", "int128"):
+        return O.bsort128(x, signed=dtype == "int128", descending=descending)
     if dtype == "bfloat16":
         w = x.astype(np.uint64)
         O.bsort_words(w, O.BF16, descending)
@@ -231,7 +234,7 @@ def cpu_baseline(x, descending, sample_log2, dtype=None):
     """The oracle (literal partition, single thread) on the first 2^k keys."""
     import oracle as O
     O.build()
-    m = min(x.size, 1 << sample_log2)
+    m = min(x.shape[0], 1 << sample_log2)
     sample = np.ascontiguousarray(x[:m])
     t0 = time.perf_counter()
     oracle_sort(O, sample, descending, dtype)
@@ -601,9 +604,11 @@ def main():
 
     n = 1 << args.log2n
     x = W.make(args.dist, args.dtype, n, seed=args.seed + rank)
-    esize = x.dtype.itemsize
+    wide = args.dtype in W.WIDE_DTYPES  # 16-byte keys: uint64 (n, 2) arrays, passed with a dtype override
+    kdt = args.dtype if wide else None
+    esize = 16 if wide else x.dtype.itemsize
     total_steps = args.warmup + args.steps
-    base = torch.from_numpy(x).to(dev)
+    base = torch.from_numpy(x.view(np.int64) if wide else x).to(dev)
     if args.dtype == "bfloat16":  # the generator gives bfloat16 as uint16 bit patterns
         base = base.view(torch.bfloat16)
     bufs = [base.clone() for _ in range(total_steps)]
@@ -618,7 +623,7 @@ def main():
     stream = torch.cuda.current_stream()
 
     for i in range(args.warmup):
-        bs.bsort_keys_ws(h, bufs[i], ws, descending=args.desc, stream=stream, mode=mode)
+        bs.bsort_keys_ws(h, bufs[i], ws, descending=args.desc, stream=stream, mode=mode, dtype=kdt)
     torch.cuda.synchronize()
     if h.get_error(stream) != 0:
         raise RuntimeError("device error word set during warm-up")
@@ -635,7 +640,7 @@ def main():
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for i in range(args.warmup, total_steps):
-            bs.bsort_keys_ws(h, bufs[i], ws, descending=args.desc, stream=stream, mode=mode)
+            bs.bsort_keys_ws(h, bufs[i], ws, descending=args.desc, stream=stream, mode=mode, dtype=kdt)
         e1.record(stream)
         torch.cuda.synchronize()
         return e0.elapsed_time(e1)
@@ -724,19 +729,19 @@ def main():
         line["clocks"] = clock_info
 
     if not args.no_e2e:
-        host = torch.from_numpy(x.copy()).pin_memory()
+        host = torch.from_numpy(x.view(np.int64).copy() if wide else x.copy()).pin_memory()
         if args.dtype == "bfloat16":
             host = host.view(torch.bfloat16)
         pristine = host.clone()
         for _ in range(2):
             host.copy_(pristine)
-            bs.bsort_keys_host(host, descending=args.desc)
+            bs.bsort_keys_host(host, descending=args.desc, dtype=kdt)
         ts = []
         for _ in range(max(3, min(args.steps, 5))):
             host.copy_(pristine)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            bs.bsort_keys_host(host, descending=args.desc)
+            bs.bsort_keys_host(host, descending=args.desc, dtype=kdt)
             ts.append(time.perf_counter() - t0)
         e2e_s = statistics.median(ts)
         line["e2e"] = {"value": n / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": n * esize,

@@ -623,15 +623,21 @@ def selftest_bounded_wait(stream=None) -> int:
     return int(lib().bsort_selftest_bounded_wait(_stream_ptr(stream)))
 
 
-def bsort_keys_host(keys, descending: bool = False, stream=None) -> None:
-    """End-to-end sort of a host array (numpy array or CPU tensor), in place."""
+def bsort_keys_host(keys, descending: bool = False, stream=None, dtype=None) -> None:
+    """End-to-end sort of a host array (numpy array or CPU tensor), in place;
+    ``dtype`` reads its bytes as keys of that dtype (e.g. "uint128")."""
     if isinstance(keys, np.ndarray):
         if not keys.flags.c_contiguous:
             raise ValueError("bsort sorts contiguous arrays only")
         ptr, n, code = keys.ctypes.data, keys.size, _dtype_code(keys.dtype.name)
+        nbytes = keys.nbytes
     else:
         if keys.is_cuda or not keys.is_contiguous():
             raise TypeError("expected a contiguous CPU tensor")
         ptr, n, code = keys.data_ptr(), keys.numel(), _dtype_code(keys.dtype)
+        nbytes = keys.numel() * keys.element_size()
+    if dtype is not None:
+        name = str(dtype).replace("torch.", "")
+        n, code = nbytes // KEY_BYTES[name], _dtype_code(name)
     _check(lib().bsort_keys_host(ctypes.c_void_p(ptr), n, code, int(bool(descending)),
                                  _stream_ptr(stream)), "bsort_keys_host")

@@ -254,4 +254,32 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 
 __device__ __forceinline__ void set_error(Ctl *ctl, uint32_t bits) { atomicOr(&ctl->error, bits); }
 
+// Chunk records of the buckets of list q (the ones a level's classify just
+// opened), written by the whole grid: one warp per bucket, its chunks in
+// order.  A bucket's first chunk starts at the bucket; the others start on
+// the chunk grid of the 16-byte-aligned base of the bucket (128 / w keys per
+// 16 bytes), so every chunk after the first is an aligned window.
+__device__ __forceinline__ void write_child_chunks(const Work &wk, int q) {
+    const uint32_t nb = min(wk.ctl->n_buckets[q], wk.max_buckets);
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    const uint64_t vk = 128u / static_cast<uint32_t>(wk.w);
+    for (uint32_t i = gw; i < nb; i += nw) {
+        const Bucket b = wk.buckets[q][i];
+        const uint64_t base = b.start - b.start % vk;
+        const uint64_t end = b.start + b.len;
+        for (uint32_t k = lane; k < b.num_chunks; k += 32) {
+            if (b.first_chunk + k >= wk.max_chunks) break;
+            const uint64_t cs = k == 0 ? b.start : base + static_cast<uint64_t>(k) * wk.chunk_keys;
+            const uint64_t ce_lim = base + static_cast<uint64_t>(k + 1) * wk.chunk_keys;
+            Chunk ch;
+            ch.start = cs;
+            ch.len = static_cast<uint32_t>((ce_lim < end ? ce_lim : end) - cs);
+            ch.bucket = i;
+            wk.chunks[q][b.first_chunk + k] = ch;
+        }
+    }
+}
+
 }  // namespace bsort

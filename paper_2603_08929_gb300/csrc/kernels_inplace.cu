@@ -117,6 +117,7 @@ __global__ void k_ip_plan(Work wk, int level) {
     constexpr int B = IpCfg<K>::B;
     const int p = level & 1;
     if (wk.ctl->error) return;
+    write_child_chunks(wk, p ^ 1);  // records of the buckets this level's classify opened
     const uint32_t nb = wk.ctl->n_buckets[p];
     __shared__ uint32_t sh[3];
     for (uint32_t i = blockIdx.x; i < nb; i += gridDim.x) {

@@ -652,7 +652,7 @@ template <typename K, int THREADS, int NB>
 __global__ void __launch_bounds__(THREADS) k_hist(Work wk, int level) {
     pdl_enter();
     constexpr int WARPS = THREADS / 32;
-    constexpr int ROWS = NB <= kBins ? WARPS : 4;
+    constexpr int ROWS = NB <= kBins ? WARPS / 2 : 4;  // two warps per row
     __shared__ uint32_t sh[ROWS * NB];
     __shared__ K ta[WARPS], to[WARPS];
     const int p = level & 1;
@@ -754,8 +754,7 @@ __global__ void __launch_bounds__(THREADS) k_colscan(Work wk, int level) {
 // children that become buckets, with their start/len/h/src in the arguments.
 template <int THREADS>
 __device__ void emit_buckets(const Work &wk, int q, bool take, uint64_t start, uint64_t len, int h, int src, int raw,
-                             uint32_t *tmp, uint32_t *sh_choff, uint32_t *sh_slot, uint32_t *sh_bases,
-                             unsigned long long *sh_cstart, unsigned long long *sh_cend) {
+                             uint32_t *tmp, uint32_t *sh_bases) {
     // chunk boundaries sit on 16-byte boundaries of the buffer except the
     // bucket's own start, so every tile after the first is an aligned window
     const uint64_t vk = 128u / static_cast<uint32_t>(wk.w);
@@ -774,10 +773,6 @@ __device__ void emit_buckets(const Work &wk, int q, bool take, uint64_t start, u
         sh_bases[0] = ok ? b0 : 0xffffffffu;
         sh_bases[1] = c0;
     }
-    sh_choff[threadIdx.x] = ch_off;
-    sh_slot[threadIdx.x] = take ? slot_off : 0xffffffffu;
-    sh_cstart[threadIdx.x] = start;  // the children's extents, for the chunk records below
-    sh_cend[threadIdx.x] = start + len;
     __syncthreads();
     const uint32_t b0 = sh_bases[0], c0 = sh_bases[1];
     if (b0 != 0xffffffffu) {
@@ -795,29 +790,8 @@ __device__ void emit_buckets(const Work &wk, int q, bool take, uint64_t start, u
             wk.buckets[q][b0 + slot_off] = nb;
         }
         __syncthreads();
-        // chunk records: k-th chunk of this parent belongs to the child whose
-        // [choff, choff + nchunks) contains k
-        for (uint32_t k = threadIdx.x; k < nc_total; k += THREADS) {
-            int lo = 0, hi = THREADS - 1;  // largest d with choff[d] <= k and a bucket
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (sh_choff[mid] <= k) lo = mid;
-                else hi = mid - 1;
-            }
-            // children without chunks never satisfy choff <= k past the owner
-            const int d = lo;
-            const uint64_t cstart = sh_cstart[d], cend = sh_cend[d];
-            const uint32_t i = k - sh_choff[d];
-            const uint64_t nb_base = cstart - cstart % vk;
-            const uint64_t cs = i == 0 ? cstart : nb_base + static_cast<uint64_t>(i) * wk.chunk_keys;
-            const uint64_t ce_lim = nb_base + static_cast<uint64_t>(i + 1) * wk.chunk_keys;
-            const uint64_t ce = ce_lim < cend ? ce_lim : cend;
-            Chunk ch;
-            ch.start = cs;
-            ch.len = static_cast<uint32_t>(ce - cs);
-            ch.bucket = b0 + sh_slot[d];
-            wk.chunks[q][c0 + k] = ch;
-        }
+        // the children's chunk records are written by the next kernel's grid
+        // (write_child_chunks), not by this one CTA
     }
     __syncthreads();
 }
@@ -856,8 +830,7 @@ __global__ void __launch_bounds__(THREADS) k_classify(Work wk, int level) {
     __shared__ K ta[THREADS / 32], to[THREADS / 32];
     __shared__ unsigned long long tmp64[THREADS / 32 + 1];
     __shared__ uint32_t tmp[THREADS / 32 + 1];
-    __shared__ uint32_t sh_choff[THREADS], sh_slot[THREADS], sh_bases[2];
-    __shared__ unsigned long long sh_cstart[THREADS], sh_cend[THREADS];
+    __shared__ uint32_t sh_bases[2];
     __shared__ int itmp[THREADS / 32 + 1], sh_i2[THREADS];
     __shared__ uint32_t sh_u[THREADS], sh_u2[THREADS];
     const int p = level & 1, q = p ^ 1;
@@ -905,8 +878,7 @@ __global__ void __launch_bounds__(THREADS) k_classify(Work wk, int level) {
         if (hb < shift) {
             // the digit is constant: re-open the bucket at its highest varying bit
             if (threadIdx.x == 0) wk.buckets[p][i].scatter = 0;
-            emit_buckets<THREADS>(wk, q, threadIdx.x == 0, b.start, b.len, hb + 1, b.src, b.raw, tmp, sh_choff,
-                                  sh_slot, sh_bases, sh_cstart, sh_cend);
+            emit_buckets<THREADS>(wk, q, threadIdx.x == 0, b.start, b.len, hb + 1, b.src, b.raw, tmp, sh_bases);
             continue;
         }
         if (threadIdx.x == 0) {
@@ -932,8 +904,7 @@ __global__ void __launch_bounds__(THREADS) k_classify(Work wk, int level) {
             if (big && hc == 0) {
                 emit_fill<K>(wk, base, tot, static_cast<K>(high_bits<K>(a, b.h) | static_cast<K>(d)));
             }
-            emit_buckets<THREADS>(wk, q, big && hc > 0, base, tot, hc, dst, 0, tmp, sh_choff, sh_slot, sh_bases,
-                                  sh_cstart, sh_cend);
+            emit_buckets<THREADS>(wk, q, big && hc > 0, base, tot, hc, dst, 0, tmp, sh_bases);
             // Small children become finish units.  Children of at most
             // merge_cap / 4 keys ("tiny") merge with their tiny neighbours:
             // inside a run of adjacent tiny children (empty children do not
@@ -1121,6 +1092,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_scatter(Work wk, int level) {
     const int p = level & 1;
     const int t = threadIdx.x;
     if (wk.ctl->error) return;
+    write_child_chunks(wk, p ^ 1);  // records of the buckets this level's classify opened
     if (t == 0) *bad = 0;  // stays 0 unless a check fails (then the CTA stops)
     const uint32_t nch = wk.ctl->n_chunks[p];
     // Chunk metadata arrives by cp.async two chunks ahead in a ring of three
