@@ -652,7 +652,7 @@ template <typename K, int THREADS, int NB>
 __global__ void __launch_bounds__(THREADS) k_hist(Work wk, int level) {
     pdl_enter();
     constexpr int WARPS = THREADS / 32;
-    constexpr int ROWS = NB <= kBins ? WARPS / 2 : 4;  // two warps per row
+    constexpr int ROWS = NB <= kBins ? WARPS / 4 : 4;  // four warps per row
     __shared__ uint32_t sh[ROWS * NB];
     __shared__ K ta[WARPS], to[WARPS];
     const int p = level & 1;
