@@ -77,10 +77,17 @@ struct MsdLayout {
     bool inplace;
     size_t ip_big, ip_stripes, ip_ncnt, ip_rem, ip_part, ip_ovf, ip_state, lists_end;
     uint32_t max_big, max_stripes, max_slots;
+    // stable key-value sort: value bytes (0: keys only), and whether the
+    // values are positions made by the sort (then vals0 holds their parity-0
+    // buffer; otherwise the caller's values are that buffer)
+    int kv_bytes;
+    bool kv_pos;
+    size_t vals0, vals1;
 };
 
-MsdLayout msd_layout(size_t n, int key_bytes, size_t nseg = 0, bool inplace = false, const Tuning &tune = Tuning()) {
-    const MsdShape s = msd_shape(key_bytes, tune, inplace);
+MsdLayout msd_layout(size_t n, int key_bytes, size_t nseg = 0, bool inplace = false, const Tuning &tune = Tuning(),
+                     int kv_bytes = 0, bool kv_pos = false) {
+    const MsdShape s = msd_shape(key_bytes, tune, inplace, kv_bytes);
     MsdLayout L;
     // finish units hold at least merge_cap / 4 keys unless merged, and merged
     // groups reach merge_cap unless a run ends: the unit count per level is
@@ -103,6 +110,10 @@ MsdLayout msd_layout(size_t n, int key_bytes, size_t nseg = 0, bool inplace = fa
     };
     L.inplace = inplace;
     L.alt = take(inplace ? 0 : n * key_bytes);
+    L.kv_bytes = kv_bytes;
+    L.kv_pos = kv_pos;
+    L.vals0 = take(kv_pos ? n * kv_bytes : 0);
+    L.vals1 = take(kv_bytes ? n * kv_bytes : 0);
     L.ctl = take(sizeof(Ctl));
     L.buckets0 = take(sizeof(Bucket) * L.max_buckets);
     L.buckets1 = take(sizeof(Bucket) * L.max_buckets);
@@ -220,7 +231,7 @@ bsort_status check_args(const void *keys, size_t n, bsort_dtype dt, DtypeInfo *d
 
 Work make_work(const MsdLayout &L, char *ws, void *keys, size_t n, const DtypeInfo &di, const Codec &codec,
                const Tuning &tune = Tuning()) {
-    const MsdShape s = msd_shape(di.bytes, tune, L.inplace);
+    const MsdShape s = msd_shape(di.bytes, tune, L.inplace, L.kv_bytes);
     Work wk;
     wk.ctl = reinterpret_cast<Ctl *>(ws + L.ctl);
     wk.buckets[0] = reinterpret_cast<Bucket *>(ws + L.buckets0);
@@ -252,6 +263,12 @@ Work make_work(const MsdLayout &L, char *ws, void *keys, size_t n, const DtypeIn
     wk.stop_level = s.levels;
     wk.keys_vec_ok = (reinterpret_cast<uintptr_t>(keys) & 15) == 0;
     wk.inplace = L.inplace;
+    wk.kv = L.kv_bytes;
+    wk.kv_positions = L.kv_pos;
+    wk.vals = L.kv_pos ? static_cast<void *>(ws + L.vals0) : nullptr;  // else the caller's values
+    wk.vals_alt = L.kv_bytes ? static_cast<void *>(ws + L.vals1) : nullptr;
+    wk.out_vals = nullptr;
+    wk.out_idx = nullptr;
     wk.ip_big = L.inplace ? reinterpret_cast<IpBig *>(ws + L.ip_big) : nullptr;
     wk.ip_stripes = L.inplace ? reinterpret_cast<IpStripe *>(ws + L.ip_stripes) : nullptr;
     wk.ip_ncnt = L.inplace ? reinterpret_cast<uint32_t *>(ws + L.ip_ncnt) : nullptr;
@@ -292,7 +309,8 @@ const Tuning &tune_of(const bsort_handle *h, int key_bytes) {
 }
 
 bsort_status run_sort(bsort_handle *h, void *keys, size_t n, const DtypeInfo &di, int descending,
-                      void *workspace, size_t ws_bytes, cudaStream_t st, bool inplace = false) {
+                      void *workspace, size_t ws_bytes, cudaStream_t st, bool inplace = false,
+                      const Tuning *tune_override = nullptr) {
     (void)cudaGetLastError();  // clear a stale non-sticky error
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return BSORT_ERR_CUDA;
@@ -331,7 +349,7 @@ bsort_status run_sort(bsort_handle *h, void *keys, size_t n, const DtypeInfo &di
         h->last_fixed_aux = L.total;
     } else {
         if (inplace && di.bytes > 8) return BSORT_ERR_UNSUPPORTED;
-        const Tuning &tune = tune_of(h, di.bytes);
+        const Tuning &tune = tune_override ? *tune_override : tune_of(h, di.bytes);
         const MsdLayout L = msd_layout(n, di.bytes, 0, inplace, tune);
         if (ws_bytes < L.total) return BSORT_ERR_WORKSPACE_TOO_SMALL;
         h->last_inplace = inplace;
@@ -411,10 +429,10 @@ size_t workspace_for(size_t n, const DtypeInfo &di, bool inplace = false, const 
     return di.bytes <= 2 ? count_layout(n, di.bytes).total : msd_layout(n, di.bytes, 0, inplace, tune).total;
 }
 
-// Key-value sorting workspace: the 64-bit words, the first sort's
-// permutation (8-byte keys), the final input positions, then an 8-byte MSD
-// workspace whose alternate buffer (its first n * 8 bytes) doubles as the
-// gather target afterwards, and one error word.
+// Key-value sorting workspace of 1- and 2-byte keys: the 64-bit words, the
+// final input positions, then an 8-byte MSD workspace whose alternate buffer
+// (its first n * 8 bytes) doubles as the gather target afterwards, and one
+// error word.  (The layout keeps room for the two-sort form of wider keys.)
 struct PairsLayout {
     size_t words, perm, idx, err, inner, inner_bytes, total;
 };
@@ -437,6 +455,34 @@ PairsLayout pairs_layout(size_t n, int key_bytes, const Tuning &tune8) {
     return L;
 }
 
+// Key-value sorting workspace of 4- and 8-byte keys (the value-carrying MSD
+// path): the MSD workspace with carry_bytes-wide value buffers (positions:
+// both parities, else the alternate one), then the gather target of values
+// that follow positions.
+struct PairsKvLayout {
+    MsdLayout msd;
+    size_t tmp, total;
+};
+
+PairsKvLayout pairs_kv_layout(size_t n, int key_bytes, int carry_bytes, bool positions, size_t gather_bytes) {
+    PairsKvLayout P;
+    P.msd = msd_layout(n, key_bytes, 0, false, Tuning(), carry_bytes, positions);
+    P.tmp = P.msd.total;
+    P.total = align_up(P.tmp + gather_bytes * n);
+    return P;
+}
+
+// Workspace of a key-value sort of n keys of key_bytes, for every form of
+// request (values carried, positions, positions then a gather of 8-byte values).
+size_t pairs_workspace_for(size_t n, int key_bytes, const Tuning &tune8) {
+    if (key_bytes <= 2) return pairs_layout(n, key_bytes, tune8).total;
+    size_t b = msd_layout(n, key_bytes).total;  // keys alone (no values, no positions asked for)
+    b = std::max(b, pairs_kv_layout(n, key_bytes, 4, false, 0).total);
+    b = std::max(b, pairs_kv_layout(n, key_bytes, 8, false, 0).total);
+    b = std::max(b, pairs_kv_layout(n, key_bytes, 4, true, 8).total);
+    return b;
+}
+
 bool to_tuning(const bsort_tuning *in, int key_bytes, Tuning *out) {
     Tuning t;
     if (in) {
@@ -448,6 +494,61 @@ bool to_tuning(const bsort_tuning *in, int key_bytes, Tuning *out) {
     if (!tuning_valid(key_bytes, t)) return false;
     *out = t;
     return true;
+}
+
+// Stable key-value sort of 4- or 8-byte keys by the value-carrying MSD
+// path.  Values of 4 or 8 bytes travel with their keys when no positions are
+// asked for; otherwise 32-bit input positions travel (made when a key is
+// first read), the int64 positions are written beside the sorted keys, and
+// the values (any width) follow by one gather along the positions.
+bsort_status run_pairs_kv(bsort_handle *h, void *keys, void *values, size_t value_bytes, int64_t *indices, size_t n,
+                          const DtypeInfo &di, int descending, void *workspace, cudaStream_t st) {
+    (void)cudaGetLastError();
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return BSORT_ERR_CUDA;
+    const int sms = num_sms_of(dev);
+    if (h->profiling) {
+        const bsort_status es = ensure_events(h);
+        if (es != BSORT_OK) return es;
+    }
+    begin_call(h, st);
+    const bool carry = values && !indices && (value_bytes == 4 || value_bytes == 8);
+    const int cb = carry ? static_cast<int>(value_bytes) : 4;
+    const bool gather = !carry && values;
+    const PairsKvLayout P = pairs_kv_layout(n, di.bytes, cb, !carry, gather ? value_bytes : 0);
+    char *ws = static_cast<char *>(workspace);
+    Work wk = make_work(P.msd, ws, keys, n, di, codec_for(di, descending));
+    if (carry) {
+        wk.vals = values;
+        wk.out_vals = values;
+    } else {
+        wk.out_idx = indices;
+        wk.out_vals = gather ? wk.vals : nullptr;
+    }
+    if (di.bytes == 4) {
+        if (cb == 4) launch_msd_kv<uint32_t, uint32_t>(wk, st, h->rec, sms);
+        else launch_msd_kv<uint32_t, uint64_t>(wk, st, h->rec, sms);
+    } else {
+        if (cb == 4) launch_msd_kv<uint64_t, uint32_t>(wk, st, h->rec, sms);
+        else launch_msd_kv<uint64_t, uint64_t>(wk, st, h->rec, sms);
+    }
+    h->last_stream = st;
+    h->last_n = n;
+    h->last_key_bytes = di.bytes;
+    h->last_path = 3;
+    h->last_ctl = wk.ctl;
+    h->last_inplace = false;
+    h->last_fixed_aux = P.total;
+    if (gather) {
+        h->rec.begin(BSORT_K_FILL, -1);
+        launch_gather(values, static_cast<int>(value_bytes), static_cast<const uint32_t *>(wk.vals), n, ws + P.tmp,
+                      wk.ctl, st, sms);
+        h->rec.end();
+        if (cudaMemcpyAsync(values, ws + P.tmp, value_bytes * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return BSORT_ERR_CUDA;
+    }
+    end_call(h, st, n, di.bytes);
+    return cudaGetLastError() == cudaSuccess ? BSORT_OK : BSORT_ERR_CUDA;
 }
 
 }  // namespace
@@ -523,7 +624,7 @@ bsort_status bsort_pairs_workspace_bytes(size_t n, bsort_dtype dt, size_t *bytes
     DtypeInfo di;
     if (!bytes || !dtype_info(dt, &di)) return BSORT_ERR_INVALID_ARG;
     if (di.bytes > 8) return BSORT_ERR_UNSUPPORTED;
-    *bytes = pairs_layout(n, di.bytes, Tuning()).total;
+    *bytes = pairs_workspace_for(n, di.bytes, Tuning());
     return BSORT_OK;
 }
 
@@ -533,7 +634,7 @@ bsort_status bsort_pairs_workspace_bytes_tuned(size_t n, bsort_dtype dt, const b
     if (di.bytes > 8) return BSORT_ERR_UNSUPPORTED;
     Tuning t;
     if (!to_tuning(tuning8, 8, &t)) return BSORT_ERR_INVALID_ARG;
-    *bytes = pairs_layout(n, di.bytes, t).total;
+    *bytes = pairs_workspace_for(n, di.bytes, t);
     return BSORT_OK;
 }
 
@@ -560,6 +661,14 @@ bsort_status bsort_pairs_ws(bsort_handle *handle, void *keys, void *values, size
     }
     if (!workspace) return BSORT_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(workspace) % kAlign) return BSORT_ERR_MISALIGNED;
+    if (di.bytes >= 4) {
+        if (ws_bytes < pairs_workspace_for(n, di.bytes, Tuning())) return BSORT_ERR_WORKSPACE_TOO_SMALL;
+        if (!values && !indices) {  // equal keys are bit-identical: the keys-only sort gives the same keys
+            const Tuning defaults;
+            return run_sort(handle, keys, n, di, descending, workspace, ws_bytes, st, false, &defaults);
+        }
+        return run_pairs_kv(handle, keys, values, value_bytes, indices, n, di, descending, workspace, st);
+    }
     const PairsLayout L = pairs_layout(n, di.bytes, handle->tune[1]);
     if (ws_bytes < L.total) return BSORT_ERR_WORKSPACE_TOO_SMALL;
     (void)cudaGetLastError();

@@ -75,7 +75,7 @@ struct Fill {
     uint64_t value;
     uint64_t value_hi;
     uint32_t len;
-    uint32_t pad;
+    uint32_t src;  // key-value sorting: the buffer parity the run's values sit in
 };
 
 // In-place mode: a bucket of this level too large for the whole-bucket
@@ -144,6 +144,14 @@ struct Work {
     bool keys_vec_ok;     // caller's buffer is 16-byte aligned (vector loads)
     // in-place mode (digit permutation inside the caller's buffer)
     bool inplace;
+    // key-value sorting (stable): values travel beside the keys, in buffers of
+    // the same parity (vals beside `keys`, vals_alt beside `alt`)
+    int32_t kv;             // 0: keys only; else the value bytes (4 or 8)
+    bool kv_positions;      // the values are the input positions (argsort), made at the first read
+    void *vals;
+    void *vals_alt;
+    void *out_vals;         // where the sorted values go (the caller's values, or u32 positions)
+    int64_t *out_idx;       // argsort: int64 positions written beside (may be null)
     IpBig *ip_big;          // [max_big]
     IpStripe *ip_stripes;   // [max_stripes]
     uint32_t *ip_ncnt;      // [max_big][kBins] full blocks per digit

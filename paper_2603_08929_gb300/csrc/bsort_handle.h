@@ -19,7 +19,7 @@ struct bsort_handle {
     // state of the last call
     Ctl *last_ctl = nullptr;
     cudaStream_t last_stream = nullptr;
-    int last_path = 0;  // 0 none, 1 counting, 2 msd
+    int last_path = 0;  // 0 none, 1 counting, 2 msd, 3 key-value msd
     bool last_inplace = false;
     size_t last_fixed_aux = 0;  // bytes of the last call's workspace outside the in-place buffers
     int last_key_bytes = 0;

@@ -76,7 +76,9 @@ struct Tuning {
 
 // false: a field is out of range.
 bool tuning_valid(int key_bytes, const Tuning &t);
-MsdShape msd_shape(int key_bytes, const Tuning &t = Tuning(), bool inplace = false);
+// kv_bytes: 0 for keys only, else the value bytes of the stable key-value
+// sort (4 or 8), which has its own fixed shape.
+MsdShape msd_shape(int key_bytes, const Tuning &t = Tuning(), bool inplace = false, int kv_bytes = 0);
 
 // Launches the whole MSD pipeline for 4- or 8-byte keys.
 template <typename K>
@@ -87,6 +89,11 @@ void launch_msd(const Work &wk, cudaStream_t st, Recorder &rec, int num_sms);
 template <typename K>
 void launch_msd_segmented(const Work &wk, const uint64_t *d_offsets, uint32_t nseg, cudaStream_t st, Recorder &rec,
                           int num_sms);
+
+// Stable key-value sort of 4- or 8-byte keys K with 4- or 8-byte values V
+// (Work.kv set): values travel with their keys through every level.
+template <typename K, typename V>
+void launch_msd_kv(const Work &wk, cudaStream_t st, Recorder &rec, int num_sms);
 
 // Sets kernel attributes (call before stream capture).
 template <typename K>

@@ -798,7 +798,7 @@ __device__ void emit_buckets(const Work &wk, int q, bool take, uint64_t start, u
 
 // Fill pieces for every thread whose `take` is set (thread-private loop).
 template <typename K>
-__device__ void emit_fill(const Work &wk, uint64_t start, uint64_t len, K value) {
+__device__ void emit_fill(const Work &wk, uint64_t start, uint64_t len, K value, int src) {
     const uint32_t pieces = static_cast<uint32_t>((len + kFillPiece - 1) / kFillPiece);
     const uint32_t f0 = atomicAdd(&wk.ctl->n_fills, pieces);
     if (f0 + pieces > wk.max_fills) {
@@ -814,7 +814,7 @@ __device__ void emit_fill(const Work &wk, uint64_t start, uint64_t len, K value)
         f.value = static_cast<uint64_t>(value);
         if constexpr (sizeof(K) > 8) f.value_hi = static_cast<uint64_t>(value >> 64);
         else f.value_hi = 0;
-        f.pad = 0;
+        f.src = static_cast<uint32_t>(src);
         wk.fills[f0 + i] = f;
     }
 }
@@ -867,7 +867,7 @@ __global__ void __launch_bounds__(THREADS) k_classify(Work wk, int level) {
         if (a == o) {  // every key identical: write the value, no sort needed
             if (threadIdx.x == 0) {
                 wk.buckets[p][i].scatter = 0;
-                emit_fill<K>(wk, b.start, b.len, a);
+                emit_fill<K>(wk, b.start, b.len, a, b.raw ? 2 : b.src);
             }
             continue;
         }
@@ -902,7 +902,7 @@ __global__ void __launch_bounds__(THREADS) k_classify(Work wk, int level) {
             const bool big = tot > wk.unit_cap;
             // children with no bits left are constant: value = common prefix | digit
             if (big && hc == 0) {
-                emit_fill<K>(wk, base, tot, static_cast<K>(high_bits<K>(a, b.h) | static_cast<K>(d)));
+                emit_fill<K>(wk, base, tot, static_cast<K>(high_bits<K>(a, b.h) | static_cast<K>(d)), dst);
             }
             emit_buckets<THREADS>(wk, q, big && hc > 0, base, tot, hc, dst, 0, tmp, sh_bases);
             // Small children become finish units.  Children of at most
@@ -1907,6 +1907,350 @@ __global__ void k_drain(Work wk, int level) {
     }
 }
 
+// ---- key-value sorting (stable): values travel with their keys -------------
+//
+// The keys-only levels partition freely inside a digit (equal keys are
+// bit-identical).  With values riding along, equal keys must keep their input
+// order, so the scatter and the finish below rank stably: a tile's keys sit
+// warp-striped (item j of lane l of warp w is tile index (w * ITEMS + j) * 32
+// + l) and each key's place is its digit's start in the tile plus the keys of
+// that digit before it in tile order -- per-(digit, warp) counters and
+// per-warp peer masks, as the stable LSD passes use.  The histogram, column
+// scan and classify steps only look at keys and are shared with keys-only
+// sorting; a chunk is one tile, so a chunk's stable tile order is its order.
+
+// Place of every item in the tile ordered by digit, ties in tile order.  The
+// peer masks must be zero on entry; they are zero again on return.
+template <typename K, int THREADS, int ITEMS, typename RS>
+__device__ __forceinline__ void stable_places(const K (&keys)[ITEMS], uint32_t vmask, int shift, uint32_t mask,
+                                              uint32_t (&place)[ITEMS]) {
+    constexpr int WARPS = THREADS / 32;
+    constexpr int STRIDE = WARPS + 1;
+    static_assert(THREADS >= kBins, "one thread per digit in the scans");
+    uint32_t *wc = RS::wc(), *wm0 = RS::wm(), *scan = RS::scan();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int t = threadIdx.x;
+    for (int i = t; i < (static_cast<int>(mask) + 1) * STRIDE; i += THREADS) wc[i] = 0;
+    __syncthreads();
+    const unsigned lt = lanemask_lt();
+    const unsigned bit = 1u << lane;
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        const bool valid = (vmask >> j) & 1u;
+        place[j] = 0;
+        if (__any_sync(kFull, valid)) {  // warp-uniform
+            uint32_t *wm = wm0 + ((j & 1) * WARPS + warp) * kBins;
+            const uint32_t d = static_cast<uint32_t>(keys[j] >> shift) & mask;
+            uint32_t *wcd = wc + d * STRIDE + warp;
+            if (valid) atomicOr(&wm[d], bit);
+            __syncwarp();
+            const uint32_t peers = wm[d];
+            const uint32_t before = *wcd;
+            __syncwarp();
+            const uint32_t r = __popc(peers & lt);
+            if (valid && r == 0) {
+                *wcd = before + __popc(peers);
+                wm[d] = 0;
+            }
+            place[j] = before + r;
+        }
+    }
+    __syncthreads();
+    // digit totals, their prefix, then each warp's start inside its digit
+    uint32_t run = 0;
+    if (t <= static_cast<int>(mask)) {
+#pragma unroll
+        for (int w = 0; w < WARPS; ++w) run += wc[t * STRIDE + w];
+    }
+    uint32_t total;
+    const uint32_t ex = block_exclusive_scan<THREADS>(run, scan, total);
+    if (t <= static_cast<int>(mask)) {
+        uint32_t acc = ex;
+#pragma unroll
+        for (int w = 0; w < WARPS; ++w) {
+            const uint32_t x = wc[t * STRIDE + w];
+            wc[t * STRIDE + w] = acc;
+            acc += x;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j)
+        if ((vmask >> j) & 1u)
+            place[j] += wc[(static_cast<uint32_t>(keys[j] >> shift) & mask) * STRIDE + warp];
+    __syncthreads();
+}
+
+// A value of the key-value sort: 4 or 8 bytes.
+template <int VB>
+struct ValT;
+template <>
+struct ValT<4> {
+    using T = uint32_t;
+};
+template <>
+struct ValT<8> {
+    using T = uint64_t;
+};
+
+template <typename V>
+__device__ __forceinline__ const V *vals_of(const Work &wk, int src) {
+    return static_cast<const V *>(src ? wk.vals_alt : wk.vals);
+}
+
+template <typename V>
+__device__ __forceinline__ V *vals_dst_of(const Work &wk, int src) {
+    return static_cast<V *>(src ? wk.vals : wk.vals_alt);
+}
+
+
+// Stable scatter of one level, keys and values: each chunk (one tile) is
+// loaded warp-striped, ranked stably by digit, staged (keys and values) in
+// digit order, and written out in staging order to its digit runs.  The
+// destinations come from the histogram pass exactly as in k_scatter; every
+// one is checked against the bucket before it is written.
+template <typename K, typename V, int THREADS, int ITEMS>
+struct ScatterKvSmem {
+    static constexpr int TILE = THREADS * ITEMS;
+    static constexpr size_t kVals = sizeof(K) * TILE;
+    static constexpr size_t kRank = ((kVals + sizeof(V) * TILE) + 15) & ~size_t(15);
+    using RS = RankSmem<THREADS, kRank, true>;
+    static constexpr size_t kOff = (RS::kEnd + 15) & ~size_t(15);  // u64[kBins]
+    static constexpr size_t kEnd = kOff + 8 * kBins;
+};
+
+template <typename K, typename V, int THREADS, int ITEMS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) k_scatter_kv(Work wk, int level) {
+    pdl_enter();
+    using SM = ScatterKvSmem<K, V, THREADS, ITEMS>;
+    using RS = typename SM::RS;
+    constexpr int WARPS = THREADS / 32;
+    constexpr int STRIDE = WARPS + 1;
+    K *sm_keys = reinterpret_cast<K *>(g_dyn_smem);
+    V *sm_vals = reinterpret_cast<V *>(g_dyn_smem + SM::kVals);
+    unsigned long long *off = reinterpret_cast<unsigned long long *>(g_dyn_smem + SM::kOff);
+    const int p = level & 1;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (wk.ctl->error) return;
+    write_child_chunks(wk, p ^ 1);  // records of the buckets this level's classify opened
+    for (int i = t; i < 2 * WARPS * kBins; i += THREADS) RS::wm()[i] = 0;  // peer masks start clear
+    const uint32_t nch = wk.ctl->n_chunks[p];
+    for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) {
+        __syncthreads();  // the previous chunk's staging is written out
+        const Chunk ch = wk.chunks[p][c];
+        const Bucket b = wk.buckets[p][ch.bucket];
+        if (!b.scatter) continue;  // block-uniform
+        const int r_eff = min(wk.radix_bits, b.h);
+        const int shift = b.h - r_eff;
+        const uint32_t mask = (1u << r_eff) - 1;
+        const K *__restrict__ src = src_of<K>(wk, b.src);
+        const V *__restrict__ vsrc = vals_of<V>(wk, b.src);
+        const bool make_pos = wk.kv_positions && b.raw;
+        K k[ITEMS];
+        V v[ITEMS];
+        uint32_t vmask = 0;
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            const uint32_t idx = static_cast<uint32_t>((warp * ITEMS + j) * 32 + lane);
+            k[j] = 0;
+            v[j] = 0;
+            if (idx < ch.len) {
+                k[j] = src[ch.start + idx];
+                v[j] = make_pos ? static_cast<V>(ch.start + idx) : vsrc[ch.start + idx];
+                vmask |= 1u << j;
+            }
+        }
+        if (b.raw) {
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) k[j] = encode_key(k[j], wk.codec);
+        }
+        uint32_t place[ITEMS];
+        stable_places<K, THREADS, ITEMS, RS>(k, vmask, shift, mask, place);
+        // digit d's run: staging slots from its tile start, destinations from
+        // the histogram's prefix (off[d] = destination - tile start)
+        if (t <= static_cast<int>(mask))
+            off[t] = b.start + wk.bucket_base[static_cast<size_t>(ch.bucket) * wk.bins + t] +
+                     wk.hist[static_cast<size_t>(t) * wk.max_chunks + c] - RS::wc()[t * STRIDE];
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            if ((vmask >> j) & 1u) {
+                sm_keys[place[j]] = k[j];
+                sm_vals[place[j]] = v[j];
+            }
+        }
+        __syncthreads();
+        K *__restrict__ dst = dst_of<K>(wk, b.src);
+        V *__restrict__ vdst = vals_dst_of<V>(wk, b.src);
+        bool oob = false;
+        for (uint32_t q = t; q < ch.len; q += THREADS) {
+            const K key = sm_keys[q];
+            const uint64_t pos = off[static_cast<uint32_t>(key >> shift) & mask] + q;
+            if (pos - b.start < b.len) {
+                dst[pos] = key;
+                vdst[pos] = sm_vals[q];
+            } else {
+                oob = true;
+            }
+        }
+        if (oob) set_error(wk.ctl, kErrBounds);
+    }
+}
+
+
+
+// Stable finish of a unit, keys and values: loaded warp-striped (input
+// order), then one stable pass per digit of at most 8 bits over the unit's
+// varying bits, least significant first, each staging keys and values in
+// shared memory; the last pass's staging is the sorted unit, written decoded
+// to its final place (values beside, or int64 positions for an argsort).
+template <typename K, typename V, int THREADS, int ITEMS>
+struct FinishKvSmem {
+    static constexpr int TILE = THREADS * ITEMS;
+    static constexpr int WARPS = THREADS / 32;
+    static constexpr size_t kVals = sizeof(K) * TILE;
+    static constexpr size_t kTa = (kVals + sizeof(V) * TILE + 15) & ~size_t(15);
+    static constexpr size_t kTo = kTa + sizeof(K) * WARPS;
+    static constexpr size_t kRank = (kTo + sizeof(K) * WARPS + 15) & ~size_t(15);
+    using RS = RankSmem<THREADS, kRank, true>;
+    static constexpr size_t kEnd = RS::kEnd;
+};
+
+template <typename K, typename V>
+__device__ __forceinline__ void kv_out(const Work &wk, uint64_t i, V v) {
+    if (wk.kv_positions) {
+        if (wk.out_idx) wk.out_idx[i] = static_cast<int64_t>(v);
+        if (wk.out_vals) static_cast<V *>(wk.out_vals)[i] = v;  // 32-bit positions for a gather of the values
+    } else {
+        static_cast<V *>(wk.out_vals)[i] = v;
+    }
+}
+
+template <typename K, typename V, int THREADS, int ITEMS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) k_finish_kv(Work wk) {
+    pdl_enter();
+    using SM = FinishKvSmem<K, V, THREADS, ITEMS>;
+    using RS = typename SM::RS;
+    constexpr int WARPS = THREADS / 32;
+    K *sm_keys = reinterpret_cast<K *>(g_dyn_smem);
+    V *sm_vals = reinterpret_cast<V *>(g_dyn_smem + SM::kVals);
+    K *ta = reinterpret_cast<K *>(g_dyn_smem + SM::kTa);
+    K *to = reinterpret_cast<K *>(g_dyn_smem + SM::kTo);
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (wk.ctl->error) return;
+    for (int i = t; i < 2 * WARPS * kBins; i += THREADS) RS::wm()[i] = 0;  // peer masks start clear
+    const uint32_t nu = min(wk.ctl->n_units, wk.max_units);
+    K *__restrict__ out = static_cast<K *>(wk.keys);
+    for (uint32_t u = blockIdx.x; u < nu; u += gridDim.x) {
+        __syncthreads();  // the previous unit's staging is written out
+        const Unit un = wk.units[u];
+        if (un.len > static_cast<uint32_t>(SM::TILE) || un.start + un.len > wk.n) {  // block-uniform
+            if (t == 0) set_error(wk.ctl, kErrBounds);
+            continue;
+        }
+        const K *__restrict__ src = src_of<K>(wk, un.src);
+        const V *__restrict__ vsrc = vals_of<V>(wk, un.src);
+        const bool make_pos = wk.kv_positions && un.raw;
+        const int len = static_cast<int>(un.len);
+        K k[ITEMS];
+        V v[ITEMS];
+        uint32_t vmask = 0;
+        K a = static_cast<K>(~K(0)), o = 0;
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            const int idx = (warp * ITEMS + j) * 32 + lane;
+            k[j] = 0;
+            v[j] = 0;
+            if (idx < len) {
+                K key = src[un.start + idx];
+                if (un.raw) key = encode_key(key, wk.codec);
+                k[j] = key;
+                v[j] = make_pos ? static_cast<V>(un.start + idx) : vsrc[un.start + idx];
+                vmask |= 1u << j;
+                a &= key;
+                o |= key;
+            }
+        }
+        block_and_or_k<K, THREADS>(a, o, ta, to);
+        const K diff = a ^ o;
+        if (diff == 0) {  // one repeated key: the values stay in input order
+            const K val = decode_key(a, wk.codec);
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) {
+                if ((vmask >> j) & 1u) {
+                    const uint64_t i = un.start + static_cast<uint64_t>((warp * ITEMS + j) * 32 + lane);
+                    out[i] = val;
+                    kv_out<K, V>(wk, i, v[j]);
+                }
+            }
+            continue;
+        }
+        const int lo = lsb_pos<K>(diff);
+        const int hi = msb_pos<K>(diff) + 1;
+        const int passes = (hi - lo + kRadixBits - 1) / kRadixBits;
+        const int width = (hi - lo + passes - 1) / passes;
+        for (int ps = 0; ps < passes; ++ps) {
+            const int sh = lo + ps * width;
+            const uint32_t m = (1u << min(width, hi - sh)) - 1u;
+            uint32_t place[ITEMS];
+            stable_places<K, THREADS, ITEMS, RS>(k, vmask, sh, m, place);
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) {
+                if ((vmask >> j) & 1u) {
+                    sm_keys[place[j]] = k[j];
+                    sm_vals[place[j]] = v[j];
+                }
+            }
+            __syncthreads();
+            if (ps + 1 < passes) {  // back to registers in tile order for the next pass
+#pragma unroll
+                for (int j = 0; j < ITEMS; ++j) {
+                    const int idx = (warp * ITEMS + j) * 32 + lane;
+                    if (idx < len) {
+                        k[j] = sm_keys[idx];
+                        v[j] = sm_vals[idx];
+                    }
+                }
+            }
+        }
+        for (int i = t; i < len; i += THREADS) {
+            out[un.start + i] = decode_key(sm_keys[i], wk.codec);
+            kv_out<K, V>(wk, un.start + i, sm_vals[i]);
+        }
+    }
+}
+
+// Constant runs of the key-value sort: the key written len times, the run's
+// values moved, in their order, to the output (src 1: from the alternate
+// values; 0: already in place unless they are argsort positions; 2: a run
+// never moved, its values the input's).
+template <typename K, typename V>
+__global__ void k_fill_kv(Work wk) {
+    pdl_enter();
+    if (wk.ctl->error) return;
+    const uint32_t nf = wk.ctl->n_fills;
+    K *out = static_cast<K *>(wk.keys);
+    for (uint32_t f = blockIdx.x; f < nf; f += gridDim.x) {
+        const Fill fl = wk.fills[f];
+        if (fl.start + fl.len > wk.n) {
+            set_error(wk.ctl, kErrBounds);
+            continue;
+        }
+        K val = static_cast<K>(fl.value);
+        if constexpr (sizeof(K) > 8) val |= static_cast<K>(fl.value_hi) << 64;
+        const K key = decode_key(val, wk.codec);
+        const V *vsrc = vals_of<V>(wk, fl.src == 1 ? 1 : 0);
+        for (uint32_t i = threadIdx.x; i < fl.len; i += blockDim.x) {
+            const uint64_t at = fl.start + i;
+            out[at] = key;
+            if (fl.src == 2) {
+                if (wk.kv_positions) kv_out<K, V>(wk, at, static_cast<V>(at));
+            } else if (fl.src == 1 || wk.kv_positions) {
+                kv_out<K, V>(wk, at, vsrc[at]);
+            }
+        }
+    }
+}
+
 template <typename K>
 struct Cfg;
 template <>
@@ -1931,11 +2275,44 @@ struct Cfg<u128> {
     static constexpr int kFinItems = 5;
 };
 
+// Key-value sorting: 256-thread CTAs; the scatter tile (one chunk) is 4096
+// pairs, the finish tile holds the largest unit.  4-byte keys with 4-byte
+// values keep the keys-only finish capacity (5120), so the same buckets end
+// after the same levels.
+template <typename K, typename V>
+struct KvCfg {
+    static constexpr int kPairBytes = static_cast<int>(sizeof(K) + sizeof(V));
+    static constexpr int kThreads = 256;
+    static constexpr int kItems = 16;
+    static constexpr int kScatterCtas = kPairBytes <= 8 ? 3 : 2;
+    static constexpr int kFinThreads = 256;
+    static constexpr int kFinItems = kPairBytes <= 8 ? 20 : (kPairBytes <= 12 ? 12 : 10);
+    static constexpr int kFinCtas = 3;
+};
+
 }  // namespace
 
-MsdShape msd_shape(int key_bytes, const Tuning &t, bool inplace) {
+MsdShape msd_shape(int key_bytes, const Tuning &t, bool inplace, int kv_bytes) {
     MsdShape s;
     uint32_t fin;
+    if (kv_bytes) {  // key-value sorting: fixed shape, 8-bit digits, one scatter tile per chunk
+        const bool k4 = key_bytes == 4, v4 = kv_bytes == 4;
+        s.tile = k4 ? (v4 ? KvCfg<uint32_t, uint32_t>::kThreads * KvCfg<uint32_t, uint32_t>::kItems
+                          : KvCfg<uint32_t, uint64_t>::kThreads * KvCfg<uint32_t, uint64_t>::kItems)
+                    : (v4 ? KvCfg<uint64_t, uint32_t>::kThreads * KvCfg<uint64_t, uint32_t>::kItems
+                          : KvCfg<uint64_t, uint64_t>::kThreads * KvCfg<uint64_t, uint64_t>::kItems);
+        fin = k4 ? (v4 ? KvCfg<uint32_t, uint32_t>::kFinThreads * KvCfg<uint32_t, uint32_t>::kFinItems
+                       : KvCfg<uint32_t, uint64_t>::kFinThreads * KvCfg<uint32_t, uint64_t>::kFinItems)
+                 : (v4 ? KvCfg<uint64_t, uint32_t>::kFinThreads * KvCfg<uint64_t, uint32_t>::kFinItems
+                       : KvCfg<uint64_t, uint64_t>::kFinThreads * KvCfg<uint64_t, uint64_t>::kFinItems);
+        s.radix_bits = kRadixBits;
+        s.bins = kBins;
+        s.levels = (key_bytes * 8 + kRadixBits - 1) / kRadixBits;
+        s.chunk = s.tile;
+        s.unit_cap = fin;  // the finish loads a unit with scalar loads: no alignment slack
+        s.merge_cap = (s.unit_cap * 4 / 5) & ~63u;
+        return s;
+    }
     if (key_bytes == 4) {
         s.tile = Cfg<uint32_t>::kThreads * Cfg<uint32_t>::kItems;
         fin = Cfg<uint32_t>::kFinThreads * Cfg<uint32_t>::kFinItems;
@@ -2077,6 +2454,59 @@ void launch_msd_segmented(const Work &wk, const uint64_t *d_offsets, uint32_t ns
     msd_levels_and_finish<K>(wk, st, rec, num_sms, true);
 }
 
+// Stable key-value sort: the keys-only histogram, column scan and classify
+// steps, the value-carrying scatter per level, then the stable finish and the
+// fills.
+template <typename K, typename V>
+void launch_msd_kv(const Work &wk, cudaStream_t st, Recorder &rec, int num_sms) {
+    using C = KvCfg<K, V>;
+    constexpr int T = C::kThreads, I = C::kItems, SB = C::kScatterCtas;
+    constexpr int FT = C::kFinThreads, FI = C::kFinItems, FB = C::kFinCtas;
+    constexpr size_t kScatterSmem = ScatterKvSmem<K, V, T, I>::kEnd;
+    constexpr size_t kFinishSmem = FinishKvSmem<K, V, FT, FI>::kEnd;
+    static const bool attrs = [] {  // once per process
+        cudaFuncSetAttribute(k_scatter_kv<K, V, T, I, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kScatterSmem));
+        cudaFuncSetAttribute(k_finish_kv<K, V, FT, FI, FB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kFinishSmem));
+        return true;
+    }();
+    (void)attrs;
+    const bool direct = wk.n <= wk.unit_cap;
+    const uint32_t nc0 = direct ? 0u : static_cast<uint32_t>((wk.n + wk.chunk_keys - 1) / wk.chunk_keys);
+    rec.begin(BSORT_K_INIT, -1);
+    k_init<<<direct ? 1 : max(1u, min(1024u, (nc0 + 255) / 256)), 256, 0, st>>>(wk, nc0, direct ? 1 : 0);
+    rec.end();
+    if (!direct) {
+        for (int level = 0; level < wk.levels; ++level) {
+            rec.begin(BSORT_K_HIST, level);
+            launch_pdl(k_hist<K, 512, kBins>, num_sms * 4, 512, 0, st, wk, level);
+            rec.end();
+            rec.begin(BSORT_K_SCAN, level);
+            launch_pdl(k_colscan<1024>, kBins, 1024, 0, st, wk, level);
+            rec.end();
+            rec.begin(BSORT_K_CLASSIFY, level);
+            launch_pdl(k_classify<kBins, K>, num_sms * 4, kBins, 0, st, wk, level);
+            rec.end();
+            rec.begin(BSORT_K_SCATTER, level);
+            launch_pdl(k_scatter_kv<K, V, T, I, SB>, num_sms * SB, T, kScatterSmem, st, wk, level);
+            rec.end();
+        }
+    }
+    rec.begin(BSORT_K_FINISH, -1);
+    launch_pdl(k_finish_kv<K, V, FT, FI, FB>, num_sms * FB, FT, kFinishSmem, st, wk);
+    rec.end();
+    if (!direct) {
+        rec.begin(BSORT_K_FILL, -1);
+        launch_pdl(k_fill_kv<K, V>, num_sms * 2, 256, 0, st, wk);
+        rec.end();
+    }
+}
+
+template void launch_msd_kv<uint32_t, uint32_t>(const Work &, cudaStream_t, Recorder &, int);
+template void launch_msd_kv<uint32_t, uint64_t>(const Work &, cudaStream_t, Recorder &, int);
+template void launch_msd_kv<uint64_t, uint32_t>(const Work &, cudaStream_t, Recorder &, int);
+template void launch_msd_kv<uint64_t, uint64_t>(const Work &, cudaStream_t, Recorder &, int);
 template void msd_prepare<uint32_t>();
 template void msd_prepare<uint64_t>();
 template void msd_prepare<u128>();

@@ -114,20 +114,75 @@ def test_pairs_tuned_handle(tuning8):
 
 
 def test_pairs_launch_counts():
-    """Key-value sorting launches its own pack / index / gather kernels plus
-    one (4-byte keys) or two (8-byte keys) sorts of the packed words."""
+    """4- and 8-byte keys: one value-carrying MSD pass sequence (init, four
+    kernels per 8-bit level, finish, fill), plus one gather when values follow
+    the positions.  1- and 2-byte keys: the packed-word sort with its own
+    pack / index / gather kernels."""
     import torch
     import paper_2603_08929_gb300 as bs
     n = 1 << 20
+    for dtype, kb in (("int32", 4), ("float64", 8)):
+        x = W.make("uniform", dtype, n, seed=9)
+        vals = np.arange(n, dtype=np.int32)
+        _, _, _, hp = run_pairs(x, vals, False, indices=False)
+        assert hp.launch_count() == 3 + 4 * kb, (dtype, hp.launch_count())
+        _, _, _, hp = run_pairs(x, vals, False, indices=True)
+        assert hp.launch_count() == 4 + 4 * kb, (dtype, hp.launch_count())
     h = bs.Handle()
-    w = torch.zeros(n, dtype=torch.int64, device="cuda")  # same launch sequence as the 8-byte packed words
+    w = torch.zeros(n, dtype=torch.int64, device="cuda")  # same launch sequence as the packed words
     ws = torch.empty(bs.workspace_bytes(n, "int64"), dtype=torch.uint8, device="cuda")
     bs.bsort_keys_ws(h, w, ws)
     c = h.launch_count()
-    for dtype, want in (("int32", c + 3), ("float64", 2 * c + 6)):
-        x = W.make("uniform", dtype, n, seed=9)
-        _, _, _, hp = run_pairs(x, np.arange(n, dtype=np.int32), False)
-        assert hp.launch_count() == want, (dtype, hp.launch_count(), want)
+    _, _, _, hp = run_pairs(W.make("uniform", "int16", n, seed=9), np.arange(n, dtype=np.int32), False)
+    assert hp.launch_count() == c + 3, (hp.launch_count(), c + 3)
+
+
+KV_KEYS = ["int32", "uint32", "float32", "int64", "uint64", "float64"]
+
+
+@pytest.mark.parametrize("vdtype", ["int32", "int64"])
+@pytest.mark.parametrize("dtype", KV_KEYS)
+def test_pairs_carried_values(dtype, vdtype):
+    """Values of 4 and 8 bytes travel with their keys through every level
+    (no positions asked for): equal to the oracle's stable permutation, for
+    tie-heavy, skewed, presorted and uniform keys, ascending and descending,
+    at a size spanning many scatter tiles with a ragged last one."""
+    n = 3 * 4096 * 17 + 1234
+    for j, dist in enumerate(_dists(dtype)):
+        x = W.make(dist, dtype, n, seed=60 + j)
+        vals = W.make("uniform", vdtype, n, seed=70 + j)
+        desc = j % 2 == 1
+        check(x, vals, desc, run_pairs(x, vals, desc, indices=False))
+
+
+@pytest.mark.parametrize("dtype", ["int32", "uint64"])
+@pytest.mark.parametrize("n", [2, 31, 2559, 2560, 2561, 3072, 3073, 5119, 5120, 5121, 65536 + 7])
+def test_pairs_unit_boundaries(dtype, n):
+    """Sizes around the finish capacity of each key/value width (one unit
+    sorted directly, or the MSD levels first), every request form."""
+    x = W.make("distinct8" if n % 2 else "uniform", dtype, n, seed=n)
+    for vd in ("int32", "int64", "uint8"):
+        vals = W.make("uniform", vd, n, seed=n + 1)
+        check(x, vals, n % 3 == 0, run_pairs(x, vals, n % 3 == 0, indices=False))
+        check(x, vals, n % 3 == 1, run_pairs(x, vals, n % 3 == 1, indices=True))
+    check(x, None, False, run_pairs(x, None, False, indices=True))
+
+
+@pytest.mark.parametrize("dtype", ["int32", "float64"])
+def test_pairs_degenerate_keys(dtype):
+    """All keys equal (the whole array one run: values keep input order, the
+    positions are the identity), two values only, and keys that agree on
+    their top bytes (the levels re-open in place, keys still raw)."""
+    n = 200003
+    np_t = np.dtype(dtype)
+    same = np.full(n, 3, dtype=np_t)
+    two = np.where(np.arange(n) % 3 == 0, 1, -2).astype(np_t)
+    low = (W.make("uniform", "uint32", n, seed=5) & 0x3ff).astype(np_t)
+    for x in (same, two, low):
+        vals = np.arange(n, dtype=np.int64) * 3
+        check(x, vals, False, run_pairs(x, vals, False, indices=False))
+        check(x, vals, True, run_pairs(x, vals, True, indices=True))
+        check(x, None, False, run_pairs(x, None, False, indices=True))
 
 
 def test_python_helpers():
@@ -154,12 +209,30 @@ def test_pairs_large_properties(dtype, log2n):
     n = 1 << log2n
     x = W.make("distinct8", dtype, n, seed=11)
     k, _, ix, _ = run_pairs(x, None, False)
+    check_stable_permutation(x, k, ix)
+
+
+def check_stable_permutation(x, k, ix, desc=False):
+    n = x.size
     assert ix.min() >= 0 and ix.max() < n
     seen = np.zeros(n, dtype=bool)
     seen[ix] = True
     assert seen.all(), "positions are not a permutation"
     assert_bit_exact(k, x[ix], "keys gathered by the positions")
-    assert par_first_unsorted(k, False) == -1
+    assert par_first_unsorted(k, desc) == -1
     kw = k.view({4: np.uint32, 8: np.uint64}[k.dtype.itemsize])
     same = kw[1:] == kw[:-1]
     assert np.all(ix[1:][same] > ix[:-1][same]), "ties out of input order"
+
+
+@pytest.mark.parametrize("dist", ["uniform", "distinct8"])
+def test_pairs_carried_at_size(dist):
+    """The key-value workload at full size: 2^28 int32 keys carrying int32
+    values (their input positions, so the carried values are the
+    permutation): a permutation, the keys it gathers are the output, sorted,
+    ties in input order."""
+    n = 1 << 28
+    x = W.make(dist, "int32", n, seed=12)
+    vals = np.arange(n, dtype=np.int32)
+    k, v, _, _ = run_pairs(x, vals, False, indices=False)
+    check_stable_permutation(x, k, v.astype(np.int64))
