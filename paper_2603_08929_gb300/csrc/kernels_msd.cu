@@ -1915,34 +1915,69 @@ __global__ void k_drain(Work wk, int level) {
 // warp-striped (item j of lane l of warp w is tile index (w * ITEMS + j) * 32
 // + l) and each key's place is its digit's start in the tile plus the keys of
 // that digit before it in tile order -- per-(digit, warp) counters and
-// per-warp peer masks, as the stable LSD passes use.  The histogram, column
-// scan and classify steps only look at keys and are shared with keys-only
-// sorting; a chunk is one tile, so a chunk's stable tile order is its order.
+// per-warp peer masks.  The histogram, column scan and classify steps only
+// look at keys and are shared with keys-only sorting; a chunk's tiles are
+// ranked in order, each digit's destination moving on by the tile's count.
 
-// Place of every item in the tile ordered by digit, ties in tile order.  The
-// peer masks must be zero on entry; they are zero again on return.
-template <typename K, int THREADS, int ITEMS, typename RS>
+// Shared memory of the stable ranking at byte offset BASE: two sets of
+// per-(digit, warp) counters, digit-major with one pad word per digit
+// (successive rankings alternate between the sets, so that one is cleared
+// while the other is in use), the per-warp peer masks (two sets, alternating
+// by item), and the scan scratch.
+template <int THREADS, size_t BASE>
+struct StableSmem {
+    static constexpr int WARPS = THREADS / 32;
+    static constexpr int STRIDE = WARPS + 1;
+    static constexpr int kWcWords = kBins * STRIDE;
+    static constexpr size_t kWc = BASE;
+    static constexpr size_t kWm = kWc + 16 * ((8 * kWcWords + 15) / 16);
+    static constexpr size_t kScan = kWm + 8 * WARPS * kBins;
+    static constexpr size_t kEnd = kScan + 16 * ((4 * (WARPS + 1) + 15) / 16);
+    __device__ static uint32_t *wc(int set) {
+        return reinterpret_cast<uint32_t *>(g_dyn_smem + kWc) + set * kWcWords;
+    }
+    __device__ static uint32_t *wm() { return reinterpret_cast<uint32_t *>(g_dyn_smem + kWm); }
+    __device__ static uint32_t *scan() { return reinterpret_cast<uint32_t *>(g_dyn_smem + kScan); }
+    // Both counter sets (and the peer masks) zeroed; the caller syncs before the first ranking.
+    __device__ static void clear() {
+        for (int i = threadIdx.x; i < 2 * kWcWords; i += blockDim.x) wc(0)[i] = 0;
+        for (int i = threadIdx.x; i < 2 * WARPS * kBins; i += blockDim.x) wm()[i] = 0;
+    }
+};
+
+// Place of every item in the tile ordered by digit, ties in tile order;
+// thread d <= mask also gets the tile's count of digit d.  Counter set `set`
+// must be zero on entry; the other set is zeroed here for the next ranking
+// (the caller passes the sets alternately and has a barrier between this
+// call's last read of the counters -- the place lookups at the end -- and
+// the next call).  Three barriers.
+template <typename K, int THREADS, int ITEMS, typename SS>
 __device__ __forceinline__ void stable_places(const K (&keys)[ITEMS], uint32_t vmask, int shift, uint32_t mask,
-                                              uint32_t (&place)[ITEMS]) {
+                                              uint32_t (&place)[ITEMS], int set, uint32_t &count) {
     constexpr int WARPS = THREADS / 32;
     constexpr int STRIDE = WARPS + 1;
     static_assert(THREADS >= kBins, "one thread per digit in the scans");
-    uint32_t *wc = RS::wc(), *wm0 = RS::wm(), *scan = RS::scan();
+    uint32_t *wc = SS::wc(set);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int t = threadIdx.x;
-    for (int i = t; i < (static_cast<int>(mask) + 1) * STRIDE; i += THREADS) wc[i] = 0;
-    __syncthreads();
+    {
+        uint32_t *wc_next = SS::wc(set ^ 1);
+        for (int i = t; i < SS::kWcWords; i += THREADS) wc_next[i] = 0;
+    }
     const unsigned lt = lanemask_lt();
-    const unsigned bit = 1u << lane;
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
         const bool valid = (vmask >> j) & 1u;
         place[j] = 0;
         if (__any_sync(kFull, valid)) {  // warp-uniform
-            uint32_t *wm = wm0 + ((j & 1) * WARPS + warp) * kBins;
             const uint32_t d = static_cast<uint32_t>(keys[j] >> shift) & mask;
             uint32_t *wcd = wc + d * STRIDE + warp;
-            if (valid) atomicOr(&wm[d], bit);
+            // lanes of one digit find each other through the warp's mask word
+            // of the digit (two mask sets alternate by item, so a set is
+            // cleared before its next use without another barrier); the
+            // lowest lane of the group advances the warp's counter
+            uint32_t *wm = SS::wm() + ((j & 1) * WARPS + warp) * kBins;
+            if (valid) atomicOr(&wm[d], 1u << lane);
             __syncwarp();
             const uint32_t peers = wm[d];
             const uint32_t before = *wcd;
@@ -1956,21 +1991,33 @@ __device__ __forceinline__ void stable_places(const K (&keys)[ITEMS], uint32_t v
         }
     }
     __syncthreads();
-    // digit totals, their prefix, then each warp's start inside its digit
+    // thread d: total of digit d; exclusive prefix over digits (warp scan,
+    // then the totals of the warps before); the warps' starts written back
     uint32_t run = 0;
     if (t <= static_cast<int>(mask)) {
 #pragma unroll
         for (int w = 0; w < WARPS; ++w) run += wc[t * STRIDE + w];
     }
-    uint32_t total;
-    const uint32_t ex = block_exclusive_scan<THREADS>(run, scan, total);
+    count = run;
+    uint32_t x = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    uint32_t *tmp = SS::scan();
+    if (lane == 31) tmp[warp] = x;
+    __syncthreads();
+    uint32_t acc = x - run;
+#pragma unroll
+    for (int w = 0; w < WARPS; ++w)
+        if (w < warp) acc += tmp[w];
     if (t <= static_cast<int>(mask)) {
-        uint32_t acc = ex;
 #pragma unroll
         for (int w = 0; w < WARPS; ++w) {
-            const uint32_t x = wc[t * STRIDE + w];
+            const uint32_t c = wc[t * STRIDE + w];
             wc[t * STRIDE + w] = acc;
-            acc += x;
+            acc += c;
         }
     }
     __syncthreads();
@@ -1978,7 +2025,6 @@ __device__ __forceinline__ void stable_places(const K (&keys)[ITEMS], uint32_t v
     for (int j = 0; j < ITEMS; ++j)
         if ((vmask >> j) & 1u)
             place[j] += wc[(static_cast<uint32_t>(keys[j] >> shift) & mask) * STRIDE + warp];
-    __syncthreads();
 }
 
 // A value of the key-value sort: 4 or 8 bytes.
@@ -2004,105 +2050,172 @@ __device__ __forceinline__ V *vals_dst_of(const Work &wk, int src) {
 }
 
 
-// Stable scatter of one level, keys and values: each chunk (one tile) is
+// Stable scatter of one level, keys and values: each tile of a chunk is
 // loaded warp-striped, ranked stably by digit, staged (keys and values) in
 // digit order, and written out in staging order to its digit runs.  The
-// destinations come from the histogram pass exactly as in k_scatter; every
-// one is checked against the bucket before it is written.
+// chunk's destinations come from the histogram pass exactly as in k_scatter
+// and move on by each tile's digit counts; every one is checked against the
+// bucket before it is written.  The loop is software-pipelined: the next
+// tile's keys and values are loaded into the (then free) registers while the
+// staged tile is written out, and the next chunk's record while this tile is
+// ranked.
 template <typename K, typename V, int THREADS, int ITEMS>
 struct ScatterKvSmem {
     static constexpr int TILE = THREADS * ITEMS;
     static constexpr size_t kVals = sizeof(K) * TILE;
     static constexpr size_t kRank = ((kVals + sizeof(V) * TILE) + 15) & ~size_t(15);
-    using RS = RankSmem<THREADS, kRank, true>;
+    using RS = StableSmem<THREADS, kRank>;
     static constexpr size_t kOff = (RS::kEnd + 15) & ~size_t(15);  // u64[kBins]
     static constexpr size_t kEnd = kOff + 8 * kBins;
 };
+
+// Keys and values of tile positions [0, len) of a buffer range into
+// registers, warp-striped with IT items per thread (item j of lane l of warp
+// w is position (w * IT + j) * 32 + l); raw argsort ranges make their
+// positions.  Returns the validity mask.
+template <typename K, typename V, int ITEMS>
+__device__ __forceinline__ uint32_t kv_load(const Work &wk, int src, bool raw, uint64_t start, uint32_t len, int it,
+                                            K (&k)[ITEMS], V (&v)[ITEMS]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const K *__restrict__ ks = src_of<K>(wk, src);
+    const V *__restrict__ vs = vals_of<V>(wk, src);
+    const bool make_pos = wk.kv_positions && raw;
+    uint32_t vmask = 0;
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        const uint32_t idx = static_cast<uint32_t>((warp * it + j) * 32 + lane);
+        k[j] = 0;
+        v[j] = 0;
+        if (j < it && idx < len) {
+            k[j] = ks[start + idx];
+            v[j] = make_pos ? static_cast<V>(start + idx) : vs[start + idx];
+            vmask |= 1u << j;
+        }
+    }
+    return vmask;
+}
 
 template <typename K, typename V, int THREADS, int ITEMS, int MINB>
 __global__ void __launch_bounds__(THREADS, MINB) k_scatter_kv(Work wk, int level) {
     pdl_enter();
     using SM = ScatterKvSmem<K, V, THREADS, ITEMS>;
     using RS = typename SM::RS;
+    constexpr uint32_t TILE = THREADS * ITEMS;
     constexpr int WARPS = THREADS / 32;
     constexpr int STRIDE = WARPS + 1;
     K *sm_keys = reinterpret_cast<K *>(g_dyn_smem);
     V *sm_vals = reinterpret_cast<V *>(g_dyn_smem + SM::kVals);
     unsigned long long *off = reinterpret_cast<unsigned long long *>(g_dyn_smem + SM::kOff);
     const int p = level & 1;
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int t = threadIdx.x;
     if (wk.ctl->error) return;
     write_child_chunks(wk, p ^ 1);  // records of the buckets this level's classify opened
-    for (int i = t; i < 2 * WARPS * kBins; i += THREADS) RS::wm()[i] = 0;  // peer masks start clear
+    RS::clear();
+    __syncthreads();
+    int set = 0;  // counter set of the next ranking
     const uint32_t nch = wk.ctl->n_chunks[p];
-    for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) {
-        __syncthreads();  // the previous chunk's staging is written out
-        const Chunk ch = wk.chunks[p][c];
-        const Bucket b = wk.buckets[p][ch.bucket];
-        if (!b.scatter) continue;  // block-uniform
+    // pipeline position: tile ti of chunk c (record ch, its bucket b), whose
+    // keys and values are in k / v
+    K k[ITEMS];
+    V v[ITEMS];
+    uint32_t vmask = 0;
+    uint32_t c = blockIdx.x, ti = 0;
+    Chunk ch = {};
+    Bucket b = {};
+    auto tile_len = [&](const Chunk &x, uint32_t i) -> uint32_t {
+        const uint32_t s0 = i * TILE;
+        return s0 < x.len ? min(x.len - s0, TILE) : 0u;
+    };
+    auto load_tile = [&]() {
+        vmask = b.scatter ? kv_load<K, V, ITEMS>(wk, b.src, b.raw, ch.start + static_cast<uint64_t>(ti) * TILE,
+                                                 tile_len(ch, ti), ITEMS, k, v)
+                          : 0u;
+    };
+    if (c < nch) {
+        ch = wk.chunks[p][c];
+        b = wk.buckets[p][ch.bucket];
+        load_tile();
+    }
+    uint64_t dest = 0;  // thread d <= mask: where digit d's next key of this chunk goes
+    while (c < nch) {
+        const uint32_t ntiles = b.scatter ? max(1u, (ch.len + TILE - 1) / TILE) : 1u;
+        const bool last_tile = ti + 1 >= ntiles;
+        const uint32_t cn = c + gridDim.x;
+        Chunk chn = {};
+        if (last_tile && cn < nch) chn = wk.chunks[p][cn];  // arrives while this tile is ranked
         const int r_eff = min(wk.radix_bits, b.h);
         const int shift = b.h - r_eff;
         const uint32_t mask = (1u << r_eff) - 1;
-        const K *__restrict__ src = src_of<K>(wk, b.src);
-        const V *__restrict__ vsrc = vals_of<V>(wk, b.src);
-        const bool make_pos = wk.kv_positions && b.raw;
-        K k[ITEMS];
-        V v[ITEMS];
-        uint32_t vmask = 0;
+        const uint32_t tl = tile_len(ch, ti);
+        if (b.scatter) {  // block-uniform
+            // a chunk's digit d starts at bucket start + digit base + keys of
+            // digit d in the bucket's earlier chunks; each tile moves it on
+            if (ti == 0 && t <= static_cast<int>(mask))
+                dest = b.start + wk.bucket_base[static_cast<size_t>(ch.bucket) * wk.bins + t] +
+                       wk.hist[static_cast<size_t>(t) * wk.max_chunks + c];
+            if (b.raw) {
 #pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            const uint32_t idx = static_cast<uint32_t>((warp * ITEMS + j) * 32 + lane);
-            k[j] = 0;
-            v[j] = 0;
-            if (idx < ch.len) {
-                k[j] = src[ch.start + idx];
-                v[j] = make_pos ? static_cast<V>(ch.start + idx) : vsrc[ch.start + idx];
-                vmask |= 1u << j;
+                for (int j = 0; j < ITEMS; ++j) k[j] = encode_key(k[j], wk.codec);
+            }
+            uint32_t place[ITEMS], cnt;
+            stable_places<K, THREADS, ITEMS, RS>(k, vmask, shift, mask, place, set, cnt);
+            // digit d's run: staging slots from its tile start, so the key at
+            // staging slot q goes to off[d] + q
+            if (t <= static_cast<int>(mask)) {
+                off[t] = dest - RS::wc(set)[t * STRIDE];
+                dest += cnt;
+            }
+            set ^= 1;
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) {
+                if ((vmask >> j) & 1u) {
+                    sm_keys[place[j]] = k[j];
+                    sm_vals[place[j]] = v[j];
+                }
+            }
+            __syncthreads();
+        }
+        const Bucket cb = b;
+        // the next tile into the registers; its loads overlap the write-out below
+        if (!last_tile) {
+            ++ti;
+            load_tile();
+        } else {
+            c = cn;
+            ti = 0;
+            if (c < nch) {
+                ch = chn;
+                b = wk.buckets[p][ch.bucket];
+                load_tile();
             }
         }
-        if (b.raw) {
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j) k[j] = encode_key(k[j], wk.codec);
-        }
-        uint32_t place[ITEMS];
-        stable_places<K, THREADS, ITEMS, RS>(k, vmask, shift, mask, place);
-        // digit d's run: staging slots from its tile start, destinations from
-        // the histogram's prefix (off[d] = destination - tile start)
-        if (t <= static_cast<int>(mask))
-            off[t] = b.start + wk.bucket_base[static_cast<size_t>(ch.bucket) * wk.bins + t] +
-                     wk.hist[static_cast<size_t>(t) * wk.max_chunks + c] - RS::wc()[t * STRIDE];
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            if ((vmask >> j) & 1u) {
-                sm_keys[place[j]] = k[j];
-                sm_vals[place[j]] = v[j];
+        if (cb.scatter) {
+            K *__restrict__ dst = dst_of<K>(wk, cb.src);
+            V *__restrict__ vdst = vals_dst_of<V>(wk, cb.src);
+            bool oob = false;
+            for (uint32_t q = t; q < tl; q += THREADS) {
+                const K key = sm_keys[q];
+                const uint64_t pos = off[static_cast<uint32_t>(key >> shift) & mask] + q;
+                if (pos - cb.start < cb.len) {
+                    dst[pos] = key;
+                    vdst[pos] = sm_vals[q];
+                } else {
+                    oob = true;
+                }
             }
+            if (oob) set_error(wk.ctl, kErrBounds);
         }
-        __syncthreads();
-        K *__restrict__ dst = dst_of<K>(wk, b.src);
-        V *__restrict__ vdst = vals_dst_of<V>(wk, b.src);
-        bool oob = false;
-        for (uint32_t q = t; q < ch.len; q += THREADS) {
-            const K key = sm_keys[q];
-            const uint64_t pos = off[static_cast<uint32_t>(key >> shift) & mask] + q;
-            if (pos - b.start < b.len) {
-                dst[pos] = key;
-                vdst[pos] = sm_vals[q];
-            } else {
-                oob = true;
-            }
-        }
-        if (oob) set_error(wk.ctl, kErrBounds);
+        // (the next tile stages only after the barriers inside its ranking)
     }
 }
 
-
-
 // Stable finish of a unit, keys and values: loaded warp-striped (input
-// order), then one stable pass per digit of at most 8 bits over the unit's
+// order, IT = ceil(len / THREADS) items per thread so that every warp has
+// work), then one stable pass per digit of at most 8 bits over the unit's
 // varying bits, least significant first, each staging keys and values in
 // shared memory; the last pass's staging is the sorted unit, written decoded
 // to its final place (values beside, or int64 positions for an argsort).
+// The next unit is loaded into the registers while the staged one is written.
 template <typename K, typename V, int THREADS, int ITEMS>
 struct FinishKvSmem {
     static constexpr int TILE = THREADS * ITEMS;
@@ -2111,11 +2224,11 @@ struct FinishKvSmem {
     static constexpr size_t kTa = (kVals + sizeof(V) * TILE + 15) & ~size_t(15);
     static constexpr size_t kTo = kTa + sizeof(K) * WARPS;
     static constexpr size_t kRank = (kTo + sizeof(K) * WARPS + 15) & ~size_t(15);
-    using RS = RankSmem<THREADS, kRank, true>;
+    using RS = StableSmem<THREADS, kRank>;
     static constexpr size_t kEnd = RS::kEnd;
 };
 
-template <typename K, typename V>
+template <typename V>
 __device__ __forceinline__ void kv_out(const Work &wk, uint64_t i, V v) {
     if (wk.kv_positions) {
         if (wk.out_idx) wk.out_idx[i] = static_cast<int64_t>(v);
@@ -2130,57 +2243,66 @@ __global__ void __launch_bounds__(THREADS, MINB) k_finish_kv(Work wk) {
     pdl_enter();
     using SM = FinishKvSmem<K, V, THREADS, ITEMS>;
     using RS = typename SM::RS;
-    constexpr int WARPS = THREADS / 32;
     K *sm_keys = reinterpret_cast<K *>(g_dyn_smem);
     V *sm_vals = reinterpret_cast<V *>(g_dyn_smem + SM::kVals);
     K *ta = reinterpret_cast<K *>(g_dyn_smem + SM::kTa);
     K *to = reinterpret_cast<K *>(g_dyn_smem + SM::kTo);
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     if (wk.ctl->error) return;
-    for (int i = t; i < 2 * WARPS * kBins; i += THREADS) RS::wm()[i] = 0;  // peer masks start clear
+    RS::clear();  // (the AND/OR reduction's barriers come before the first ranking)
+    int set = 0;  // counter set of the next ranking
     const uint32_t nu = min(wk.ctl->n_units, wk.max_units);
     K *__restrict__ out = static_cast<K *>(wk.keys);
-    for (uint32_t u = blockIdx.x; u < nu; u += gridDim.x) {
-        __syncthreads();  // the previous unit's staging is written out
-        const Unit un = wk.units[u];
-        if (un.len > static_cast<uint32_t>(SM::TILE) || un.start + un.len > wk.n) {  // block-uniform
+    // a unit that fits the tile and the buffer, else an empty one (and the bounds error)
+    auto fetch = [&](uint32_t u) {
+        Unit un = wk.units[u];
+        if (un.len > static_cast<uint32_t>(SM::TILE) || un.start + un.len > wk.n) {
             if (t == 0) set_error(wk.ctl, kErrBounds);
-            continue;
+            un.len = 0;
         }
-        const K *__restrict__ src = src_of<K>(wk, un.src);
-        const V *__restrict__ vsrc = vals_of<V>(wk, un.src);
-        const bool make_pos = wk.kv_positions && un.raw;
-        const int len = static_cast<int>(un.len);
-        K k[ITEMS];
-        V v[ITEMS];
-        uint32_t vmask = 0;
+        return un;
+    };
+    K k[ITEMS];
+    V v[ITEMS];
+    uint32_t vmask = 0;
+    int it = 0;
+    uint32_t u = blockIdx.x;
+    Unit un = {};
+    if (u < nu) {
+        un = fetch(u);
+        it = static_cast<int>((un.len + THREADS - 1) / THREADS);
+        vmask = kv_load<K, V, ITEMS>(wk, un.src, un.raw, un.start, un.len, it, k, v);
+    }
+    for (; u < nu; u += gridDim.x) {
+        const uint32_t un_next = u + gridDim.x;
+        const Unit cur = un;
+        const int cit = it;
+        const int len = static_cast<int>(cur.len);
         K a = static_cast<K>(~K(0)), o = 0;
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) {
-            const int idx = (warp * ITEMS + j) * 32 + lane;
-            k[j] = 0;
-            v[j] = 0;
-            if (idx < len) {
-                K key = src[un.start + idx];
-                if (un.raw) key = encode_key(key, wk.codec);
-                k[j] = key;
-                v[j] = make_pos ? static_cast<V>(un.start + idx) : vsrc[un.start + idx];
-                vmask |= 1u << j;
-                a &= key;
-                o |= key;
+            if ((vmask >> j) & 1u) {
+                if (cur.raw) k[j] = encode_key(k[j], wk.codec);
+                a &= k[j];
+                o |= k[j];
             }
         }
         block_and_or_k<K, THREADS>(a, o, ta, to);
         const K diff = a ^ o;
-        if (diff == 0) {  // one repeated key: the values stay in input order
+        if (diff == 0) {  // one repeated key (or an empty unit): the values stay in input order
             const K val = decode_key(a, wk.codec);
 #pragma unroll
             for (int j = 0; j < ITEMS; ++j) {
                 if ((vmask >> j) & 1u) {
-                    const uint64_t i = un.start + static_cast<uint64_t>((warp * ITEMS + j) * 32 + lane);
+                    const uint64_t i = cur.start + static_cast<uint64_t>((warp * cit + j) * 32 + lane);
                     out[i] = val;
-                    kv_out<K, V>(wk, i, v[j]);
+                    kv_out<V>(wk, i, v[j]);
                 }
+            }
+            if (un_next < nu) {
+                un = fetch(un_next);
+                it = static_cast<int>((un.len + THREADS - 1) / THREADS);
+                vmask = kv_load<K, V, ITEMS>(wk, un.src, un.raw, un.start, un.len, it, k, v);
             }
             continue;
         }
@@ -2192,7 +2314,9 @@ __global__ void __launch_bounds__(THREADS, MINB) k_finish_kv(Work wk) {
             const int sh = lo + ps * width;
             const uint32_t m = (1u << min(width, hi - sh)) - 1u;
             uint32_t place[ITEMS];
-            stable_places<K, THREADS, ITEMS, RS>(k, vmask, sh, m, place);
+            uint32_t cnt;
+            stable_places<K, THREADS, ITEMS, RS>(k, vmask, sh, m, place, set, cnt);
+            set ^= 1;
 #pragma unroll
             for (int j = 0; j < ITEMS; ++j) {
                 if ((vmask >> j) & 1u) {
@@ -2204,48 +2328,64 @@ __global__ void __launch_bounds__(THREADS, MINB) k_finish_kv(Work wk) {
             if (ps + 1 < passes) {  // back to registers in tile order for the next pass
 #pragma unroll
                 for (int j = 0; j < ITEMS; ++j) {
-                    const int idx = (warp * ITEMS + j) * 32 + lane;
-                    if (idx < len) {
+                    const int idx = (warp * cit + j) * 32 + lane;
+                    if ((vmask >> j) & 1u) {
                         k[j] = sm_keys[idx];
                         v[j] = sm_vals[idx];
                     }
                 }
             }
         }
-        for (int i = t; i < len; i += THREADS) {
-            out[un.start + i] = decode_key(sm_keys[i], wk.codec);
-            kv_out<K, V>(wk, un.start + i, sm_vals[i]);
+        if (un_next < nu) {  // next unit into the registers; its loads overlap the write-out
+            un = fetch(un_next);
+            it = static_cast<int>((un.len + THREADS - 1) / THREADS);
+            vmask = kv_load<K, V, ITEMS>(wk, un.src, un.raw, un.start, un.len, it, k, v);
         }
+        for (int i = t; i < len; i += THREADS) {
+            out[cur.start + i] = decode_key(sm_keys[i], wk.codec);
+            kv_out<V>(wk, cur.start + i, sm_vals[i]);
+        }
+        // (the next unit stages only after the barriers of its AND/OR and ranking)
     }
 }
 
 // Constant runs of the key-value sort: the key written len times, the run's
 // values moved, in their order, to the output (src 1: from the alternate
 // values; 0: already in place unless they are argsort positions; 2: a run
-// never moved, its values the input's).
+// never moved, its values the input's).  Four elements per thread in flight.
 template <typename K, typename V>
-__global__ void k_fill_kv(Work wk) {
+__global__ void __launch_bounds__(256) k_fill_kv(Work wk) {
     pdl_enter();
+    constexpr int U = 4;
     if (wk.ctl->error) return;
     const uint32_t nf = wk.ctl->n_fills;
     K *out = static_cast<K *>(wk.keys);
     for (uint32_t f = blockIdx.x; f < nf; f += gridDim.x) {
         const Fill fl = wk.fills[f];
         if (fl.start + fl.len > wk.n) {
-            set_error(wk.ctl, kErrBounds);
+            if (threadIdx.x == 0) set_error(wk.ctl, kErrBounds);
             continue;
         }
         K val = static_cast<K>(fl.value);
         if constexpr (sizeof(K) > 8) val |= static_cast<K>(fl.value_hi) << 64;
         const K key = decode_key(val, wk.codec);
-        const V *vsrc = vals_of<V>(wk, fl.src == 1 ? 1 : 0);
-        for (uint32_t i = threadIdx.x; i < fl.len; i += blockDim.x) {
-            const uint64_t at = fl.start + i;
-            out[at] = key;
-            if (fl.src == 2) {
-                if (wk.kv_positions) kv_out<K, V>(wk, at, static_cast<V>(at));
-            } else if (fl.src == 1 || wk.kv_positions) {
-                kv_out<K, V>(wk, at, vsrc[at]);
+        const bool move = fl.src == 1 || (fl.src == 0 && wk.kv_positions);
+        const bool make = fl.src == 2 && wk.kv_positions;
+        const V *__restrict__ vsrc = vals_of<V>(wk, fl.src == 1 ? 1 : 0);
+        for (uint32_t i0 = threadIdx.x; i0 < fl.len; i0 += U * blockDim.x) {
+            V x[U];
+#pragma unroll
+            for (int e = 0; e < U; ++e) {
+                const uint32_t i = i0 + e * blockDim.x;
+                x[e] = (move && i < fl.len) ? vsrc[fl.start + i] : static_cast<V>(fl.start + i);
+            }
+#pragma unroll
+            for (int e = 0; e < U; ++e) {
+                const uint32_t i = i0 + e * blockDim.x;
+                if (i < fl.len) {
+                    out[fl.start + i] = key;
+                    if (move || make) kv_out<V>(wk, fl.start + i, x[e]);
+                }
             }
         }
     }
@@ -2275,8 +2415,11 @@ struct Cfg<u128> {
     static constexpr int kFinItems = 5;
 };
 
-// Key-value sorting: 256-thread CTAs; the scatter tile (one chunk) is 4096
-// pairs, the finish tile holds the largest unit.  4-byte keys with 4-byte
+// Scatter tiles per chunk of the key-value sort.
+constexpr uint32_t kKvChunkTiles = 4;
+
+// Key-value sorting: 256-thread CTAs; the scatter tile is 4096 pairs (a
+// chunk is kKvChunkTiles of them), the finish tile holds the largest unit.  4-byte keys with 4-byte
 // values keep the keys-only finish capacity (5120), so the same buckets end
 // after the same levels.
 template <typename K, typename V>
@@ -2284,7 +2427,7 @@ struct KvCfg {
     static constexpr int kPairBytes = static_cast<int>(sizeof(K) + sizeof(V));
     static constexpr int kThreads = 256;
     static constexpr int kItems = 16;
-    static constexpr int kScatterCtas = kPairBytes <= 8 ? 3 : 2;
+    static constexpr int kScatterCtas = 2;
     static constexpr int kFinThreads = 256;
     static constexpr int kFinItems = kPairBytes <= 8 ? 20 : (kPairBytes <= 12 ? 12 : 10);
     static constexpr int kFinCtas = 3;
@@ -2308,7 +2451,7 @@ MsdShape msd_shape(int key_bytes, const Tuning &t, bool inplace, int kv_bytes) {
         s.radix_bits = kRadixBits;
         s.bins = kBins;
         s.levels = (key_bytes * 8 + kRadixBits - 1) / kRadixBits;
-        s.chunk = s.tile;
+        s.chunk = s.tile * kKvChunkTiles;
         s.unit_cap = fin;  // the finish loads a unit with scalar loads: no alignment slack
         s.merge_cap = (s.unit_cap * 4 / 5) & ~63u;
         return s;
@@ -2498,7 +2641,7 @@ void launch_msd_kv(const Work &wk, cudaStream_t st, Recorder &rec, int num_sms) 
     rec.end();
     if (!direct) {
         rec.begin(BSORT_K_FILL, -1);
-        launch_pdl(k_fill_kv<K, V>, num_sms * 2, 256, 0, st, wk);
+        launch_pdl(k_fill_kv<K, V>, num_sms * 4, 256, 0, st, wk);
         rec.end();
     }
 }
