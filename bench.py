@@ -102,7 +102,8 @@ def whole_job(ms_per_step_local, keys_per_rank, world, device):
 
 
 def measured_traffic(kind, dtype, keys_per_launch):
-    """DRAM bytes per launch of kernel `kind` from the committed ncu record, or
+    """DRAM bytes per launch of kernel `kind` from the committed ncu record
+    (`dtype`: the key dtype, or key_value dtypes for a key-value sort), or
     None when there is no record for it or the kernel sources changed since."""
     import glob
     import hashlib
@@ -499,8 +500,10 @@ def run_serve(args, rank, world):
 def run_pairs_mode(args, rank, world):
     """Stable key-value sort of 2^log2n keys of --dtype (--dist) with
     --value-dtype values (or, with 'none', the int64 positions: an argsort).
-    Each step restores keys and values from pristine copies (untimed) and
-    times one bsort_pairs_ws call with CUDA events."""
+    Every step sorts its own copy of keys and values (made before timing).
+    The value: K bsort_pairs_ws calls between two CUDA events; then the same K
+    calls on restored copies with the library's events around every launch
+    group, for the per-kernel times and the roofline."""
     import torch
     import paper_2603_08929_gb300 as bs
     from paper_2603_08929_gb300 import build as B
@@ -511,8 +514,9 @@ def run_pairs_mode(args, rank, world):
     x = torch.from_numpy(W.make(args.dist, args.dtype, n, seed=args.seed + rank)).to(dev)
     argsort = args.value_dtype == "none"
     v0 = None if argsort else torch.from_numpy(W.make("uniform", args.value_dtype, n, seed=args.seed + 1)).to(dev)
-    keys = torch.empty_like(x)
-    vals = None if argsort else torch.empty_like(v0)
+    total_steps = args.warmup + args.steps
+    keys = [x.clone() for _ in range(total_steps)]
+    vals = [None if argsort else v0.clone() for _ in range(total_steps)]
     idx = torch.empty(n, dtype=torch.int64, device=dev) if argsort else None
     tuning8 = {"radix_bits": args.radix_bits, "unit_keys": args.unit_keys, "chunk_tiles": args.chunk_tiles}
     tuning8 = tuning8 if any(tuning8.values()) else None
@@ -521,44 +525,91 @@ def run_pairs_mode(args, rank, world):
     if tuning8:
         h.set_tuning(8, tuning8)
     stream = torch.cuda.current_stream()
-    times = []
+    for i in range(args.warmup):
+        bs.bsort_pairs_ws(h, keys[i], ws, values=vals[i], indices=idx, descending=args.desc, stream=stream)
+    torch.cuda.synchronize()
+    if h.get_error(stream) != 0:
+        raise RuntimeError("device error word set during warm-up")
     clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
-    for i in range(args.warmup + args.steps):
-        if i == args.warmup and clocks:
-            clocks.start()
-        keys.copy_(x)
-        if vals is not None:
-            vals.copy_(v0)
+    if clocks:
+        clocks.start()
+
+    def timed_region():
+        if world > 1:
+            torch.distributed.barrier()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        bs.bsort_pairs_ws(h, keys, ws, values=vals, indices=idx, descending=args.desc, stream=stream)
+        for i in range(args.warmup, total_steps):
+            bs.bsort_pairs_ws(h, keys[i], ws, values=vals[i], indices=idx, descending=args.desc, stream=stream)
         e1.record(stream)
         torch.cuda.synchronize()
-        if i >= args.warmup:
-            times.append(e0.elapsed_time(e1))
+        return e0.elapsed_time(e1)
+
+    elapsed_ms = timed_region()
+    out_k = keys[-1].clone()
+    for i in range(args.warmup, total_steps):
+        keys[i].copy_(x)
+        if not argsort:
+            vals[i].copy_(v0)
+    h.set_profiling(True)
+    elapsed_prof_ms = timed_region()
+    prof = h.profile()
+    h.set_profiling(False)
+    launches = prof["launches"]  # kernels of the K timed calls
+    if world > 1:
+        torch.distributed.barrier()
     clock_info = clocks.stop() if clocks else None
     if h.get_error(stream) != 0:
         raise RuntimeError("device error word set in the key-value sort")
-    ms = sum(times) / len(times)
+    per_kind = {}
+    for r in prof["records"]:
+        k = per_kind.setdefault(r["kind"], {"ms": 0.0, "bytes": 0, "launches": 0})
+        k["ms"] += r["ms"]
+        k["bytes"] += r["counted_bytes"]
+        k["launches"] += 1
+    ms_per_step, value = whole_job(elapsed_ms / args.steps, n, world, dev)
     signed_ok = args.dtype in ("int8", "int16", "int32", "int64", "uint8")  # torch compares these on the device
-    ok = (bool(torch.all(keys[1:] <= keys[:-1]).item()) if args.desc else
-          bool(torch.all(keys[1:] >= keys[:-1]).item())) if signed_ok else None
+    ok = (bool(torch.all(out_k[1:] <= out_k[:-1]).item()) if args.desc else
+          bool(torch.all(out_k[1:] >= out_k[:-1]).item())) if signed_ok else None
     esize = x.element_size()
     vsize = 8 if argsort else v0.element_size()
     peak, peak_src = load_peaks()
     floor_bytes = n * (2 * esize + (vsize if argsort else 2 * vsize))  # read keys (+values), write keys + values/positions
+    dom_kind = max(per_kind.items(), key=lambda kv: kv[1]["ms"])[0]
+    dk = per_kind[dom_kind]
+    achieved = dk["bytes"] / (dk["ms"] * 1e-3) / 1e9 if dk["ms"] > 0 else 0.0
+    sort_ms = sum(k["ms"] for k in per_kind.values()) / args.steps
+    total_bytes = sum(k["bytes"] for k in per_kind.values()) / args.steps
+    sort_gbs = total_bytes / (ms_per_step * 1e-3) / 1e9
+    tag = "%s_%s" % (args.dtype, args.value_dtype)
+    carried = 4 if argsort else vsize  # bytes travelling with each key through the levels
     line = {
-        "metric": METRIC, "value": n / (ms * 1e-3) / 1e9, "unit": "Gpairs/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": value, "unit": "Gpairs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": DTYPE_TAG.get(args.dtype, args.dtype), "data": "synthetic",
         "config": {"workload": "stable key-value sort, %s %s keys, 2^%d, %s, %s" % (
             args.dtype, args.dist, args.log2n, "argsort (int64 positions)" if argsort else
             "%s values" % args.value_dtype, "descending" if args.desc else "ascending"),
-            "n": n, "l2": "inputs > L2 at this size; restored from pristine copies before each step (untimed)",
+            "n": n, "l2": "inputs > L2 at this size; each step sorts its own copy",
+            "timing": "value: K calls between two CUDA events, nothing between their launches; kernel times "
+                      "and the roofline: the same K calls on restored copies with the library's events around "
+                      "every launch group (ms_per_step_instrumented)",
             "tuning_of_the_word_sort": tuning8 or "library defaults"},
-        "gpu_launches": h.launch_count(),
-        "min_bytes_frac": floor_bytes / (ms * 1e-3) / 1e9 / peak,
+        "gpu_launches": launches,
+        "ms_per_step_instrumented": elapsed_prof_ms / args.steps,
+        "roofline": {"bound": "hbm", "kernel": dom_kind, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": peak_src,
+                     "traffic": measured_traffic(
+                         dom_kind, tag, dk["bytes"] / (2 * (esize + carried)) / max(dk["launches"], 1))
+                     if dom_kind in ("finish", "scatter") and not tuning8 else None},
+        "sort_roofline": {"counted_bytes_per_step": total_bytes, "achieved": sort_gbs, "frac": sort_gbs / peak,
+                          "peak": peak},
+        "kernels": {k: {"ms_per_step": v["ms"] / args.steps, "share": v["ms"] / (sort_ms * args.steps),
+                        "gbs": v["bytes"] / (v["ms"] * 1e-3) / 1e9 if v["ms"] > 0 else 0.0,
+                        "launches_per_step": v["launches"] / args.steps}
+                    for k, v in sorted(per_kind.items())},
+        "min_bytes_frac": floor_bytes / (ms_per_step * 1e-3) / 1e9 / peak,
         "min_bytes_note": "bytes any key-value sort must move (read keys%s, write keys and %s) / time / %s HBM "
                           "copy bandwidth" % ("" if argsort else " and values", "positions" if argsort else "values",
                                               peak_src),

@@ -245,14 +245,20 @@ bsort_status bsort_keys_host(void *host_keys, size_t n, bsort_dtype dt, int desc
  * (BSORT_ERR_MISALIGNED); workspace: bsort_pairs_workspace_bytes, 256-byte
  * aligned, owned by the caller.  Asynchronous on `stream`; device-side
  * failures land in the handle's error word (bsort_get_error).
- * Method: each key's order-preserving code (high 32 bits) and its input
- * position (low 32 bits) form one 64-bit word; the words are distinct, so the
- * 8-byte MSD sort of the words is the stable order.  8-byte keys take two
- * such sorts, on the low and then the high half of their code (LSD over the
- * halves).  Values (and 8-byte keys) follow by one gather.  The handle's
- * tuning for 8-byte keys applies to these sorts; a tuned handle needs the
- * workspace of bsort_pairs_workspace_bytes_tuned with that tuning (NULL:
- * defaults).
+ * Method, 4- and 8-byte keys: the MSD levels of bsort_keys with a stable
+ * scatter (ties keep their order inside every tile, tiles and chunks in
+ * buffer order) and a stable LSD finish, the values travelling with their
+ * keys through every level.  Values of 4 or 8 bytes travel themselves when
+ * no indices are asked for; otherwise 32-bit input positions travel (made
+ * when a key is first read), the int64 indices are written beside the sorted
+ * keys and values of any width follow by one gather along the positions.
+ * With neither values nor indices the keys-only sort runs.  1- and 2-byte
+ * keys: each key's order-preserving code (high 32 bits) and its input
+ * position (low 32 bits) form one 64-bit word; the words are distinct, so
+ * the 8-byte MSD sort of the words is the stable order; values follow by one
+ * gather.  The handle's tuning for 8-byte keys applies to that word sort
+ * only (bsort_pairs_workspace_bytes_tuned gives its workspace; NULL:
+ * defaults); the value-carrying levels have a fixed shape.
  */
 bsort_status bsort_pairs_workspace_bytes(size_t n, bsort_dtype dt, size_t *bytes);
 bsort_status bsort_pairs_workspace_bytes_tuned(size_t n, bsort_dtype dt, const bsort_tuning *tuning8, size_t *bytes);
@@ -447,7 +453,10 @@ typedef struct {
     int32_t call;            /* index of the call since the records were last read */
     float ms;                /* CUDA-event time of this launch group on the call's stream */
     uint64_t keys;           /* keys this launch processed (device counters) */
-    uint64_t counted_bytes;  /* algorithmic HBM bytes of this launch */
+    uint64_t counted_bytes;  /* algorithmic HBM bytes of this launch: keys read (histogram),
+                              * keys read and written (scatter, finish), keys written (fill);
+                              * a key-value call adds the values each key carries and, in the
+                              * finish and fills, the values or int64 positions written */
 } bsort_profile_record;
 
 typedef struct {

@@ -290,12 +290,14 @@ void begin_call(bsort_handle *h, cudaStream_t st) {
     h->rec.active = h->profiling && h->events && h->rec.calls < BSORT_PROFILE_MAX_CALLS;
 }
 
-void end_call(bsort_handle *h, cudaStream_t st, size_t n, int key_bytes) {
+void end_call(bsort_handle *h, cudaStream_t st, size_t n, int key_bytes, int val_bytes = 0, int out_bytes = 0) {
     if (h->rec.active) {
         const int c = h->rec.calls;
         h->prof_path[c] = h->last_path;
         h->prof_key_bytes[c] = key_bytes;
         h->prof_n[c] = n;
+        h->prof_val_bytes[c] = val_bytes;
+        h->prof_out_bytes[c] = out_bytes;
         if (h->last_ctl) cudaMemcpyAsync(h->prof_ctl + c, h->last_ctl, sizeof(Ctl), cudaMemcpyDeviceToDevice, st);
         ++h->rec.calls;
     }
@@ -539,6 +541,9 @@ bsort_status run_pairs_kv(bsort_handle *h, void *keys, void *values, size_t valu
     h->last_ctl = wk.ctl;
     h->last_inplace = false;
     h->last_fixed_aux = P.total;
+    // value bytes written per output element: the carried values, or int64
+    // positions (plus the 32-bit ones kept for the gather)
+    const int out_bytes = carry ? cb : (indices ? 8 : 0) + (gather ? 4 : 0);
     if (gather) {
         h->rec.begin(BSORT_K_FILL, -1);
         launch_gather(values, static_cast<int>(value_bytes), static_cast<const uint32_t *>(wk.vals), n, ws + P.tmp,
@@ -547,7 +552,7 @@ bsort_status run_pairs_kv(bsort_handle *h, void *keys, void *values, size_t valu
         if (cudaMemcpyAsync(values, ws + P.tmp, value_bytes * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
             return BSORT_ERR_CUDA;
     }
-    end_call(h, st, n, di.bytes);
+    end_call(h, st, n, di.bytes, cb, out_bytes);
     return cudaGetLastError() == cudaSuccess ? BSORT_OK : BSORT_ERR_CUDA;
 }
 
@@ -1072,6 +1077,9 @@ bsort_status bsort_handle_get_profile(bsort_handle *handle, bsort_profile *out) 
         const Ctl &ctl = ctls[src.call];
         const uint64_t b = static_cast<uint64_t>(handle->prof_key_bytes[src.call]);
         const uint64_t n = handle->prof_n[src.call];
+        // key-value calls: vb value bytes read with each key, ob written
+        const uint64_t vb = static_cast<uint64_t>(handle->prof_val_bytes[src.call]);
+        const uint64_t ob = static_cast<uint64_t>(handle->prof_out_bytes[src.call]);
         uint64_t keys = 0, bytes = 0;
         switch (r.kind) {
         case BSORT_K_HIST:
@@ -1080,15 +1088,15 @@ bsort_status bsort_handle_get_profile(bsort_handle *handle, bsort_profile *out) 
             break;
         case BSORT_K_SCATTER:
             keys = r.level >= 0 && r.level < kMaxLevels ? ctl.scatter_keys[r.level] : 0;
-            bytes = 2 * keys * b;
+            bytes = 2 * keys * (b + vb);
             break;
         case BSORT_K_FINISH:
             keys = ctl.finish_keys;
-            bytes = 2 * keys * b;
+            bytes = vb ? keys * (2 * b + vb + ob) : 2 * keys * b;
             break;
         case BSORT_K_FILL:
             keys = ctl.fill_keys;
-            bytes = keys * b;
+            bytes = vb ? keys * (b + vb + ob) : keys * b;  // (an upper bound: runs in place move no values)
             break;
         case BSORT_K_COUNT_HIST:
         case BSORT_K_COUNT_FILL:

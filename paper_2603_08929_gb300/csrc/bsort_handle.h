@@ -32,6 +32,10 @@ struct bsort_handle {
     int prof_path[BSORT_PROFILE_MAX_CALLS] = {0};
     int prof_key_bytes[BSORT_PROFILE_MAX_CALLS] = {0};
     uint64_t prof_n[BSORT_PROFILE_MAX_CALLS] = {0};
+    // key-value calls: bytes of the value carried through the levels, and of
+    // the value written per output element by the finish and fills (0: keys only)
+    int prof_val_bytes[BSORT_PROFILE_MAX_CALLS] = {0};
+    int prof_out_bytes[BSORT_PROFILE_MAX_CALLS] = {0};
     Recorder rec;
     std::mutex mu;
 };
