@@ -1919,6 +1919,15 @@ __global__ void k_drain(Work wk, int level) {
 // look at keys and are shared with keys-only sorting; a chunk's tiles are
 // ranked in order, each digit's destination moving on by the tile's count.
 
+// Scatter tiles per chunk of the key-value sort.
+constexpr uint32_t kKvChunkTiles = 4;
+
+// Key-value finish of 8-byte keys: units with more varying bits than
+// kKvWideBits are sorted by their top 16 bits, then runs of ties up to
+// kKvTieRun keys by comparison.
+constexpr int kKvWideBits = 24;
+constexpr int kKvTieRun = 16;
+
 // Shared memory of the stable ranking at byte offset BASE: two sets of
 // per-(digit, warp) counters, digit-major with one pad word per digit
 // (successive rankings alternate between the sets, so that one is cleared
@@ -2308,30 +2317,111 @@ __global__ void __launch_bounds__(THREADS, MINB) k_finish_kv(Work wk) {
         }
         const int lo = lsb_pos<K>(diff);
         const int hi = msb_pos<K>(diff) + 1;
-        const int passes = (hi - lo + kRadixBits - 1) / kRadixBits;
-        const int width = (hi - lo + passes - 1) / passes;
-        for (int ps = 0; ps < passes; ++ps) {
-            const int sh = lo + ps * width;
-            const uint32_t m = (1u << min(width, hi - sh)) - 1u;
-            uint32_t place[ITEMS];
-            uint32_t cnt;
-            stable_places<K, THREADS, ITEMS, RS>(k, vmask, sh, m, place, set, cnt);
-            set ^= 1;
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j) {
-                if ((vmask >> j) & 1u) {
-                    sm_keys[place[j]] = k[j];
-                    sm_vals[place[j]] = v[j];
+        if constexpr (sizeof(K) == 8) {
+            // Stable passes of at most 8 bits over the bits [from, to), least
+            // significant first; the unit ends staged in shared memory in that
+            // order.  Many varying bits (8-byte keys): the passes cover the top
+            // 16 only; the keys that still tie there form short runs in input
+            // order, each sorted in place by the whole key (insertion sort:
+            // stable) by the thread that finds its start.  A run longer than
+            // kKvTieRun sends the unit through the passes of the low bits and
+            // then the top bits again, from this order (still stable: equal keys
+            // keep their order).
+            const bool wide = hi - lo > kKvWideBits;
+            const int top = wide ? hi - 16 : lo;
+            int from = top, to = hi;
+            bool reload = false;  // the registers are stale: the unit is staged
+            for (int step = 0;; ++step) {
+                const int passes = (to - from + kRadixBits - 1) / kRadixBits;
+                const int width = (to - from + passes - 1) / passes;
+                for (int ps = 0; ps < passes; ++ps) {
+                    if (ps > 0 || reload) {  // back to registers in tile order
+    #pragma unroll
+                        for (int j = 0; j < ITEMS; ++j) {
+                            const int idx = (warp * cit + j) * 32 + lane;
+                            if ((vmask >> j) & 1u) {
+                                k[j] = sm_keys[idx];
+                                v[j] = sm_vals[idx];
+                            }
+                        }
+                    }
+                    const int sh = from + ps * width;
+                    const uint32_t m = (1u << min(width, to - sh)) - 1u;
+                    uint32_t place[ITEMS];
+                    uint32_t cnt;
+                    stable_places<K, THREADS, ITEMS, RS>(k, vmask, sh, m, place, set, cnt);
+                    set ^= 1;
+    #pragma unroll
+                    for (int j = 0; j < ITEMS; ++j) {
+                        if ((vmask >> j) & 1u) {
+                            sm_keys[place[j]] = k[j];
+                            sm_vals[place[j]] = v[j];
+                        }
+                    }
+                    __syncthreads();
                 }
+                if (!wide || step == 2) break;
+                reload = true;
+                if (step == 1) {  // the low bits are done: the top bits again
+                    from = top;
+                    to = hi;
+                    continue;
+                }
+                uint32_t longest = 0;
+                for (int i = t; i < len; i += THREADS) {
+                    const K ki = sm_keys[i];
+                    if (i > 0 && ((sm_keys[i - 1] ^ ki) >> top) == 0) continue;  // inside a run
+                    int e = i + 1;
+                    while (e < len && e - i <= kKvTieRun && ((sm_keys[e] ^ ki) >> top) == 0) ++e;
+                    const uint32_t run = static_cast<uint32_t>(e - i);
+                    longest = max(longest, run);
+                    if (run >= 2 && run <= static_cast<uint32_t>(kKvTieRun)) {
+                        for (int x = i + 1; x < e; ++x) {
+                            const K kx = sm_keys[x];
+                            const V vx = sm_vals[x];
+                            int y = x - 1;
+                            while (y >= i && sm_keys[y] > kx) {
+                                sm_keys[y + 1] = sm_keys[y];
+                                sm_vals[y + 1] = sm_vals[y];
+                                --y;
+                            }
+                            sm_keys[y + 1] = kx;
+                            sm_vals[y + 1] = vx;
+                        }
+                    }
+                }
+                if (block_reduce_max<THREADS>(longest, RS::scan()) <= static_cast<uint32_t>(kKvTieRun)) break;
+                from = lo;  // a long run: every pass, the low bits first
+                to = top;
             }
-            __syncthreads();
-            if (ps + 1 < passes) {  // back to registers in tile order for the next pass
-#pragma unroll
+        } else {
+            // 4-byte keys: stable passes of at most 8 bits over the varying bits,
+            // least significant first; the unit ends staged in shared memory.
+            const int passes = (hi - lo + kRadixBits - 1) / kRadixBits;
+            const int width = (hi - lo + passes - 1) / passes;
+            for (int ps = 0; ps < passes; ++ps) {
+                const int sh = lo + ps * width;
+                const uint32_t m = (1u << min(width, hi - sh)) - 1u;
+                uint32_t place[ITEMS];
+                uint32_t cnt;
+                stable_places<K, THREADS, ITEMS, RS>(k, vmask, sh, m, place, set, cnt);
+                set ^= 1;
+    #pragma unroll
                 for (int j = 0; j < ITEMS; ++j) {
-                    const int idx = (warp * cit + j) * 32 + lane;
                     if ((vmask >> j) & 1u) {
-                        k[j] = sm_keys[idx];
-                        v[j] = sm_vals[idx];
+                        sm_keys[place[j]] = k[j];
+                        sm_vals[place[j]] = v[j];
+                    }
+                }
+                __syncthreads();
+                if (ps + 1 < passes) {  // back to registers in tile order for the next pass
+    #pragma unroll
+                    for (int j = 0; j < ITEMS; ++j) {
+                        const int idx = (warp * cit + j) * 32 + lane;
+                        if ((vmask >> j) & 1u) {
+                            k[j] = sm_keys[idx];
+                            v[j] = sm_vals[idx];
+                        }
                     }
                 }
             }
@@ -2414,9 +2504,6 @@ struct Cfg<u128> {
     static constexpr int kFinThreads = 256;  // 256 x 5 = 1280 keys
     static constexpr int kFinItems = 5;
 };
-
-// Scatter tiles per chunk of the key-value sort.
-constexpr uint32_t kKvChunkTiles = 4;
 
 // Key-value sorting: 256-thread CTAs; the scatter tile is 4096 pairs (a
 // chunk is kKvChunkTiles of them), the finish tile holds the largest unit.  4-byte keys with 4-byte

@@ -168,6 +168,28 @@ def test_pairs_unit_boundaries(dtype, n):
     check(x, None, False, run_pairs(x, None, False, indices=True))
 
 
+@pytest.mark.parametrize("dtype", ["int64", "uint64", "int32"])
+@pytest.mark.parametrize("n", [2000, 2559, 5000, 100003])
+@pytest.mark.parametrize("high", [4, 256, 1 << 16])
+def test_pairs_wide_units(dtype, n, high):
+    """Finish units with more than 24 varying bits: stable passes over the
+    top 16, then runs of ties there sorted by the whole key -- short runs
+    (high = 2^16 top values: few ties; 256: runs of a few keys) and runs too
+    long for that (high = 4), which take every pass.  Keys: a random high
+    part above a gap of zero bits and a random low part."""
+    rng = np.random.default_rng(n + high)
+    shift = 40 if dtype != "int32" else 28
+    lowbits = 20 if dtype != "int32" else 16
+    hi_part = rng.integers(0, min(high, 1 << (63 - shift if dtype != "int32" else 3)), n).astype(np.int64)
+    x = ((hi_part << shift) | rng.integers(0, 1 << lowbits, n)).astype(dtype)
+    if dtype.startswith("int"):
+        x[::7] = -x[::7]  # both signs
+    vals = W.make("uniform", "int64", n, seed=n + 3)
+    check(x, vals, False, run_pairs(x, vals, False, indices=False))
+    check(x, vals, True, run_pairs(x, vals, True, indices=True))
+    check(x, None, False, run_pairs(x, None, False, indices=True))
+
+
 @pytest.mark.parametrize("dtype", ["int32", "float64"])
 def test_pairs_degenerate_keys(dtype):
     """All keys equal (the whole array one run: values keep input order, the
