@@ -1954,18 +1954,23 @@ struct StableSmem {
     }
 };
 
-// Place of every item in the tile ordered by digit, ties in tile order;
-// thread d <= mask also gets the tile's count of digit d.  Counter set `set`
-// must be zero on entry; the other set is zeroed here for the next ranking
-// (the caller passes the sets alternately and has a barrier between this
-// call's last read of the counters -- the place lookups at the end -- and
-// the next call).  Three barriers.
-template <typename K, int THREADS, int ITEMS, typename SS>
-__device__ __forceinline__ void stable_places(const K (&keys)[ITEMS], uint32_t vmask, int shift, uint32_t mask,
-                                              uint32_t (&place)[ITEMS], int set, uint32_t &count) {
+// Places every valid item of the tile -- key and value -- in out_k / out_v
+// ordered by digit, ties in tile order; thread d <= mask also gets the
+// tile's count of digit d.  Counter set `set` must be zero on entry; the
+// other set is zeroed here for the next ranking (the caller passes the sets
+// alternately and has a barrier between this call's last read of the
+// counters -- the lookups at the end -- and the next call; the placed items
+// are visible after the caller's next barrier).  A rank inside a warp's
+// digit is below 2^16 (the tile is smaller), so two share a register.
+// Three barriers.
+template <typename K, typename V, int THREADS, int ITEMS, typename SS>
+__device__ __forceinline__ void stable_rank_place(const K (&keys)[ITEMS], const V (&vals)[ITEMS], uint32_t vmask,
+                                                  int shift, uint32_t mask, int set, uint32_t &count, K *out_k,
+                                                  V *out_v) {
     constexpr int WARPS = THREADS / 32;
     constexpr int STRIDE = WARPS + 1;
     static_assert(THREADS >= kBins, "one thread per digit in the scans");
+    static_assert(THREADS * ITEMS < 65536, "ranks fit 16 bits");
     uint32_t *wc = SS::wc(set);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int t = threadIdx.x;
@@ -1974,10 +1979,12 @@ __device__ __forceinline__ void stable_places(const K (&keys)[ITEMS], uint32_t v
         for (int i = t; i < SS::kWcWords; i += THREADS) wc_next[i] = 0;
     }
     const unsigned lt = lanemask_lt();
+    uint32_t rank[(ITEMS + 1) / 2];  // item j's rank in its warp's digit at bit 16 (j & 1)
+#pragma unroll
+    for (int j = 0; j < (ITEMS + 1) / 2; ++j) rank[j] = 0;
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
         const bool valid = (vmask >> j) & 1u;
-        place[j] = 0;
         if (__any_sync(kFull, valid)) {  // warp-uniform
             const uint32_t d = static_cast<uint32_t>(keys[j] >> shift) & mask;
             uint32_t *wcd = wc + d * STRIDE + warp;
@@ -1996,7 +2003,7 @@ __device__ __forceinline__ void stable_places(const K (&keys)[ITEMS], uint32_t v
                 *wcd = before + __popc(peers);
                 wm[d] = 0;
             }
-            place[j] = before + r;
+            rank[j >> 1] |= (before + r) << ((j & 1) * 16);
         }
     }
     __syncthreads();
@@ -2031,9 +2038,14 @@ __device__ __forceinline__ void stable_places(const K (&keys)[ITEMS], uint32_t v
     }
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < ITEMS; ++j)
-        if ((vmask >> j) & 1u)
-            place[j] += wc[(static_cast<uint32_t>(keys[j] >> shift) & mask) * STRIDE + warp];
+    for (int j = 0; j < ITEMS; ++j) {
+        if ((vmask >> j) & 1u) {
+            const uint32_t p = wc[(static_cast<uint32_t>(keys[j] >> shift) & mask) * STRIDE + warp] +
+                               ((rank[j >> 1] >> ((j & 1) * 16)) & 0xffffu);
+            out_k[p] = keys[j];
+            out_v[p] = vals[j];
+        }
+    }
 }
 
 // A value of the key-value sort: 4 or 8 bytes.
@@ -2166,8 +2178,9 @@ __global__ void __launch_bounds__(THREADS, MINB) k_scatter_kv(Work wk, int level
 #pragma unroll
                 for (int j = 0; j < ITEMS; ++j) k[j] = encode_key(k[j], wk.codec);
             }
-            uint32_t place[ITEMS], cnt;
-            stable_places<K, THREADS, ITEMS, RS>(k, vmask, shift, mask, place, set, cnt);
+            uint32_t cnt;
+            stable_rank_place<K, V, THREADS, ITEMS, RS>(k, v, vmask, shift, mask, set, cnt, sm_keys,
+                                                          sm_vals);
             // digit d's run: staging slots from its tile start, so the key at
             // staging slot q goes to off[d] + q
             if (t <= static_cast<int>(mask)) {
@@ -2175,13 +2188,6 @@ __global__ void __launch_bounds__(THREADS, MINB) k_scatter_kv(Work wk, int level
                 dest += cnt;
             }
             set ^= 1;
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j) {
-                if ((vmask >> j) & 1u) {
-                    sm_keys[place[j]] = k[j];
-                    sm_vals[place[j]] = v[j];
-                }
-            }
             __syncthreads();
         }
         const Bucket cb = b;
@@ -2336,7 +2342,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_finish_kv(Work wk) {
                 const int width = (to - from + passes - 1) / passes;
                 for (int ps = 0; ps < passes; ++ps) {
                     if (ps > 0 || reload) {  // back to registers in tile order
-    #pragma unroll
+#pragma unroll
                         for (int j = 0; j < ITEMS; ++j) {
                             const int idx = (warp * cit + j) * 32 + lane;
                             if ((vmask >> j) & 1u) {
@@ -2347,17 +2353,10 @@ __global__ void __launch_bounds__(THREADS, MINB) k_finish_kv(Work wk) {
                     }
                     const int sh = from + ps * width;
                     const uint32_t m = (1u << min(width, to - sh)) - 1u;
-                    uint32_t place[ITEMS];
                     uint32_t cnt;
-                    stable_places<K, THREADS, ITEMS, RS>(k, vmask, sh, m, place, set, cnt);
+                    stable_rank_place<K, V, THREADS, ITEMS, RS>(k, v, vmask, sh, m, set, cnt, sm_keys,
+                                                                  sm_vals);
                     set ^= 1;
-    #pragma unroll
-                    for (int j = 0; j < ITEMS; ++j) {
-                        if ((vmask >> j) & 1u) {
-                            sm_keys[place[j]] = k[j];
-                            sm_vals[place[j]] = v[j];
-                        }
-                    }
                     __syncthreads();
                 }
                 if (!wide || step == 2) break;
@@ -2402,20 +2401,13 @@ __global__ void __launch_bounds__(THREADS, MINB) k_finish_kv(Work wk) {
             for (int ps = 0; ps < passes; ++ps) {
                 const int sh = lo + ps * width;
                 const uint32_t m = (1u << min(width, hi - sh)) - 1u;
-                uint32_t place[ITEMS];
                 uint32_t cnt;
-                stable_places<K, THREADS, ITEMS, RS>(k, vmask, sh, m, place, set, cnt);
+                stable_rank_place<K, V, THREADS, ITEMS, RS>(k, v, vmask, sh, m, set, cnt, sm_keys,
+                                                              sm_vals);
                 set ^= 1;
-    #pragma unroll
-                for (int j = 0; j < ITEMS; ++j) {
-                    if ((vmask >> j) & 1u) {
-                        sm_keys[place[j]] = k[j];
-                        sm_vals[place[j]] = v[j];
-                    }
-                }
                 __syncthreads();
                 if (ps + 1 < passes) {  // back to registers in tile order for the next pass
-    #pragma unroll
+#pragma unroll
                     for (int j = 0; j < ITEMS; ++j) {
                         const int idx = (warp * cit + j) * 32 + lane;
                         if ((vmask >> j) & 1u) {
