@@ -155,10 +155,13 @@ class LibrarySegmentOps:
     """The device step of the batched form: one segmented sort."""
 
     def sort_segments(self, keys, offsets, descending):
+        """``offsets``: the run's segment boundaries relative to ``keys`` (a
+        numpy array or a tensor on any device)."""
         import torch
         from . import bsort_keys_segmented
-        if keys.numel() > 1 and offsets.numel() > 1:
-            off = torch.as_tensor(offsets, dtype=torch.int64, device=keys.device)
+        off = torch.as_tensor(np.asarray(offsets.cpu() if hasattr(offsets, "cpu") else offsets, dtype=np.int64),
+                              device=keys.device)
+        if keys.numel() > 1 and off.numel() > 1:
             bsort_keys_segmented(keys, off, descending=descending)
 
 

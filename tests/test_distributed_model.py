@@ -222,3 +222,27 @@ def test_gloo_ranks_sort_a_batch(world):
     assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
     sizes = np.diff(off)
     assert max(off[r[2]] - off[r[1]] for r in res) <= sizes.sum() / world + 2 * sizes.max()
+
+
+@pytest.mark.parametrize("as_tensor", [False, True])
+def test_library_segment_ops_hands_the_library_an_int64_tensor(monkeypatch, as_tensor):
+    """The device step of the batched form receives the run's boundaries as
+    numpy (from the plan) or as a tensor; the segmented sort it calls wants
+    an int64 tensor on the keys' device.  The library call is replaced here
+    by a recorder (no GPU)."""
+    import torch
+    import paper_2603_08929_gb300 as pkg
+    from paper_2603_08929_gb300 import distributed as D
+    seen = []
+    monkeypatch.setattr(pkg, "bsort_keys_segmented",
+                        lambda keys, off, descending=False: seen.append((keys, off, descending)))
+    keys = torch.arange(10, dtype=torch.int32)
+    off = np.array([0, 3, 3, 10], dtype=np.int64)
+    D.LibrarySegmentOps().sort_segments(keys, torch.from_numpy(off) if as_tensor else off, True)
+    (k, o, desc), = seen
+    assert k is keys and desc is True
+    assert isinstance(o, torch.Tensor) and o.dtype == torch.int64 and o.device == keys.device
+    assert o.tolist() == off.tolist()
+    seen.clear()
+    D.LibrarySegmentOps().sort_segments(keys[:1], np.array([0, 1]), False)  # one key: nothing to sort
+    assert not seen
