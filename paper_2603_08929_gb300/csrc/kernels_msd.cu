@@ -2048,18 +2048,6 @@ __device__ __forceinline__ void stable_rank_place(const K (&keys)[ITEMS], const 
     }
 }
 
-// A value of the key-value sort: 4 or 8 bytes.
-template <int VB>
-struct ValT;
-template <>
-struct ValT<4> {
-    using T = uint32_t;
-};
-template <>
-struct ValT<8> {
-    using T = uint64_t;
-};
-
 template <typename V>
 __device__ __forceinline__ const V *vals_of(const Work &wk, int src) {
     return static_cast<const V *>(src ? wk.vals_alt : wk.vals);
