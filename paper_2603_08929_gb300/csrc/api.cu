@@ -87,7 +87,7 @@ struct MsdLayout {
 
 MsdLayout msd_layout(size_t n, int key_bytes, size_t nseg = 0, bool inplace = false, const Tuning &tune = Tuning(),
                      int kv_bytes = 0, bool kv_pos = false) {
-    const MsdShape s = msd_shape(key_bytes, tune, inplace, kv_bytes);
+    const MsdShape s = msd_shape(key_bytes, tune, inplace, kv_bytes, n);
     MsdLayout L;
     // finish units hold at least merge_cap / 4 keys unless merged, and merged
     // groups reach merge_cap unless a run ends: the unit count per level is
@@ -231,7 +231,7 @@ bsort_status check_args(const void *keys, size_t n, bsort_dtype dt, DtypeInfo *d
 
 Work make_work(const MsdLayout &L, char *ws, void *keys, size_t n, const DtypeInfo &di, const Codec &codec,
                const Tuning &tune = Tuning()) {
-    const MsdShape s = msd_shape(di.bytes, tune, L.inplace, L.kv_bytes);
+    const MsdShape s = msd_shape(di.bytes, tune, L.inplace, L.kv_bytes, n);
     Work wk;
     wk.ctl = reinterpret_cast<Ctl *>(ws + L.ctl);
     wk.buckets[0] = reinterpret_cast<Bucket *>(ws + L.buckets0);

@@ -77,8 +77,10 @@ struct Tuning {
 // false: a field is out of range.
 bool tuning_valid(int key_bytes, const Tuning &t);
 // kv_bytes: 0 for keys only, else the value bytes of the stable key-value
-// sort (4 or 8), which has its own fixed shape.
-MsdShape msd_shape(int key_bytes, const Tuning &t = Tuning(), bool inplace = false, int kv_bytes = 0);
+// sort (4 or 8), which has its own shape (its finish capacity depends on n
+// for 4-byte keys with 8-byte values).
+MsdShape msd_shape(int key_bytes, const Tuning &t = Tuning(), bool inplace = false, int kv_bytes = 0,
+                   uint64_t n = 0);
 
 // Launches the whole MSD pipeline for 4- or 8-byte keys.
 template <typename K>

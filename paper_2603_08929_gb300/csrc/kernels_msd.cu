@@ -2485,10 +2485,10 @@ struct Cfg<u128> {
     static constexpr int kFinItems = 5;
 };
 
+constexpr uint64_t kKvBigChild = 2600;
+
 // Key-value sorting: 256-thread CTAs; the scatter tile is 4096 pairs (a
-// chunk is kKvChunkTiles of them), the finish tile holds the largest unit.  4-byte keys with 4-byte
-// values keep the keys-only finish capacity (5120), so the same buckets end
-// after the same levels.
+// chunk is kKvChunkTiles of them), the finish tile holds the largest unit.
 template <typename K, typename V>
 struct KvCfg {
     static constexpr int kPairBytes = static_cast<int>(sizeof(K) + sizeof(V));
@@ -2498,11 +2498,19 @@ struct KvCfg {
     static constexpr int kFinThreads = 256;
     static constexpr int kFinItems = kPairBytes <= 8 ? 20 : (kPairBytes <= 12 ? 12 : 10);
     static constexpr int kFinCtas = 3;
+    // 4-byte keys with 8-byte values, large arrays: a 5120-pair finish (96 KB
+    // of shared memory, two CTAs per SM), so that level-1 children of ~4096
+    // pairs finish without a third scatter level; chosen when the average
+    // level-1 child passes kKvBigChild pairs (smaller arrays keep the
+    // 3072-pair finish at three CTAs per SM)
+    static constexpr bool kHasBig = sizeof(K) == 4 && sizeof(V) == 8;
+    static constexpr int kFinItemsBig = 20;
+    static constexpr int kFinCtasBig = 2;
 };
 
 }  // namespace
 
-MsdShape msd_shape(int key_bytes, const Tuning &t, bool inplace, int kv_bytes) {
+MsdShape msd_shape(int key_bytes, const Tuning &t, bool inplace, int kv_bytes, uint64_t n) {
     MsdShape s;
     uint32_t fin;
     if (kv_bytes) {  // key-value sorting: fixed shape, 8-bit digits, one scatter tile per chunk
@@ -2515,6 +2523,8 @@ MsdShape msd_shape(int key_bytes, const Tuning &t, bool inplace, int kv_bytes) {
                        : KvCfg<uint32_t, uint64_t>::kFinThreads * KvCfg<uint32_t, uint64_t>::kFinItems)
                  : (v4 ? KvCfg<uint64_t, uint32_t>::kFinThreads * KvCfg<uint64_t, uint32_t>::kFinItems
                        : KvCfg<uint64_t, uint64_t>::kFinThreads * KvCfg<uint64_t, uint64_t>::kFinItems);
+        if (k4 && !v4 && n / (1u << (2 * kRadixBits)) > kKvBigChild)
+            fin = KvCfg<uint32_t, uint64_t>::kFinThreads * KvCfg<uint32_t, uint64_t>::kFinItemsBig;
         s.radix_bits = kRadixBits;
         s.bins = kBins;
         s.levels = (key_bytes * 8 + kRadixBits - 1) / kRadixBits;
@@ -2672,16 +2682,23 @@ void launch_msd_kv(const Work &wk, cudaStream_t st, Recorder &rec, int num_sms) 
     using C = KvCfg<K, V>;
     constexpr int T = C::kThreads, I = C::kItems, SB = C::kScatterCtas;
     constexpr int FT = C::kFinThreads, FI = C::kFinItems, FB = C::kFinCtas;
+    constexpr int FIB = C::kFinItemsBig, FBB = C::kFinCtasBig;
     constexpr size_t kScatterSmem = ScatterKvSmem<K, V, T, I>::kEnd;
     constexpr size_t kFinishSmem = FinishKvSmem<K, V, FT, FI>::kEnd;
+    constexpr size_t kFinishSmemBig = FinishKvSmem<K, V, FT, FIB>::kEnd;
     static const bool attrs = [] {  // once per process
         cudaFuncSetAttribute(k_scatter_kv<K, V, T, I, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(kScatterSmem));
         cudaFuncSetAttribute(k_finish_kv<K, V, FT, FI, FB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(kFinishSmem));
+        if constexpr (C::kHasBig)
+            cudaFuncSetAttribute(k_finish_kv<K, V, FT, FIB, FBB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(kFinishSmemBig));
         return true;
     }();
     (void)attrs;
+    // the finish whose tile the shape's unit capacity was sized for
+    const bool big = C::kHasBig && wk.unit_cap > static_cast<uint32_t>(FT * FI);
     const bool direct = wk.n <= wk.unit_cap;
     const uint32_t nc0 = direct ? 0u : static_cast<uint32_t>((wk.n + wk.chunk_keys - 1) / wk.chunk_keys);
     rec.begin(BSORT_K_INIT, -1);
@@ -2704,7 +2721,12 @@ void launch_msd_kv(const Work &wk, cudaStream_t st, Recorder &rec, int num_sms) 
         }
     }
     rec.begin(BSORT_K_FINISH, -1);
-    launch_pdl(k_finish_kv<K, V, FT, FI, FB>, num_sms * FB, FT, kFinishSmem, st, wk);
+    if (big) {
+        if constexpr (C::kHasBig)
+            launch_pdl(k_finish_kv<K, V, FT, FIB, FBB>, num_sms * FBB, FT, kFinishSmemBig, st, wk);
+    } else {
+        launch_pdl(k_finish_kv<K, V, FT, FI, FB>, num_sms * FB, FT, kFinishSmem, st, wk);
+    }
     rec.end();
     if (!direct) {
         rec.begin(BSORT_K_FILL, -1);

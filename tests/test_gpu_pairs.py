@@ -247,14 +247,15 @@ def check_stable_permutation(x, k, ix, desc=False):
     assert np.all(ix[1:][same] > ix[:-1][same]), "ties out of input order"
 
 
-@pytest.mark.parametrize("dist", ["uniform", "distinct8"])
-def test_pairs_carried_at_size(dist):
+@pytest.mark.parametrize("dist,vdtype", [("uniform", "int32"), ("distinct8", "int32"), ("uniform", "int64")])
+def test_pairs_carried_at_size(dist, vdtype):
     """The key-value workload at full size: 2^28 int32 keys carrying int32
-    values (their input positions, so the carried values are the
-    permutation): a permutation, the keys it gathers are the output, sorted,
+    values, or int64 values (the large-array finish of 12-byte pairs), the
+    values being their input positions, so the carried values are the
+    permutation: a permutation, the keys it gathers are the output, sorted,
     ties in input order."""
     n = 1 << 28
     x = W.make(dist, "int32", n, seed=12)
-    vals = np.arange(n, dtype=np.int32)
+    vals = np.arange(n, dtype=vdtype)
     k, v, _, _ = run_pairs(x, vals, False, indices=False)
     check_stable_permutation(x, k, v.astype(np.int64))
