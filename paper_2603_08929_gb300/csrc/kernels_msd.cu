@@ -956,8 +956,15 @@ __global__ void __launch_bounds__(THREADS) k_classify(Work wk, int level) {
                 un.len = ulen;
                 un.src = static_cast<uint8_t>(dst);
                 un.raw = 0;
-                // one child agrees above the digit; a merged group above the parent's bits
-                un.vbits = static_cast<uint8_t>(head ? b.h : hc);
+                // one child agrees above the digit; a merged group above the parent's bits.
+                // The fast counting finish that this enables needs sparse
+                // sub-buckets (under 16 keys per 16 values): a child averaging
+                // more than one key per 4 values, or a merged group whose
+                // children may (up to merge_cap / 4 keys each), goes to the
+                // general path without trying it
+                const uint32_t most = head ? wk.merge_cap / 4 : ulen;
+                const bool dense = hc < 18 && most > (1u << (hc >= 2 ? hc - 2 : 0));
+                un.vbits = dense ? 0 : static_cast<uint8_t>(head ? b.h : hc);
                 un.pad = 0;
                 wk.units[sh_bases[0] + slot] = un;
             }

@@ -105,6 +105,22 @@ def test_fast_path_hands_off(case):
     assert fu["counting"] + fu["compare"] + fu["lsd"] == 256, fu
 
 
+@pytest.mark.parametrize("bits", [8, 12])
+def test_dense_units_skip_the_fast_path(bits):
+    """Units whose keys are dense in their few free bits (~2000 keys over
+    2^8 or 2^12 values: sub-buckets of 16 values would hold 16 keys or more)
+    go to the general path without trying the fast one; exact either way."""
+    rng = np.random.default_rng(5 + bits)
+    parts = [(np.uint64(u) << np.uint64(bits)) | rng.integers(0, 1 << bits, 2000 + int(rng.integers(0, 100)))
+             .astype(np.uint64) for u in range(256)]
+    x = np.concatenate(parts).astype(np.uint32)
+    rng.shuffle(x)
+    got, fu = sorted_with_profile(x)
+    assert_bit_exact(got, O.bsort(x), "dense units, %d bits" % bits)
+    assert fu["counting_fast"] == 0, fu
+    assert fu["counting"] + fu["compare"] + fu["lsd"] == 256, fu
+
+
 @pytest.mark.parametrize("two_scatters", [False, True], ids=["units_in_alt", "units_in_caller_buffer"])
 @pytest.mark.parametrize("offset", [1, 2, 3])
 def test_fast_path_unaligned_buffer(offset, two_scatters):
