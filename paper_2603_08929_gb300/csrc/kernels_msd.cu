@@ -1487,6 +1487,55 @@ __device__ __forceinline__ bool finish_count_fast(const Work &wk, const Unit &un
     return true;
 }
 
+// Direct counting finish of a unit whose keys vary in at most 12 bits
+// [lo, lo + span) with at least half a key per value: one counter per value,
+// a scan, and every value's run written from its count into u16 staging
+// (equal keys are bit-identical), then the keys rebuilt from the bits they
+// all share (`a`) and written, decoded.  The keys are read again here (from
+// L2: the caller has just read them) so that this path keeps its registers
+// out of the caller's; thread t owns the values [t * per, (t + 1) * per).
+// cnt: 2^span words, staged: len halfwords, both shared memory.
+template <typename K, int THREADS>
+__device__ __noinline__ void finish_direct(const K *__restrict__ src, K *__restrict__ dstp, int len, bool raw,
+                                           Codec codec, K a, int lo, int span, uint32_t *cnt, uint16_t *staged,
+                                           uint32_t *scan_tmp, Ctl *ctl) {
+    const int t = threadIdx.x;
+    const int nv = 1 << span;
+    const uint32_t fmask = static_cast<uint32_t>(nv - 1);
+    for (int i = t; i < nv; i += THREADS) cnt[i] = 0;
+    __syncthreads();
+    for (int i = t; i < len; i += THREADS) {
+        K key = src[i];
+        if (raw) key = encode_key(key, codec);
+        atomicAdd(&cnt[static_cast<uint32_t>(key >> lo) & fmask], 1u);
+    }
+    __syncthreads();
+    const int per = nv > THREADS ? nv / THREADS : 1;
+    const int v0 = t * per;
+    uint32_t sum = 0;
+    if (v0 < nv)
+        for (int e = 0; e < per; ++e) sum += cnt[v0 + e];
+    uint32_t total;
+    uint32_t at = block_exclusive_scan<THREADS>(sum, scan_tmp, total);
+    const bool ok = total == static_cast<uint32_t>(len);
+    if (ok && v0 < nv) {
+        for (int e = 0; e < per; ++e) {
+            const uint32_t c = cnt[v0 + e];
+            for (uint32_t q = 0; q < c; ++q) staged[at + q] = static_cast<uint16_t>(v0 + e);
+            at += c;
+        }
+    }
+    __syncthreads();
+    if (!ok) {
+        if (t == 0) set_error(ctl, kErrBounds);
+        return;
+    }
+    const K common = a & ~(static_cast<K>(fmask) << lo);  // the bits every key shares
+    for (int i = t; i < len; i += THREADS)
+        dstp[i] = decode_key(static_cast<K>(common | (static_cast<K>(staged[i]) << lo)), codec);
+    if (t == 0) atomicAdd(&ctl->fin_counting, 1ull);
+}
+
 // Sorts every unit in shared memory and writes it, decoded, to its final
 // place.  With at most 16 varying bits (and enough keys to fill the
 // sub-buckets) one counting pass finishes the unit: the bits above the low 4
@@ -1580,6 +1629,13 @@ __global__ void __launch_bounds__(THREADS, 4) k_finish(Work wk) {
         const int span = hi - lo;
         const int lbits = span < 4 ? span : 4;
         const int sbits = span - lbits;
+        if constexpr (sizeof(K) == 4) {  // (wider keys rarely leave so few varying bits with so many keys)
+            if (__builtin_expect(span <= kSplitBits && (1 << span) <= 2 * len, 0)) {
+                finish_direct<K, THREADS>(src, dstp, len, raw, wk.codec, a, lo, span, w32,
+                                          reinterpret_cast<uint16_t *>(g_dyn_smem + FL::kStage16), scan_tmp, wk.ctl);
+                continue;
+            }
+        }
         if (span <= kSplitBits + 4 && (1 << sbits) <= 4 * len) {
             // counting path: count (every table entry is cleared and scanned:
             // 16 sub-buckets per thread, unused ones stay zero)

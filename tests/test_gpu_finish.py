@@ -105,11 +105,13 @@ def test_fast_path_hands_off(case):
     assert fu["counting"] + fu["compare"] + fu["lsd"] == 256, fu
 
 
-@pytest.mark.parametrize("bits", [8, 12])
+@pytest.mark.parametrize("bits", [8, 10, 12])
 def test_dense_units_skip_the_fast_path(bits):
     """Units whose keys are dense in their few free bits (~2000 keys over
-    2^8 or 2^12 values: sub-buckets of 16 values would hold 16 keys or more)
-    go to the general path without trying the fast one; exact either way."""
+    2^8 .. 2^12 values: sub-buckets of 16 values would hold 16 keys or more)
+    go to the general path without trying the fast one -- 8 and 10 free bits
+    to the direct counting (one counter per value), 12 to the counting pass;
+    exact either way."""
     rng = np.random.default_rng(5 + bits)
     parts = [(np.uint64(u) << np.uint64(bits)) | rng.integers(0, 1 << bits, 2000 + int(rng.integers(0, 100)))
              .astype(np.uint64) for u in range(256)]
@@ -155,3 +157,22 @@ def test_fast_path_2p27():
     got, fu = sorted_with_profile(x)
     assert_bit_exact(got, oracle_expected(x), "int32 2^27")
     assert fu["counting_fast"] > 0.99 * (fu["counting"] + fu["compare"] + fu["lsd"]), fu
+
+
+@pytest.mark.parametrize("case", ["int32_pos", "int32_neg", "uint32", "float32_pos", "float32_neg"])
+@pytest.mark.parametrize("n", [600, 3000, 5100])
+def test_direct_counting_of_raw_units(case, n):
+    """A small array is one unit read straight from the caller's buffer
+    (still in its own encoding); keys that differ only in 8 to 10 low bits of
+    the sort order (one sign: the sign bit is a sort-order bit) take the
+    direct counting finish: exact, both directions."""
+    rng = np.random.default_rng(n)
+    x = {"int32_pos": lambda: rng.integers(1000, 1256, n).astype(np.int32),
+         "int32_neg": lambda: rng.integers(-300, -44, n).astype(np.int32),
+         "uint32": lambda: ((0xABCD << 16) | rng.integers(0, 1024, n)).astype(np.uint32),
+         "float32_pos": lambda: (1.0 + rng.integers(0, 256, n) / 256.0).astype(np.float32),
+         "float32_neg": lambda: -(1.0 + rng.integers(0, 256, n) / 256.0).astype(np.float32)}[case]()
+    for desc in (False, True):
+        got, fu = sorted_with_profile(x, desc)
+        assert_bit_exact(got, O.bsort(x, descending=desc), "%s n=%d desc=%s" % (case, n, desc))
+        assert fu["counting"] == 1 and fu["counting_fast"] == 0, fu
