@@ -1035,6 +1035,27 @@ template <typename K, int ITEMS, bool FULL, bool SKEW>
 __device__ __forceinline__ void stage_keys(const K (&k)[ITEMS], uint32_t vmask, int shift, uint32_t mask,
                                            uint32_t *cur, K *sm_keys, int cap, bool &overflow) {
     const int lane = threadIdx.x & 31;
+    if (SKEW && FULL) {
+        // the warp's whole tile in one digit (presorted or heavily skewed
+        // input): one atomic for its 32 * ITEMS keys -- same-address atomics
+        // of every warp and item would serialise
+        const uint32_t d0 = __shfl_sync(kFull, static_cast<uint32_t>(k[0] >> shift) & mask, 0);
+        bool same = true;
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) same &= (static_cast<uint32_t>(k[j] >> shift) & mask) == d0;
+        if (__all_sync(kFull, same)) {
+            uint32_t base = 0;
+            if (lane == 0) base = atomicAdd(&cur[d0], 32u * ITEMS);
+            base = __shfl_sync(kFull, base, 0);
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) {
+                const uint32_t slot = base + static_cast<uint32_t>(j * 32 + lane);
+                overflow |= slot >= static_cast<uint32_t>(cap);
+                sm_keys[min(slot, static_cast<uint32_t>(cap - 1))] = k[j];
+            }
+            return;
+        }
+    }
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
         const bool valid = FULL || ((vmask >> j) & 1u);
