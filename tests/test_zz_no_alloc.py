@@ -7,6 +7,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle as O
 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -43,6 +44,8 @@ def test_noalloc_matches_bsort_keys_two_calls_in_a_row(lib):
                     (W.make("zipf", "uint16", 500000, seed=23), False)):
         want, got = _sort_both(lib, x, desc)
         assert np.array_equal(got.view(np.uint8), want.view(np.uint8)), x.dtype
+        # and both are the sort the paper defines
+        assert np.array_equal(got.view(np.uint8), O.bsort(x, descending=desc).view(np.uint8)), x.dtype
 
 
 def _largest_n(dtype, cap=64 << 20):
