@@ -253,12 +253,12 @@ bsort_status bsort_keys_host(void *host_keys, size_t n, bsort_dtype dt, int desc
  * when a key is first read), the int64 indices are written beside the sorted
  * keys and values of any width follow by one gather along the positions.
  * With neither values nor indices the keys-only sort runs.  1- and 2-byte
- * keys: each key's order-preserving code (high 32 bits) and its input
- * position (low 32 bits) form one 64-bit word; the words are distinct, so
- * the 8-byte MSD sort of the words is the stable order; values follow by one
- * gather.  The handle's tuning for 8-byte keys applies to that word sort
- * only (bsort_pairs_workspace_bytes_tuned gives its workspace; NULL:
- * defaults); the value-carrying levels have a fixed shape.
+ * keys: each key's order-preserving code is widened to a 32-bit word, the
+ * words are sorted so (unsigned, ascending) and narrowed back to keys.  The
+ * value-carrying levels have a fixed shape: no handle tuning applies, and
+ * bsort_pairs_workspace_bytes_tuned (kept for callers of earlier versions;
+ * it validates the tuning) returns the same bytes as
+ * bsort_pairs_workspace_bytes.
  */
 bsort_status bsort_pairs_workspace_bytes(size_t n, bsort_dtype dt, size_t *bytes);
 bsort_status bsort_pairs_workspace_bytes_tuned(size_t n, bsort_dtype dt, const bsort_tuning *tuning8, size_t *bytes);

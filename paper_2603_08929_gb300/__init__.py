@@ -358,8 +358,8 @@ def bsort_keys_ws(handle: Handle, keys, workspace, descending: bool = False, str
 
 
 def pairs_workspace_bytes(n: int, dtype, tuning8: dict = None) -> int:
-    """Workspace bytes of a key-value sort of n keys (``tuning8``: the
-    handle's tuning for 8-byte keys, which the sort of the packed words uses)."""
+    """Workspace bytes of a key-value sort of n keys (``tuning8`` is
+    validated and has no effect: the key-value levels have a fixed shape)."""
     out = ctypes.c_size_t(0)
     if tuning8 is None:
         _check(lib().bsort_pairs_workspace_bytes(int(n), _dtype_code(dtype), ctypes.byref(out)),

@@ -431,32 +431,6 @@ size_t workspace_for(size_t n, const DtypeInfo &di, bool inplace = false, const 
     return di.bytes <= 2 ? count_layout(n, di.bytes).total : msd_layout(n, di.bytes, 0, inplace, tune).total;
 }
 
-// Key-value sorting workspace of 1- and 2-byte keys: the 64-bit words, the
-// final input positions, then an 8-byte MSD workspace whose alternate buffer
-// (its first n * 8 bytes) doubles as the gather target afterwards, and one
-// error word.  (The layout keeps room for the two-sort form of wider keys.)
-struct PairsLayout {
-    size_t words, perm, idx, err, inner, inner_bytes, total;
-};
-
-PairsLayout pairs_layout(size_t n, int key_bytes, const Tuning &tune8) {
-    PairsLayout L;
-    size_t off = 0;
-    auto take = [&](size_t bytes) {
-        const size_t at = off;
-        off = align_up(off + bytes);
-        return at;
-    };
-    L.words = take(8 * n);
-    L.perm = take(key_bytes == 8 ? 4 * n : 0);
-    L.idx = take(4 * n);
-    L.err = take(4);
-    L.inner = off;
-    L.inner_bytes = msd_layout(n, 8, 0, false, tune8).total;
-    L.total = L.inner + L.inner_bytes;
-    return L;
-}
-
 // Key-value sorting workspace of 4- and 8-byte keys (the value-carrying MSD
 // path): the MSD workspace with carry_bytes-wide value buffers (positions:
 // both parities, else the alternate one), then the gather target of values
@@ -475,9 +449,11 @@ PairsKvLayout pairs_kv_layout(size_t n, int key_bytes, int carry_bytes, bool pos
 }
 
 // Workspace of a key-value sort of n keys of key_bytes, for every form of
-// request (values carried, positions, positions then a gather of 8-byte values).
-size_t pairs_workspace_for(size_t n, int key_bytes, const Tuning &tune8) {
-    if (key_bytes <= 2) return pairs_layout(n, key_bytes, tune8).total;
+// request (values carried, positions, positions then a gather of 8-byte
+// values).  1- and 2-byte keys: their 32-bit order codes (n words) ahead of
+// the workspace of a 4-byte key-value sort.
+size_t pairs_workspace_for(size_t n, int key_bytes) {
+    if (key_bytes <= 2) return std::max(count_layout(n, key_bytes).total, align_up(4 * n) + pairs_workspace_for(n, 4));
     size_t b = msd_layout(n, key_bytes).total;  // keys alone (no values, no positions asked for)
     b = std::max(b, pairs_kv_layout(n, key_bytes, 4, false, 0).total);
     b = std::max(b, pairs_kv_layout(n, key_bytes, 8, false, 0).total);
@@ -629,7 +605,7 @@ bsort_status bsort_pairs_workspace_bytes(size_t n, bsort_dtype dt, size_t *bytes
     DtypeInfo di;
     if (!bytes || !dtype_info(dt, &di)) return BSORT_ERR_INVALID_ARG;
     if (di.bytes > 8) return BSORT_ERR_UNSUPPORTED;
-    *bytes = pairs_workspace_for(n, di.bytes, Tuning());
+    *bytes = pairs_workspace_for(n, di.bytes);
     return BSORT_OK;
 }
 
@@ -638,8 +614,8 @@ bsort_status bsort_pairs_workspace_bytes_tuned(size_t n, bsort_dtype dt, const b
     if (!bytes || !dtype_info(dt, &di)) return BSORT_ERR_INVALID_ARG;
     if (di.bytes > 8) return BSORT_ERR_UNSUPPORTED;
     Tuning t;
-    if (!to_tuning(tuning8, 8, &t)) return BSORT_ERR_INVALID_ARG;
-    *bytes = pairs_workspace_for(n, di.bytes, t);
+    if (!to_tuning(tuning8, 8, &t)) return BSORT_ERR_INVALID_ARG;  // (validated; the key-value levels have a fixed shape)
+    *bytes = pairs_workspace_for(n, di.bytes);
     return BSORT_OK;
 }
 
@@ -666,62 +642,28 @@ bsort_status bsort_pairs_ws(bsort_handle *handle, void *keys, void *values, size
     }
     if (!workspace) return BSORT_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(workspace) % kAlign) return BSORT_ERR_MISALIGNED;
-    if (di.bytes >= 4) {
-        if (ws_bytes < pairs_workspace_for(n, di.bytes, Tuning())) return BSORT_ERR_WORKSPACE_TOO_SMALL;
-        if (!values && !indices) {  // equal keys are bit-identical: the keys-only sort gives the same keys
-            const Tuning defaults;
-            return run_sort(handle, keys, n, di, descending, workspace, ws_bytes, st, false, &defaults);
-        }
-        return run_pairs_kv(handle, keys, values, value_bytes, indices, n, di, descending, workspace, st);
+    if (ws_bytes < pairs_workspace_for(n, di.bytes)) return BSORT_ERR_WORKSPACE_TOO_SMALL;
+    if (!values && !indices) {  // equal keys are bit-identical: the keys-only sort gives the same keys
+        const Tuning defaults;
+        return run_sort(handle, keys, n, di, descending, workspace, ws_bytes, st, false, &defaults);
     }
-    const PairsLayout L = pairs_layout(n, di.bytes, handle->tune[1]);
-    if (ws_bytes < L.total) return BSORT_ERR_WORKSPACE_TOO_SMALL;
+    if (di.bytes >= 4) return run_pairs_kv(handle, keys, values, value_bytes, indices, n, di, descending, workspace, st);
+    // 1- and 2-byte keys: their order codes as 32-bit words, sorted as
+    // unsigned keys carrying the values (or positions), then narrowed back
     (void)cudaGetLastError();
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return BSORT_ERR_CUDA;
     const int sms = num_sms_of(dev);
-    char *ws = static_cast<char *>(workspace);
-    uint64_t *words = reinterpret_cast<uint64_t *>(ws + L.words);
-    uint32_t *perm = di.bytes == 8 ? reinterpret_cast<uint32_t *>(ws + L.perm) : nullptr;
-    uint32_t *idx = reinterpret_cast<uint32_t *>(ws + L.idx);
-    uint32_t *err = reinterpret_cast<uint32_t *>(ws + L.err);
-    char *inner = ws + L.inner;
-    void *tmp = inner;  // the inner sort's alternate buffer, free once the sorts are done
     const Codec codec = codec_for(di, descending);
-    DtypeInfo word_info;
-    dtype_info(BSORT_U64, &word_info);
-    int launches = 0;
-    if (cudaMemsetAsync(err, 0, 4, st) != cudaSuccess) return BSORT_ERR_CUDA;
-    launch_pairs_pack(keys, di.bytes, n, codec, 0, nullptr, words, err, st, sms);
-    ++launches;
-    bsort_status s = run_sort(handle, words, n, word_info, 0, inner, L.inner_bytes, st);
-    launches += handle->rec.launches;
+    uint32_t *wide = static_cast<uint32_t *>(workspace);
+    launch_widen(keys, di.bytes, n, codec, wide, st, sms);
+    DtypeInfo word;
+    dtype_info(BSORT_U32, &word);
+    const bsort_status s = run_pairs_kv(handle, wide, values, value_bytes, indices, n, word, 0,
+                                        static_cast<char *>(workspace) + align_up(4 * n), st);
     if (s != BSORT_OK) return s;
-    if (di.bytes == 8) {
-        launch_pairs_perm(words, n, perm, handle->last_ctl, err, st, sms);
-        launch_pairs_pack(keys, 8, n, codec, 1, perm, words, err, st, sms);
-        launches += 2;
-        s = run_sort(handle, words, n, word_info, 0, inner, L.inner_bytes, st);
-        launches += handle->rec.launches;
-        if (s != BSORT_OK) return s;
-    }
-    Ctl *ctl = handle->last_ctl;
-    const bool gathers = values || di.bytes == 8;  // positions kept only for the gathers
-    launch_pairs_index(words, perm, n, di.bytes <= 4 ? keys : nullptr, di.bytes, codec, gathers ? idx : nullptr,
-                       indices, ctl, err, st, sms);
-    ++launches;
-    if (di.bytes == 8) {  // keys by their positions, then back into the caller's buffer
-        launch_gather(keys, 8, idx, n, tmp, ctl, st, sms);
-        ++launches;
-        if (cudaMemcpyAsync(keys, tmp, 8 * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return BSORT_ERR_CUDA;
-    }
-    if (values) {
-        launch_gather(values, static_cast<int>(value_bytes), idx, n, tmp, ctl, st, sms);
-        ++launches;
-        if (cudaMemcpyAsync(values, tmp, value_bytes * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-            return BSORT_ERR_CUDA;
-    }
-    handle->rec.launches = launches;
+    launch_narrow(wide, di.bytes, n, codec, keys, st, sms);
+    handle->rec.launches += 2;
     return cudaGetLastError() == cudaSuccess ? BSORT_OK : BSORT_ERR_CUDA;
 }
 

@@ -101,16 +101,14 @@ void launch_msd_kv(const Work &wk, cudaStream_t st, Recorder &rec, int num_sms);
 template <typename K>
 void msd_prepare();
 
-// Key-value sorting: the pieces around the 8-byte sort of (code << 32 |
-// position) words.  Each launches one kernel.  `err` is a device word that
-// survives the sorts' control-block resets; k_pairs_index folds it into `ctl`.
-void launch_pairs_pack(const void *keys, int key_bytes, uint64_t n, const Codec &codec, int part,
-                       const uint32_t *perm, uint64_t *words, uint32_t *err, cudaStream_t st, int num_sms);
-void launch_pairs_perm(const uint64_t *words, uint64_t n, uint32_t *perm, const Ctl *ctl, uint32_t *err,
-                       cudaStream_t st, int num_sms);
-void launch_pairs_index(const uint64_t *words, const uint32_t *perm, uint64_t n, void *keys, int key_bytes,
-                        const Codec &codec, uint32_t *idx, int64_t *indices, Ctl *ctl, const uint32_t *err,
-                        cudaStream_t st, int num_sms);
+// Key-value sorting of 1- and 2-byte keys: wide[i] = the key's order code
+// (descending folded in) as a 32-bit word, and back.  One kernel each.
+void launch_widen(const void *keys, int key_bytes, uint64_t n, const Codec &codec, uint32_t *wide, cudaStream_t st,
+                  int num_sms);
+void launch_narrow(const uint32_t *wide, int key_bytes, uint64_t n, const Codec &codec, void *keys, cudaStream_t st,
+                   int num_sms);
+// dst[i] = src[idx[i]], elements of elem_bytes (1, 2, 4 or 8); an idx entry
+// >= n sets kErrBounds in ctl.  One kernel.
 void launch_gather(const void *src, int elem_bytes, const uint32_t *idx, uint64_t n, void *dst, Ctl *ctl,
                    cudaStream_t st, int num_sms);
 

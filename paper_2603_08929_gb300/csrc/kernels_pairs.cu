@@ -1,16 +1,7 @@
-// Key-value sorting around the 8-byte MSD pipeline.
-//
-// A stable key-value sort is a sort of distinct words: each key's
-// order-preserving code (the same encode_key as the key sort, descending
-// folded in) goes to the high half of a 64-bit word and its input position to
-// the low half.  Positions make every word unique, so the unstable digit
-// passes of the 8-byte pipeline give exactly the stable order.  8-byte keys
-// take two such sorts over the halves of their code, low half first (LSD
-// order): the second sort's low half is the position in the first sort's
-// output, which orders ties of the high half by the low half and then by the
-// input position.  The kernels here build the words, turn sorted words into
-// input positions, and gather keys and values along them; all are
-// grid-stride loops over n (memory-bound, one pass each).
+// Key-value sorting helpers around the value-carrying MSD pipeline: the
+// widening of 1- and 2-byte keys to 32-bit order codes and back, and the
+// gather of values along sorted input positions.  All are grid-stride loops
+// over n (memory-bound, one pass each).
 #include "bsort_device.cuh"
 #include "bsort_launch.h"
 
@@ -25,64 +16,24 @@ __host__ __device__ inline int pairs_grid(uint64_t n, int num_sms) {
     return static_cast<int>(want < cap ? (want ? want : 1) : cap);
 }
 
-// word[i] = code << 32 | i, code = encode(keys[src]) (its low or high 32 bits
-// for 8-byte keys; part 0 / 1), src = i or perm[i].  A perm entry >= n is
-// refused (bit kErrBounds into *err, key 0 read instead).
+// wide[i] = the order code of keys[i] (encode_key, descending folded in),
+// zero-extended: the 32-bit words sort, as unsigned integers, in the keys'
+// order, equal keys to equal words.
 template <typename K>
-__global__ void __launch_bounds__(kPairThreads) k_pairs_pack(const K *__restrict__ keys, uint64_t n, Codec codec,
-                                                             int part, const uint32_t *__restrict__ perm,
-                                                             uint64_t *__restrict__ words, uint32_t *err) {
-    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
-    for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < n; i += stride) {
-        uint64_t src = i;
-        if (perm) {
-            src = perm[i];
-            if (src >= n) {
-                atomicOr(err, kErrBounds);
-                src = 0;
-            }
-        }
-        const uint64_t k = static_cast<uint64_t>(encode_key(keys[src], codec));
-        const uint64_t code = sizeof(K) <= 4 ? k : (part == 0 ? (k & 0xffffffffull) : (k >> 32));
-        words[i] = (code << 32) | i;
-    }
-}
-
-// perm[i] = low half of word[i]; thread 0 also keeps the sort's error bits
-// (the next sort clears its control block).
-__global__ void __launch_bounds__(kPairThreads) k_pairs_perm(const uint64_t *__restrict__ words, uint64_t n,
-                                                             uint32_t *__restrict__ perm, const Ctl *ctl,
-                                                             uint32_t *err) {
-    if (blockIdx.x == 0 && threadIdx.x == 0 && ctl->error) atomicOr(err, ctl->error);
+__global__ void __launch_bounds__(kPairThreads) k_widen(const K *__restrict__ keys, uint64_t n, Codec codec,
+                                                        uint32_t *__restrict__ wide) {
     const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
     for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < n; i += stride)
-        perm[i] = static_cast<uint32_t>(words[i]);
+        wide[i] = static_cast<uint32_t>(encode_key(keys[i], codec));
 }
 
-// Input position of output element i: the low half of the sorted word (then
-// through perm for 8-byte keys).  Writes idx[i], indices[i] (if requested)
-// and, for keys of at most 4 bytes, the sorted key itself (decoded from the
-// high half).  Folds the earlier error bits into the control block.
+// keys[i] = the key whose order code wide[i] holds (its low bits).
 template <typename K>
-__global__ void __launch_bounds__(kPairThreads) k_pairs_index(const uint64_t *__restrict__ words,
-                                                              const uint32_t *__restrict__ perm, uint64_t n,
-                                                              K *__restrict__ keys, Codec codec,
-                                                              uint32_t *__restrict__ idx, int64_t *__restrict__ indices,
-                                                              Ctl *ctl, const uint32_t *err) {
-    if (blockIdx.x == 0 && threadIdx.x == 0 && *err) set_error(ctl, *err);
+__global__ void __launch_bounds__(kPairThreads) k_narrow(const uint32_t *__restrict__ wide, uint64_t n, Codec codec,
+                                                         K *__restrict__ keys) {
     const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
-    for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < n; i += stride) {
-        const uint64_t w = words[i];
-        uint64_t src = static_cast<uint32_t>(w);
-        if (perm) src = src < n ? perm[src] : n;
-        if (src >= n) {
-            set_error(ctl, kErrBounds);
-            src = 0;
-        }
-        if (idx) idx[i] = static_cast<uint32_t>(src);
-        if (indices) indices[i] = static_cast<int64_t>(src);
-        if (keys) keys[i] = decode_key(static_cast<K>(w >> 32), codec);
-    }
+    for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < n; i += stride)
+        keys[i] = decode_key(static_cast<K>(wide[i]), codec);
 }
 
 // dst[i] = src[idx[i]] (idx < n by construction; a larger entry is refused).
@@ -120,32 +71,18 @@ __global__ void __launch_bounds__(kPairThreads) k_gather(const T *__restrict__ s
 
 }  // namespace
 
-void launch_pairs_pack(const void *keys, int key_bytes, uint64_t n, const Codec &codec, int part,
-                       const uint32_t *perm, uint64_t *words, uint32_t *err, cudaStream_t st, int num_sms) {
+void launch_widen(const void *keys, int key_bytes, uint64_t n, const Codec &codec, uint32_t *wide, cudaStream_t st,
+                  int num_sms) {
     const int g = pairs_grid(n, num_sms);
-    switch (key_bytes) {
-    case 1: k_pairs_pack<uint8_t><<<g, kPairThreads, 0, st>>>(static_cast<const uint8_t *>(keys), n, codec, part, perm, words, err); break;
-    case 2: k_pairs_pack<uint16_t><<<g, kPairThreads, 0, st>>>(static_cast<const uint16_t *>(keys), n, codec, part, perm, words, err); break;
-    case 4: k_pairs_pack<uint32_t><<<g, kPairThreads, 0, st>>>(static_cast<const uint32_t *>(keys), n, codec, part, perm, words, err); break;
-    default: k_pairs_pack<uint64_t><<<g, kPairThreads, 0, st>>>(static_cast<const uint64_t *>(keys), n, codec, part, perm, words, err); break;
-    }
+    if (key_bytes == 1) k_widen<uint8_t><<<g, kPairThreads, 0, st>>>(static_cast<const uint8_t *>(keys), n, codec, wide);
+    else k_widen<uint16_t><<<g, kPairThreads, 0, st>>>(static_cast<const uint16_t *>(keys), n, codec, wide);
 }
 
-void launch_pairs_perm(const uint64_t *words, uint64_t n, uint32_t *perm, const Ctl *ctl, uint32_t *err,
-                       cudaStream_t st, int num_sms) {
-    k_pairs_perm<<<pairs_grid(n, num_sms), kPairThreads, 0, st>>>(words, n, perm, ctl, err);
-}
-
-void launch_pairs_index(const uint64_t *words, const uint32_t *perm, uint64_t n, void *keys, int key_bytes,
-                        const Codec &codec, uint32_t *idx, int64_t *indices, Ctl *ctl, const uint32_t *err,
-                        cudaStream_t st, int num_sms) {
+void launch_narrow(const uint32_t *wide, int key_bytes, uint64_t n, const Codec &codec, void *keys, cudaStream_t st,
+                   int num_sms) {
     const int g = pairs_grid(n, num_sms);
-    switch (key_bytes) {
-    case 1: k_pairs_index<uint8_t><<<g, kPairThreads, 0, st>>>(words, perm, n, static_cast<uint8_t *>(keys), codec, idx, indices, ctl, err); break;
-    case 2: k_pairs_index<uint16_t><<<g, kPairThreads, 0, st>>>(words, perm, n, static_cast<uint16_t *>(keys), codec, idx, indices, ctl, err); break;
-    case 4: k_pairs_index<uint32_t><<<g, kPairThreads, 0, st>>>(words, perm, n, static_cast<uint32_t *>(keys), codec, idx, indices, ctl, err); break;
-    default: k_pairs_index<uint64_t><<<g, kPairThreads, 0, st>>>(words, perm, n, static_cast<uint64_t *>(keys), codec, idx, indices, ctl, err); break;
-    }
+    if (key_bytes == 1) k_narrow<uint8_t><<<g, kPairThreads, 0, st>>>(wide, n, codec, static_cast<uint8_t *>(keys));
+    else k_narrow<uint16_t><<<g, kPairThreads, 0, st>>>(wide, n, codec, static_cast<uint16_t *>(keys));
 }
 
 void launch_gather(const void *src, int elem_bytes, const uint32_t *idx, uint64_t n, void *dst, Ctl *ctl,

@@ -144,12 +144,13 @@ def test_pairs_argument_checks_without_a_gpu(lib):
         assert lib.bsort_pairs_ws(h, k, v, 4, ix, 10, 6, 0, ws, need - 1, None) == 5
     finally:
         lib.bsort_handle_destroy(h)
-    # 4- and 8-byte keys: the value-carrying sort (alternate keys, two 4-byte
-    # position buffers, an 8-byte gather target), untouched by the word-sort
-    # tuning; 1- and 2-byte keys: the packed-word sort, which a wider digit grows
+    # the value-carrying sort (alternate keys, two 4-byte position buffers, an
+    # 8-byte gather target); 1- and 2-byte keys add their 32-bit order codes;
+    # no tuning changes it (the key-value levels have a fixed shape)
     n = 1 << 20
     assert pkg.pairs_workspace_bytes(n, "float64") - pkg.pairs_workspace_bytes(n, "float32") >= 4 * n
     assert pkg.pairs_workspace_bytes(n, "int32") >= (4 + 4 + 4 + 8) * n
-    assert pkg.pairs_workspace_bytes(n, "int32", tuning8={"radix_bits": 11}) == pkg.pairs_workspace_bytes(n, "int32")
-    assert pkg.pairs_workspace_bytes(n, "uint8", tuning8={"radix_bits": 11}) > pkg.pairs_workspace_bytes(n, "uint8")
-    assert pkg.pairs_workspace_bytes(n, "uint8", tuning8={}) == pkg.pairs_workspace_bytes(n, "uint8")
+    assert pkg.pairs_workspace_bytes(n, "uint8") - pkg.pairs_workspace_bytes(n, "int32") >= 4 * n
+    for dt in ("int32", "uint8", "float64"):
+        assert pkg.pairs_workspace_bytes(n, dt, tuning8={"radix_bits": 11}) == pkg.pairs_workspace_bytes(n, dt)
+        assert pkg.pairs_workspace_bytes(n, dt, tuning8={}) == pkg.pairs_workspace_bytes(n, dt)

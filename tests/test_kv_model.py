@@ -18,6 +18,26 @@ import pytest
 import oracle as O
 import workloads as W
 
+UINT = {1: np.uint8, 2: np.uint16, 4: np.uint32, 8: np.uint64}
+
+
+def code(x: np.ndarray, fmt: O.KeyFormat, descending: bool) -> np.ndarray:
+    """The order code of Sec. III restated (not the library's): the sign bit
+    inverted for signed keys, every bit of a negative float inverted, the sign
+    bit of a non-negative float set; descending inverts all bits.  Also the
+    32-bit word a 1- or 2-byte key is widened to before a key-value sort."""
+    w = fmt.w
+    u = x.view(UINT[w // 8]).astype(np.uint64)
+    sign = np.uint64(1) << np.uint64(w - 1)
+    full = np.uint64((1 << w) - 1) if w < 64 else np.uint64(0xFFFFFFFFFFFFFFFF)
+    if fmt.kind == O.SIGNED:
+        k = u ^ sign
+    elif fmt.kind == O.FLOAT:
+        k = np.where(u & sign, u ^ full, u ^ sign)
+    else:
+        k = u
+    return k ^ full if descending else k
+
 
 def model_places(digits: np.ndarray, n_valid: int, warps: int, it: int) -> np.ndarray:
     """Places of a tile's valid items by the warp-striped peer-group protocol.
@@ -158,10 +178,23 @@ def model_kv_sort(codes: np.ndarray, bits: int, unit_cap: int, warps: int = 2) -
 @pytest.mark.parametrize("dist", ["uniform", "distinct8", "zipf", "sorted"])
 @pytest.mark.parametrize("dtype,desc", [("int32", False), ("float32", True), ("uint16", False)])
 def test_model_sort_is_the_stable_permutation(dist, dtype, desc):
-    from test_pairs_model import code
     n = 3000
     x = W.make(dist, dtype, n, seed=21)
     fmt = O.FORMATS[x.dtype]
     k = code(x, fmt, desc)
     got = model_kv_sort(k, fmt.w, unit_cap=300)
     assert np.array_equal(got, O.stable_argsort(x, desc))
+
+
+@pytest.mark.parametrize("dtype", ["uint8", "int8", "uint16", "int16", "float16"])
+@pytest.mark.parametrize("desc", [False, True])
+def test_small_keys_widened_to_order_codes(dtype, desc):
+    """1- and 2-byte keys are sorted as their order codes widened to 32-bit
+    words: a stable sort of the words (unsigned, ascending) is the oracle's
+    stable permutation of the keys, and narrowing the sorted words gives the
+    sorted keys."""
+    x = W.make("zipf", dtype, 20000, seed=4)
+    k = code(x, O.FORMATS[x.dtype], desc).astype(np.uint32)
+    p = np.argsort(k, kind="stable")
+    assert np.array_equal(p, O.stable_argsort(x, desc))
+    assert np.array_equal(k[p], np.sort(k))
