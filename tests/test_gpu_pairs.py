@@ -165,9 +165,10 @@ def test_pairs_unit_boundaries(dtype, n):
 def test_pairs_wide_units(dtype, n, high):
     """Finish units with more than 24 varying bits: stable passes over the
     top 16, then runs of ties there sorted by the whole key -- short runs
-    (high = 2^16 top values: few ties; 256: runs of a few keys) and runs too
-    long for that (high = 4), which take every pass.  Keys: a random high
-    part above a gap of zero bits and a random low part."""
+    (high = 2^16 top values: few ties), runs around the 16 keys the
+    insertion sort takes (256 values for ~2000-key units) and runs far
+    longer (high = 4), which take every pass.  Keys: a random high part
+    above a gap of zero bits and a random low part."""
     rng = np.random.default_rng(n + high)
     shift = 40 if dtype != "int32" else 28
     lowbits = 20 if dtype != "int32" else 16

@@ -198,3 +198,57 @@ def test_small_keys_widened_to_order_codes(dtype, desc):
     p = np.argsort(k, kind="stable")
     assert np.array_equal(p, O.stable_argsort(x, desc))
     assert np.array_equal(k[p], np.sort(k))
+
+
+def model_wide_finish(codes: np.ndarray, tie_run: int = 16):
+    """The finish of a unit of 8-byte keys with many varying bits [lo, hi):
+    stable passes over the top 16 of them, then every run of keys still tied
+    there sorted by the whole key with a stable insertion sort when it holds
+    at most tie_run keys; a longer run sends the unit through the passes of
+    the low bits and then the top bits again, from that order.  Returns the
+    permutation and whether the long-run path was taken."""
+    idx = np.arange(codes.size)
+    a, o = np.bitwise_and.reduce(codes), np.bitwise_or.reduce(codes)
+    diff = int(a ^ o)
+    lo = (diff & -diff).bit_length() - 1
+    hi = diff.bit_length()
+    top = hi - 16
+
+    def passes(idx, frm, to):
+        for s, w in lsd_passes(frm, to):
+            dg = ((codes[idx] >> np.uint64(s)) & np.uint64((1 << w) - 1)).astype(np.int64)
+            idx = idx[np.argsort(dg, kind="stable")]
+        return idx
+
+    idx = passes(idx, top, hi)
+    k = codes[idx]
+    tops = k >> np.uint64(top)
+    starts = np.flatnonzero(np.concatenate([[True], tops[1:] != tops[:-1]]))
+    ends = np.concatenate([starts[1:], [k.size]])
+    if (ends - starts).max() > tie_run:
+        return passes(passes(idx, lo, top), top, hi), True
+    idx = idx.copy()
+    for s, e in zip(starts, ends):
+        for x in range(s + 1, e):  # insertion sort, strict comparison: stable
+            y = x
+            while y > s and codes[idx[y - 1]] > codes[idx[y]]:
+                idx[y - 1], idx[y] = idx[y], idx[y - 1]
+                y -= 1
+    return idx, False
+
+
+@pytest.mark.parametrize("high,expect_long", [(1 << 16, False), (4096, False), (256, True), (4, True)])
+def test_wide_finish_is_stable(high, expect_long):
+    """Keys = random high part above zero bits and a random low part, with
+    repeats: few ties in the top 16 varying bits (high = 2^16), short tie
+    runs (4096), runs too long for the insertion sort (256: ~8 keys per top
+    value, the longest over 16; 4): the finish gives the stable order (ties
+    in input order) in every case."""
+    rng = np.random.default_rng(high)
+    n = 2000
+    hi_part = rng.integers(0, high, n).astype(np.uint64)
+    x = (hi_part << np.uint64(40)) | rng.integers(0, 1 << 20, n).astype(np.uint64)
+    x[rng.integers(0, n, 300)] = x[rng.integers(0, n, 300)]  # exact duplicates
+    got, long_path = model_wide_finish(x)
+    assert long_path == expect_long
+    assert np.array_equal(got, np.argsort(x, kind="stable"))
